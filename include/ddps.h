@@ -1,0 +1,261 @@
+/*
+ * ddps.h — C ABI of a single-GPU (sm_103a) DDPS solver.
+ *
+ * DDPS (Manguoglu, "A domain-decomposing parallel sparse linear system
+ * solver", arXiv 1008.1700) solves a sparse system A x = f as follows.
+ *   Sec. 3, Eq. (1)-(2) and Fig. 2 step 1: A is split by block rows into
+ *     A = D + R, D = diag(A_11, ..., A_pp).
+ *   Fig. 2 step 2: every diagonal block is factored, A_ii = L_i U_i (exact LU).
+ *   Fig. 2 step 3 and the Sec. 3 dropping rule: R~ is R minus dropped entries.
+ *   Fig. 2 steps 4-5: spikes G = D~^-1 R~, c = indices of G's nonzero columns.
+ *   Fig. 2 step 6: a Krylov method (BiCGStab, Sec. 4) on A x = f with the
+ *     preconditioner P = D~ + R~, applied by Fig. 3:
+ *       6.1 g = D~^-1 y;  6.2 G^ = I(c,c) + G(c,c), g^ = g(c);
+ *       6.3 solve G^ z^ = g^ (BiCGStab, tolerance eps_in);
+ *       6.4-6.5 z = g - G(:,c) z^, computed here as z = D~^-1 (y - R~ z^).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are CSR with int32 row pointers and column indices (0-based,
+ *     columns sorted inside a row, no duplicates) and float64 values.
+ *   - A handle may hold a batch of independent systems: they are stacked into
+ *     one block-diagonal matrix of order n = sum of the systems' orders, whose
+ *     block rows are listed in block_ptr; sys_block_ptr says which blocks
+ *     belong to which system.  No entry of A may couple two systems.  Krylov
+ *     scalars, norms and convergence are kept per system.
+ *   - Pointers documented "host" are read during the call only.  Pointers
+ *     documented "device" must stay valid until the stream work they are used
+ *     in has completed; the caller owns them.  The handle owns everything else
+ *     (factors, spikes, workspace) and frees it in ddps_destroy.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls enqueue work on it; a call returns before the work has
+ *     finished unless documented otherwise.
+ *   - No exception crosses the ABI.  On failure an entry point returns a
+ *     non-zero ddps_status and ddps_last_error(h) describes it.
+ */
+#ifndef DDPS_H
+#define DDPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddps_handle ddps_handle;
+
+typedef enum {
+  DDPS_OK = 0,
+  DDPS_ERR_INVALID_ARG = 1,     /* bad size, pointer, pattern or option */
+  DDPS_ERR_SINGULAR_BLOCK = 2,  /* a pivot of some A_ii fell under the threshold (Sec. 3 requires
+                                   nonsingular diagonal blocks) */
+  DDPS_ERR_NOT_CONVERGED = 3,   /* maxit_out reached: x holds the last iterate, info the residual */
+  DDPS_ERR_OUT_OF_MEMORY = 4,   /* a device allocation failed */
+  DDPS_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+  DDPS_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+  DDPS_ERR_STATE = 7            /* call order: e.g. solve before factor */
+} ddps_status;
+
+typedef enum { DDPS_FP64 = 0, DDPS_FP32 = 1, DDPS_BF16 = 2 } ddps_precision;
+
+/* Fig. 2 step 3.  COLUMN: the Sec. 3 rule — in block row R_i, column k is
+ * dropped when ||R_i(:,k)||_inf <= drop_tol * max_j ||R_i(:,j)||_inf.
+ * ABS: an entry r_ij is dropped when |r_ij| < drop_tol. */
+typedef enum { DDPS_DROP_NONE = 0, DDPS_DROP_COLUMN = 1, DDPS_DROP_ABS = 2 } ddps_drop_mode;
+
+typedef struct {
+  int32_t drop_mode;      /* ddps_drop_mode */
+  double drop_tol;        /* delta (COLUMN) or tau (ABS) */
+  int32_t factor_prec;    /* FP64 or FP32: storage and arithmetic of the block factors (Fig. 2 step 2)
+                             and of the block solves 6.1 / 6.5 */
+  int32_t spike_prec;     /* FP64, FP32, or BF16: operands of the spike products of Fig. 2 step 4
+                             (BF16 = bf16 operands on the tensor cores, fp32 accumulation) */
+  int32_t ghat_prec;      /* FP64, FP32 or BF16 storage of G^ (Sec. 3: dense per-partition arrays) */
+  int32_t inner_prec;     /* FP64 or FP32 vectors of the inner BiCGStab on G^ (6.3) */
+  double tol_out;         /* outer stop: ||f - A x||_inf <= tol_out ||f||_inf, per system */
+  int32_t maxit_out;      /* outer iteration cap (Sec. 4: 1000) */
+  double tol_in;          /* inner stop: ||g^ - G^ z^||_2 <= tol_in ||g^||_2 (Sec. 4: 1e-4) */
+  int32_t maxit_in;       /* inner iteration cap (Sec. 4: 100) */
+  double pivot_tol;       /* |u_kk| < pivot_tol * max|row k of A_ii| => DDPS_ERR_SINGULAR_BLOCK */
+  int32_t leaf_size;      /* nested-dissection leaf size of the block ordering (0 = default) */
+  int32_t rhs_chunk;      /* spike right-hand sides per pass (0 = chosen from free memory) */
+  int32_t verbose;        /* 1: print analysis statistics to stderr */
+} ddps_options;
+
+typedef struct {
+  double outer_iterations;   /* max over systems; half steps count 0.5 (Sec. 4 convention) */
+  int32_t inner_iterations;  /* total inner BiCGStab iterations, all preconditioner applications */
+  int32_t precond_applies;   /* Fig. 3 applications */
+  int32_t converged;         /* 1 if every system met tol_out */
+  int32_t guess_used;        /* 1 if a reduced initial guess was used (and accepted) */
+  double relres_inf;         /* max over systems of ||f - A x||_inf / ||f||_inf (recomputed) */
+  double first_inner_iters;  /* inner iterations of the first preconditioner application */
+  double ms_solve;           /* wall time of the call, host clock */
+} ddps_solve_info;
+
+typedef struct {
+  int64_t n, nnz, nsys, nblocks;
+  int64_t m;                 /* |c|: order of the reduced system G^ */
+  int64_t nnz_rt;            /* stored entries of R~ */
+  int64_t nfronts, nlevels;  /* multifrontal tree of all blocks */
+  int64_t factor_entries;    /* sum over fronts of m_f^2 (dense front storage) */
+  int64_t factor_lu_entries; /* entries of L and U proper (what a solve streams) */
+  int64_t ghat_entries;      /* sum over blocks of |c ∩ block| * |c_i| */
+  int64_t max_front;         /* largest front order */
+  int64_t max_rhs;           /* largest |c_i| (spike right-hand sides of one block) */
+  int64_t device_bytes;      /* device memory held by the handle */
+  double factor_flops;       /* partial-LU flops of all fronts */
+  double spike_flops;        /* multi-RHS forward/backward flops for G^ */
+} ddps_sizes;
+
+/* Fills *opt with the paper's solver settings (Sec. 4: eps_in 1e-4, 100 inner
+ * and 1000 outer iterations) and a 1e-10 outer tolerance, FP64 everywhere,
+ * no dropping. */
+void ddps_default_options(ddps_options* opt);
+
+/* Symbolic phase: split A = D + R by block rows (Eq. (1)-(2)), apply the drop
+ * rule (Fig. 2 step 3), find c (Fig. 2 step 5), order every A_ii by nested
+ * dissection and lay out the multifrontal factors, the spikes and G^.
+ * Sec. 3 notes that stages 1-5 need no right-hand side.
+ *   n, nnz            order and stored entries of the stacked matrix
+ *   rowptr, colind    host CSR pattern (n+1 and nnz entries)
+ *   p, block_ptr      host, p+1 increasing row offsets, block_ptr[0]=0, block_ptr[p]=n
+ *   nsys, sys_block_ptr  host, nsys+1 block offsets (NULL with nsys=1: one system)
+ *   values            host float64[nnz]; required when opt->drop_mode != NONE (the
+ *                     drop rule reads values), else may be NULL
+ *   opt               host options (NULL = defaults)
+ * On success *out owns the analysis and the device copies of the pattern. */
+ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                         int32_t p, const int64_t* block_ptr, int32_t nsys,
+                         const int32_t* sys_block_ptr, const double* values,
+                         const ddps_options* opt, ddps_handle** out);
+
+/* Numeric phase, Fig. 2 steps 1-4: scatter A's values into the factor fronts
+ * and R~, factor every A_ii, form the spikes and store G^ = I + G(c,c).
+ *   values  device float64[nnz], same pattern as at analysis
+ * Synchronises `stream` once at the end to read the pivot check; returns
+ * DDPS_ERR_SINGULAR_BLOCK (see ddps_last_error for block and row) when a
+ * pivot fails the threshold. */
+ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream);
+
+/* Fig. 2 step 6: right-preconditioned BiCGStab on A x = f with the DDPS
+ * preconditioner, x0 = 0, per-system scalars, stopping on the recomputed
+ * true residual (tol_out, infinity norm).
+ *   f  device float64[n];  x  device float64[n] (output)
+ *   info  host, may be NULL.
+ * Synchronises `stream` (convergence is read on the host between iterations).
+ * Returns DDPS_ERR_NOT_CONVERGED when some system misses tol_out within
+ * maxit_out (x then holds the last iterate). */
+ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, void* stream,
+                       ddps_solve_info* info);
+
+/* Same as ddps_solve with host buffers: copies f to the device, solves and
+ * copies x back (f, x: host float64[n]).  Synchronises. */
+ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, void* stream,
+                            ddps_solve_info* info);
+
+/* Initial guess for the reduced unknowns z^ of the first preconditioner
+ * application of the next solves (the hook a learned predictor fills).
+ *   zhat0  device float64[m] in the order of c; NULL removes the guess.
+ * The guess is used only if its reduced residual is smaller than that of
+ * z^ = 0; the inner BiCGStab then runs to tol_in from it as usual. */
+ddps_status ddps_set_reduced_guess(ddps_handle* h, const double* zhat0, void* stream);
+
+/* Copies the reduced solution z^ and the reduced right-hand side g^ of the
+ * first preconditioner application of the last solve (device float64[m]
+ * each; either may be NULL).  Enqueued on `stream`. */
+ddps_status ddps_get_reduced_solution(ddps_handle* h, double* zhat, double* ghat, void* stream);
+
+/* Fig. 3 step 6.1 alone: g = D~^-1 y for all blocks (device float64[n] in/out). */
+ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* stream);
+
+/* Fig. 3 step 6.2 product: w = G^ v = v + G(c,c) v (device float64[m] in/out). */
+ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream);
+
+/* Fig. 3 in full: z = P^-1 y (device float64[n] in/out).  Runs the inner
+ * solve from z^ = 0; synchronises `stream` between inner iterations. */
+ddps_status ddps_precond_apply(ddps_handle* h, const double* y, double* z, void* stream);
+
+/* y = A x with the analysed pattern and the last factored values
+ * (device float64[n] in/out). */
+ddps_status ddps_spmv(ddps_handle* h, const double* x, double* y, void* stream);
+
+/* Sizes of the analysis (host struct). */
+ddps_status ddps_get_sizes(const ddps_handle* h, ddps_sizes* s);
+
+/* The interface set c (host int64[m], global row indices, ascending within
+ * each system, systems in order). */
+ddps_status ddps_get_interface(const ddps_handle* h, int64_t* c);
+
+/* Layout of G^ for block b: rows q0..q1-1 of the reduced system (the rows of
+ * the block that lie in c) and ncols coupling columns; cols (host int64[ncols],
+ * may be NULL) receives their positions in c. */
+ddps_status ddps_get_ghat_layout(const ddps_handle* h, int32_t b, int64_t* q0, int64_t* q1,
+                                 int64_t* ncols, int64_t* cols);
+
+/* Copies G(c ∩ block b, c_b) — the off-identity part of block b's rows of
+ * G^ — row-major, converted to float64, into host memory dst
+ * ((q1-q0) * ncols entries).  Synchronises `stream`. */
+ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* stream);
+
+/* Number of kernels this handle has launched since ddps_analyze (host
+ * counter, read without synchronising). */
+int64_t ddps_launch_count(const ddps_handle* h);
+
+/* Host-only symbolic analysis: runs the analysis of ddps_analyze without any
+ * device work and reports its sizes (may be NULL), the new-to-old row
+ * permutation of the nested-dissection orders (host int32[n], may be NULL)
+ * and the interface set c (host int64 array with room for n entries, the
+ * first sizes->m are written; may be NULL).  Arguments as ddps_analyze. */
+ddps_status ddps_symbolic(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                          int32_t p, const int64_t* block_ptr, int32_t nsys,
+                          const int32_t* sys_block_ptr, const double* values,
+                          const ddps_options* opt, ddps_sizes* sizes, int32_t* perm, int64_t* c);
+
+/* Frees the handle and all device memory it holds (NULL is a no-op). */
+ddps_status ddps_destroy(ddps_handle* h);
+
+/* Text of the last error on h (or of the last failed ddps_analyze when h is NULL). */
+const char* ddps_last_error(const ddps_handle* h);
+const char* ddps_status_string(ddps_status s);
+
+/* ------------------------------------------------------------------------
+ * Learned initial guess for 6.3: a multilayer perceptron with `layers`
+ * hidden layers of width `hidden`, ReLU, linear output; loss
+ * (1/2B) sum_b ||y_b - t_b||^2; Adam with bias correction.  The network has
+ * no counterpart in the paper; it fills the initial-guess slot of the inner
+ * iterative solve (6.3), whose result still has to meet tol_in.
+ * Parameters are one float32 device array laid out
+ *   [W1 (hidden x d_in) row-major, b1, W2 (hidden x hidden), b2, ...,
+ *    W_out (d_out x hidden), b_out].
+ * ------------------------------------------------------------------------ */
+
+/* Number of float32 parameters. */
+int64_t ddps_mlp_param_count(int32_t d_in, int32_t hidden, int32_t layers, int32_t d_out);
+
+/* Bytes of device workspace the forward/backward calls need for batch B. */
+int64_t ddps_mlp_workspace_bytes(int32_t d_in, int32_t hidden, int32_t layers, int32_t d_out,
+                                 int32_t B);
+
+/* Y = net(X): X device float32[B x d_in] row-major, Y device float32[B x d_out]. */
+ddps_status ddps_mlp_forward(const float* params, int32_t d_in, int32_t hidden, int32_t layers,
+                             int32_t d_out, const float* X, int32_t B, float* Y, void* workspace,
+                             void* stream);
+
+/* grads (device float32[param_count]) = d loss / d params for targets T
+ * (device float32[B x d_out]); loss (device float32[1]) receives the loss. */
+ddps_status ddps_mlp_backward(const float* params, int32_t d_in, int32_t hidden, int32_t layers,
+                              int32_t d_out, const float* X, const float* T, int32_t B,
+                              float* grads, float* loss, void* workspace, void* stream);
+
+/* One Adam step in place over `count` parameters; m, v are device float32
+ * moment buffers (zero before step 1); step is the 1-based step number. */
+ddps_status ddps_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
+                          float lr, float beta1, float beta2, float eps, int32_t step,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDPS_H */

@@ -1,0 +1,1129 @@
+// C ABI of the DDPS solver: handle lifetime, device layout and the host-side
+// control of the numeric phases.  The arithmetic of every step runs in the
+// kernels of factor.cu, solve.cu and krylov.cu; this file only sequences them.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "ddps.h"
+#include "ddps_internal.h"
+#include "krylov.h"
+#include "launch.h"
+
+using namespace ddps;
+
+namespace {
+
+struct Fail {
+  ddps_status st;
+  std::string msg;
+};
+
+thread_local std::string g_last_error;
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw Fail{DDPS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};    \
+  } while (0)
+
+template <typename T>
+size_t esize() {
+  return sizeof(T);
+}
+
+size_t prec_size(int prec) { return prec == DDPS_FP64 ? 8 : (prec == DDPS_FP32 ? 4 : 2); }
+
+}  // namespace
+
+struct ddps_handle {
+  std::string err;
+  ddps_options opt{};
+  Analysis A;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t launches = 0;
+
+  // device copies of the pattern and maps
+  int32_t *rowptr = nullptr, *colind = nullptr;
+  double* vals = nullptr;
+  int64_t* amap = nullptr;
+  int32_t *perm = nullptr, *iperm = nullptr;
+  // multifrontal structure
+  DevFronts F{};
+  int32_t* parent = nullptr;
+  int32_t* level_fronts = nullptr;
+  int32_t* ea_list = nullptr;
+  std::vector<int32_t> ea_maxr;
+  void* arena = nullptr;
+  void* updv = nullptr;
+  void* w = nullptr;
+  double* rownorm = nullptr;
+  long long* derr = nullptr;
+  long long* herr = nullptr;  // pinned
+  // R~
+  int32_t *rt_rowptr = nullptr, *rt_col = nullptr, *rt_rhscol = nullptr, *rt_rownew = nullptr;
+  int64_t* rt_src = nullptr;
+  double* rt_val = nullptr;
+  int64_t nrt = 0;
+  // reduced system
+  int64_t* c = nullptr;
+  int32_t *c_rownew = nullptr, *qblock = nullptr, *gcols = nullptr;
+  int64_t *gq0 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr, *block_ncols = nullptr;
+  void* ghat = nullptr;
+  // spike panels
+  void* X = nullptr;
+  void* U = nullptr;
+  int32_t NR = 0;
+  // segments
+  SegView Sn{}, Sm{};
+  int32_t nseg = 0;
+  // outer workspace (FP64, n)
+  double *o_r = nullptr, *o_rhat = nullptr, *o_p = nullptr, *o_v = nullptr, *o_phat = nullptr,
+         *o_s = nullptr, *o_shat = nullptr, *o_t = nullptr, *o_xt = nullptr, *o_tmp = nullptr;
+  // preconditioner workspace
+  double *pc_g = nullptr, *pc_ghat = nullptr, *pc_zhat = nullptr, *pc_t = nullptr;
+  // host-buffer entry points stage f and x here
+  double *io_f = nullptr, *io_x = nullptr;
+  // inner workspace (inner precision, m)
+  void *i_g = nullptr, *i_z = nullptr, *i_r = nullptr, *i_rh = nullptr, *i_p = nullptr,
+       *i_v = nullptr, *i_s = nullptr, *i_t = nullptr;
+  KScal *sc_out = nullptr, *sc_in = nullptr;
+  KScal* hsc = nullptr;      // pinned host scalars of the loop being run (nseg)
+  KScal* hsc_out = nullptr;  // pinned, outer loop
+  KScal* hsc_in = nullptr;   // pinned, inner loop
+  double* partial = nullptr;
+  // guess and first reduced solution
+  double* guess = nullptr;
+  bool has_guess = false;
+  double *first_zhat = nullptr, *first_ghat = nullptr;
+  bool factored = false;
+  // statistics of the current solve
+  int64_t stat_inner = 0, stat_precond = 0;
+  double stat_first_inner = 0;
+  bool stat_guess_used = false;
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(ddps_handle* h, int64_t count) {
+  if (count <= 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{e == cudaErrorMemoryAllocation ? DDPS_ERR_OUT_OF_MEMORY : DDPS_ERR_CUDA,
+               "cudaMalloc of " + std::to_string((long long)count * sizeof(T)) +
+                   " bytes: " + cudaGetErrorString(e)};
+  }
+  h->allocs.push_back(p);
+  h->bytes += count * (int64_t)sizeof(T);
+  return (T*)p;
+}
+
+void* dalloc_bytes(ddps_handle* h, int64_t bytes) { return (void*)dalloc<unsigned char>(h, bytes); }
+
+template <typename T>
+T* dupload(ddps_handle* h, const std::vector<T>& v) {
+  T* p = dalloc<T>(h, (int64_t)v.size());
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+
+// Chunk table of a segmented vector.
+SegView make_segview(ddps_handle* h, const std::vector<int64_t>& seg_ptr) {
+  const int64_t CH = 8192;
+  std::vector<int64_t> cb, ce;
+  std::vector<int32_t> cs, scp;
+  const int nseg = (int)seg_ptr.size() - 1;
+  scp.push_back(0);
+  for (int s = 0; s < nseg; ++s) {
+    for (int64_t b = seg_ptr[s]; b < seg_ptr[s + 1]; b += CH) {
+      cb.push_back(b);
+      ce.push_back(std::min(b + CH, seg_ptr[s + 1]));
+      cs.push_back(s);
+    }
+    scp.push_back((int32_t)cb.size());
+  }
+  SegView S{};
+  S.chunk_beg = dupload(h, cb);
+  S.chunk_end = dupload(h, ce);
+  S.chunk_seg = dupload(h, cs);
+  S.seg_chunk_ptr = dupload(h, scp);
+  S.nchunks = (int32_t)cb.size();
+  S.nseg = nseg;
+  return S;
+}
+
+inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Fail{DDPS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+// ---------------------------------------------------------------------------
+// Fig. 2 steps 2 and 4 on the device
+// ---------------------------------------------------------------------------
+template <typename T, typename TG>
+void factor_impl(ddps_handle* h, cudaStream_t s) {
+  const Analysis& A = h->A;
+  T* arena = (T*)h->arena;
+  CK(cudaMemsetAsync(arena, 0, (size_t)A.arena_size * sizeof(T), s));
+  CK(cudaMemsetAsync(h->derr, 0, 3 * sizeof(long long), s));
+  launch_assemble<T>(h->vals, h->amap, A.nnz, arena, s);
+  launch_row_absmax(h->rowptr, h->amap, h->vals, h->iperm, A.n, h->rownorm, s);
+  h->launches += 2;
+  const int S = A.max_children;
+  for (int L = A.nlevels - 1; L >= 0; --L) {
+    for (int sl = 0; sl < S; ++sl) {
+      const int64_t q = (int64_t)L * S + sl;
+      const int32_t cnt = A.ea_ptr[q + 1] - A.ea_ptr[q];
+      if (cnt > 0) {
+        launch_extend_add_p<T>(h->F, h->parent, h->ea_list + A.ea_ptr[q], cnt, h->ea_maxr[q], arena, s);
+        h->launches++;
+      }
+    }
+    const int32_t nf = A.level_ptr[L + 1] - A.level_ptr[L];
+    launch_front_lu<T>(h->F, h->level_fronts + A.level_ptr[L], nf, arena, h->rownorm,
+                       h->opt.pivot_tol, h->derr, s);
+    h->launches++;
+  }
+  launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
+  h->launches++;
+  const int64_t m = (int64_t)A.c.size();
+  if (m > 0) {
+    T* X = (T*)h->X;
+    T* U = (T*)h->U;
+    const int32_t NR = h->NR;
+    for (int64_t j0 = 0; j0 < A.max_rhs; j0 += NR) {
+      CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
+      launch_spike_rhs<T>(h->rt_rownew, h->rt_rhscol, h->rt_src, h->nrt, h->vals, j0, NR, X, s);
+      h->launches++;
+      for (int L = A.nlevels - 1; L >= 0; --L) {
+        launch_fwd_multi<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                            arena, h->block_ncols, j0, NR, X, U, s);
+        h->launches++;
+      }
+      for (int L = 0; L < A.nlevels; ++L) {
+        launch_bwd_multi<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                            arena, h->block_ncols, j0, NR, X, s);
+        h->launches++;
+      }
+      launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, m, j0, NR,
+                                 X, (TG*)h->ghat, s);
+      h->launches++;
+    }
+  }
+  check_launch();
+  CK(cudaMemcpyAsync(h->herr, h->derr, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h->herr[0] != 0) {
+    const int64_t row_new = h->herr[2];
+    const int64_t row_old = h->A.perm[row_new];
+    const int32_t b = h->A.f_block[h->herr[1]];
+    throw Fail{DDPS_ERR_SINGULAR_BLOCK,
+               "pivot below threshold in diagonal block " + std::to_string(b) + " at row " +
+                   std::to_string((long long)row_old)};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fig. 3 step 6.1 (and the second block solve of the retrieval)
+// ---------------------------------------------------------------------------
+template <typename T>
+void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
+  const Analysis& A = h->A;
+  T* w = (T*)h->w;
+  T* u = (T*)h->updv;
+  const T* arena = (const T*)h->arena;
+  launch_permute_in<T>(y, h->perm, A.n, w, s);
+  for (int L = A.nlevels - 1; L >= 0; --L)
+    launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                   (int32_t)A.max_front, arena, w, u, s);
+  for (int L = 0; L < A.nlevels; ++L)
+    launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                   (int32_t)A.max_front, arena, w, s);
+  launch_permute_out<T>(w, h->perm, A.n, g, s);
+  h->launches += 2 + 2 * A.nlevels;
+}
+
+void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
+  if (h->opt.factor_prec == DDPS_FP64)
+    block_solve_impl<double>(h, y, g, s);
+  else
+    block_solve_impl<float>(h, y, g, s);
+}
+
+template <typename TG, typename TI>
+void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
+  launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
+                             h->gcols, (int64_t)h->A.c.size(), v, w, s);
+  h->launches++;
+}
+
+void download_sc(ddps_handle* h, const KScal* d, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->hsc, d, sizeof(KScal) * h->nseg, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+void upload_sc(ddps_handle* h, KScal* d, cudaStream_t s) {
+  CK(cudaMemcpyAsync(d, h->hsc, sizeof(KScal) * h->nseg, cudaMemcpyHostToDevice, s));
+}
+
+RedSpec red(const void* x, const void* y, int op, double* out) { return RedSpec{x, y, op, kScalStride, out}; }
+RedSpec nored() { return RedSpec{nullptr, nullptr, 0, 0, nullptr}; }
+
+// ---------------------------------------------------------------------------
+// Fig. 3 step 6.3: unpreconditioned BiCGStab on G^ z^ = g^, per system,
+// stopping on ||g^ - G^ z^||_2 <= tol_in ||g^||_2 or maxit_in iterations.
+// Returns the largest iteration count over the systems (half steps 0.5).
+// ---------------------------------------------------------------------------
+template <typename TG, typename TI>
+double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const double* z0,
+                   cudaStream_t s) {
+  const int64_t m = (int64_t)h->A.c.size();
+  const SegView& S = h->Sm;
+  const int ns = h->nseg;
+  KScal* sc = h->sc_in;
+  struct HostScalars {  // the inner loop keeps its own pinned scalars
+    ddps_handle* h;
+    KScal* saved;
+    explicit HostScalars(ddps_handle* hh) : h(hh), saved(hh->hsc) { h->hsc = h->hsc_in; }
+    ~HostScalars() { h->hsc = saved; }
+  } host_scalars(h);
+  TI *g = (TI*)h->i_g, *z = (TI*)h->i_z, *r = (TI*)h->i_r, *rh = (TI*)h->i_rh, *p = (TI*)h->i_p,
+     *v = (TI*)h->i_v, *sv = (TI*)h->i_s, *t = (TI*)h->i_t;
+  convert<TI, double>(m, ghat64, g, s);
+  CK(cudaMemsetAsync(z, 0, m * sizeof(TI), s));
+  CK(cudaMemsetAsync(p, 0, m * sizeof(TI), s));
+  CK(cudaMemsetAsync(v, 0, m * sizeof(TI), s));
+  CK(cudaMemsetAsync(sc, 0, ns * sizeof(KScal), s));
+  seg_reduce<TI>(S, 1, red(g, nullptr, 1, &sc[0].ref), nored(), nored(), h->partial, s);
+  CK(cudaMemcpyAsync(r, g, m * sizeof(TI), cudaMemcpyDeviceToDevice, s));
+  h->launches += 3;
+  download_sc(h, sc, s);
+  const double tol = h->opt.tol_in;
+  std::vector<double> iters(ns, 0.0);
+  for (int q = 0; q < ns; ++q) {
+    KScal& k = h->hsc[q];
+    k.active = k.ref > 0.0;
+    k.flag = 0;
+    k.half_done = 0;
+    k.rho_old = k.alpha = k.omega = 1.0;
+  }
+  upload_sc(h, sc, s);
+  if (z0) {
+    convert<TI, double>(m, z0, z, s);
+    ghat_matvec<TG, TI>(h, z, v, s);
+    vec_sub<TI>(S, sc, 1, g, v, r, s);
+    seg_reduce<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial, s);
+    h->launches += 4;
+    download_sc(h, sc, s);
+    bool any_reject = false;
+    for (int q = 0; q < ns; ++q) {
+      KScal& k = h->hsc[q];
+      k.flag = 0;
+      if (!k.active) continue;
+      if (!(k.nrm < k.ref)) {
+        k.flag = 1;  // the guess is worse than zero: start this system from zero
+        any_reject = true;
+      } else {
+        h->stat_guess_used = true;
+        if (k.nrm <= tol * k.ref) k.active = 0;
+      }
+    }
+    upload_sc(h, sc, s);
+    if (any_reject) {
+      masked_zero<TI>(S, sc, z, s);
+      masked_axpy<TI>(S, sc, r, g, nullptr, s);
+      h->launches += 2;
+    }
+    for (int q = 0; q < ns; ++q) h->hsc[q].flag = 0;
+    upload_sc(h, sc, s);
+    CK(cudaMemsetAsync(v, 0, m * sizeof(TI), s));
+  }
+  CK(cudaMemcpyAsync(rh, r, m * sizeof(TI), cudaMemcpyDeviceToDevice, s));
+  for (int it = 1; it <= h->opt.maxit_in; ++it) {
+    bool any = false;
+    for (int q = 0; q < ns; ++q) any |= h->hsc[q].active != 0;
+    if (!any) break;
+    seg_reduce<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, s);
+    sc_beta(ns, sc, it == 1, s);
+    update_p<TI>(S, sc, r, p, v, s);
+    ghat_matvec<TG, TI>(h, p, v, s);
+    seg_reduce<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial, s);
+    sc_alpha(ns, sc, s);
+    update_s<TI>(S, sc, r, v, sv, s);
+    seg_reduce<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial, s);
+    h->launches += 10;
+    download_sc(h, sc, s);
+    bool half_any = false;
+    for (int q = 0; q < ns; ++q) {
+      KScal& k = h->hsc[q];
+      if (!k.active) continue;
+      if (k.nrm <= tol * k.ref) {
+        k.half_done = 1;
+        k.active = 0;
+        iters[q] = it - 0.5;
+        half_any = true;
+      } else if (k.breakdown) {
+        k.active = 0;
+        iters[q] = it;
+      }
+    }
+    upload_sc(h, sc, s);
+    if (half_any) {
+      update_xr<TI>(S, sc, 1, z, p, nullptr, nullptr, nullptr, nullptr, s);
+      h->launches++;
+      for (int q = 0; q < ns; ++q) h->hsc[q].half_done = 0;
+      upload_sc(h, sc, s);
+    }
+    any = false;
+    for (int q = 0; q < ns; ++q) any |= h->hsc[q].active != 0;
+    if (!any) break;
+    ghat_matvec<TG, TI>(h, sv, t, s);
+    seg_reduce<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(), h->partial, s);
+    sc_omega(ns, sc, s);
+    update_xr<TI>(S, sc, 0, z, p, sv, r, sv, t, s);
+    seg_reduce<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial, s);
+    h->launches += 7;
+    download_sc(h, sc, s);
+    for (int q = 0; q < ns; ++q) {
+      KScal& k = h->hsc[q];
+      if (!k.active) continue;
+      iters[q] = it;
+      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown) k.active = 0;
+    }
+    upload_sc(h, sc, s);
+  }
+  convert<double, TI>(m, z, zhat64, s);
+  h->launches++;
+  double mx = 0;
+  for (double v2 : iters) mx = std::max(mx, v2);
+  for (int q = 0; q < ns; ++q)
+    if (h->hsc[q].active) mx = std::max(mx, (double)h->opt.maxit_in);
+  return mx;
+}
+
+double inner_dispatch(ddps_handle* h, const double* ghat64, double* zhat64, const double* z0,
+                      cudaStream_t s) {
+  const int gp = h->opt.ghat_prec, ip = h->opt.inner_prec;
+  if (gp == DDPS_FP64) return inner_solve<double, double>(h, ghat64, zhat64, z0, s);
+  if (gp == DDPS_FP32)
+    return ip == DDPS_FP64 ? inner_solve<float, double>(h, ghat64, zhat64, z0, s)
+                           : inner_solve<float, float>(h, ghat64, zhat64, z0, s);
+  return ip == DDPS_FP64 ? inner_solve<__nv_bfloat16, double>(h, ghat64, zhat64, z0, s)
+                         : inner_solve<__nv_bfloat16, float>(h, ghat64, zhat64, z0, s);
+}
+
+// Fig. 3: z = P^-1 y.
+void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, bool first) {
+  const int64_t m = (int64_t)h->A.c.size();
+  block_solve(h, y, h->pc_g, s);                                        // 6.1
+  if (m == 0) {
+    CK(cudaMemcpyAsync(z, h->pc_g, h->A.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    h->stat_precond++;
+    return;
+  }
+  launch_gather(h->pc_g, h->c, m, h->pc_ghat, s);                        // 6.2
+  h->launches++;
+  const double* z0 = (first && h->has_guess) ? h->guess : nullptr;
+  const double its = inner_dispatch(h, h->pc_ghat, h->pc_zhat, z0, s);  // 6.3
+  h->stat_inner += (int64_t)std::ceil(its);
+  if (first) {
+    h->stat_first_inner = its;
+    CK(cudaMemcpyAsync(h->first_zhat, h->pc_zhat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->first_ghat, h->pc_ghat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  // 6.4-6.5: z = g - G(:,c) z^ = D~^-1 (y - R~ z^)
+  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s);
+  h->launches++;
+  block_solve(h, h->pc_t, z, s);
+  h->stat_precond++;
+}
+
+// ---------------------------------------------------------------------------
+// Fig. 2 step 6: right-preconditioned BiCGStab on A x = f (FP64), per system,
+// convergence on the recomputed true residual ||f - A x||_inf <= tol ||f||_inf.
+// ---------------------------------------------------------------------------
+ddps_status solve_impl(ddps_handle* h, const double* f, double* x, cudaStream_t s,
+                       ddps_solve_info* info) {
+  const Analysis& A = h->A;
+  const int64_t n = A.n;
+  const SegView& S = h->Sn;
+  const int ns = h->nseg;
+  KScal* sc = h->sc_out;
+  auto spmv = [&](const double* in, double* out) {
+    launch_spmv(h->rowptr, h->colind, h->vals, n, in, out, s);
+    h->launches++;
+  };
+  h->stat_inner = 0;
+  h->stat_precond = 0;
+  h->stat_first_inner = 0;
+  h->stat_guess_used = false;
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CK(cudaMemsetAsync(h->o_p, 0, n * sizeof(double), s));
+  CK(cudaMemsetAsync(h->o_v, 0, n * sizeof(double), s));
+  CK(cudaMemsetAsync(sc, 0, ns * sizeof(KScal), s));
+  CK(cudaMemcpyAsync(h->o_r, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->o_rhat, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  seg_reduce<double>(S, 1, red(f, nullptr, 2, &sc[0].ref), nored(), nored(), h->partial, s);
+  h->launches += 2;
+  download_sc(h, sc, s);
+  const double tol = h->opt.tol_out;
+  std::vector<double> iters(ns, 0.0);
+  std::vector<int> conv(ns, 0);
+  for (int q = 0; q < ns; ++q) {
+    KScal& k = h->hsc[q];
+    k.active = k.ref > 0.0;
+    conv[q] = !k.active;
+    k.rho_old = k.alpha = k.omega = 1.0;
+  }
+  upload_sc(h, sc, s);
+  auto any_active = [&]() {
+    for (int q = 0; q < ns; ++q)
+      if (h->hsc[q].active) return true;
+    return false;
+  };
+  bool first = true;
+  for (int it = 1; it <= h->opt.maxit_out && any_active(); ++it) {
+    seg_reduce<double>(S, 1, red(h->o_rhat, h->o_r, 0, &sc[0].rho), nored(), nored(), h->partial, s);
+    sc_beta(ns, sc, it == 1, s);
+    update_p<double>(S, sc, h->o_r, h->o_p, h->o_v, s);
+    h->launches += 4;
+    precond_apply(h, h->o_p, h->o_phat, s, first);
+    first = false;
+    spmv(h->o_phat, h->o_v);
+    seg_reduce<double>(S, 1, red(h->o_rhat, h->o_v, 0, &sc[0].sigma), nored(), nored(), h->partial, s);
+    sc_alpha(ns, sc, s);
+    update_s<double>(S, sc, h->o_r, h->o_v, h->o_s, s);
+    seg_reduce<double>(S, 1, red(h->o_s, nullptr, 2, &sc[0].nrm), nored(), nored(), h->partial, s);
+    h->launches += 6;
+    download_sc(h, sc, s);
+    bool cand = false;
+    for (int q = 0; q < ns; ++q) {
+      KScal& k = h->hsc[q];
+      k.flag = k.active && k.nrm <= tol * k.ref;
+      cand |= k.flag != 0;
+    }
+    if (cand) {
+      upload_sc(h, sc, s);
+      masked_axpy<double>(S, sc, h->o_xt, x, h->o_phat, s);  // x + alpha phat
+      spmv(h->o_xt, h->o_tmp);
+      vec_sub<double>(S, sc, 1, f, h->o_tmp, h->o_tmp, s);
+      seg_reduce<double>(S, 1, red(h->o_tmp, nullptr, 2, &sc[0].nrm2), nored(), nored(), h->partial, s);
+      h->launches += 5;
+      download_sc(h, sc, s);
+      for (int q = 0; q < ns; ++q) {
+        KScal& k = h->hsc[q];
+        if (!k.flag) continue;
+        if (k.nrm2 <= tol * k.ref) {
+          k.active = 0;
+          conv[q] = 1;
+          iters[q] = it - 0.5;
+        } else {
+          k.flag = 0;
+        }
+      }
+      upload_sc(h, sc, s);
+      masked_axpy<double>(S, sc, x, h->o_xt, nullptr, s);
+      h->launches++;
+      for (int q = 0; q < ns; ++q) h->hsc[q].flag = 0;
+      upload_sc(h, sc, s);
+    }
+    if (!any_active()) break;
+    precond_apply(h, h->o_s, h->o_shat, s, false);
+    spmv(h->o_shat, h->o_t);
+    seg_reduce<double>(S, 2, red(h->o_t, h->o_s, 0, &sc[0].ts), red(h->o_t, h->o_t, 0, &sc[0].tt),
+                       nored(), h->partial, s);
+    sc_omega(ns, sc, s);
+    update_xr<double>(S, sc, 0, x, h->o_phat, h->o_shat, h->o_r, h->o_s, h->o_t, s);
+    seg_reduce<double>(S, 1, red(h->o_r, nullptr, 2, &sc[0].nrm), nored(), nored(), h->partial, s);
+    h->launches += 6;
+    download_sc(h, sc, s);
+    cand = false;
+    for (int q = 0; q < ns; ++q) {
+      KScal& k = h->hsc[q];
+      if (!k.active) continue;
+      iters[q] = it;
+      k.flag = k.nrm <= tol * k.ref;
+      cand |= k.flag != 0;
+      if (!k.flag && (k.omega == 0.0 || k.breakdown)) k.active = 0;  // breakdown: stop unconverged
+    }
+    if (cand) {
+      upload_sc(h, sc, s);
+      spmv(x, h->o_tmp);
+      vec_sub<double>(S, sc, 1, f, h->o_tmp, h->o_tmp, s);
+      seg_reduce<double>(S, 1, red(h->o_tmp, nullptr, 2, &sc[0].nrm2), nored(), nored(), h->partial, s);
+      h->launches += 3;
+      download_sc(h, sc, s);
+      for (int q = 0; q < ns; ++q) {
+        KScal& k = h->hsc[q];
+        if (!k.flag) continue;
+        if (k.nrm2 <= tol * k.ref) {
+          k.active = 0;
+          conv[q] = 1;
+          k.flag = 0;
+        }  // else keep flag: replace the recurrence residual by the true one
+      }
+      upload_sc(h, sc, s);
+      masked_axpy<double>(S, sc, h->o_r, h->o_tmp, nullptr, s);
+      h->launches++;
+      for (int q = 0; q < ns; ++q) h->hsc[q].flag = 0;
+    }
+    upload_sc(h, sc, s);
+  }
+  // final true residual of every system
+  spmv(x, h->o_tmp);
+  vec_sub<double>(S, sc, 1, f, h->o_tmp, h->o_tmp, s);
+  seg_reduce<double>(S, 1, red(h->o_tmp, nullptr, 2, &sc[0].nrm2), nored(), nored(), h->partial, s);
+  h->launches += 2;
+  download_sc(h, sc, s);
+  check_launch();
+  bool all = true;
+  double worst = 0, maxit = 0;
+  for (int q = 0; q < ns; ++q) {
+    const KScal& k = h->hsc[q];
+    const double rr = k.ref > 0 ? k.nrm2 / k.ref : 0.0;
+    worst = std::max(worst, rr);
+    maxit = std::max(maxit, iters[q]);
+    if (!conv[q] && !(rr <= tol)) all = false;
+  }
+  if (info) {
+    info->outer_iterations = maxit;
+    info->inner_iterations = (int32_t)h->stat_inner;
+    info->precond_applies = (int32_t)h->stat_precond;
+    info->converged = all ? 1 : 0;
+    info->guess_used = h->stat_guess_used ? 1 : 0;
+    info->relres_inf = worst;
+    info->first_inner_iters = h->stat_first_inner;
+  }
+  if (!all) {
+    h->err = "outer BiCGStab did not reach tol_out within maxit_out (worst relative residual " +
+             std::to_string(worst) + ")";
+    return DDPS_ERR_NOT_CONVERGED;
+  }
+  return DDPS_OK;
+}
+
+ddps_status fail(ddps_handle* h, const Fail& e) {
+  if (h) h->err = e.msg;
+  g_last_error = e.msg;
+  return e.st;
+}
+
+void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) {
+  Analysis& A = h->A;
+  const int64_t n = A.n, m = (int64_t)A.c.size();
+  h->rowptr = dupload(h, std::vector<int32_t>(rowptr, rowptr + n + 1));
+  h->colind = dupload(h, std::vector<int32_t>(colind, colind + A.nnz));
+  h->vals = dalloc<double>(h, A.nnz);
+  h->amap = dupload(h, A.amap);
+  h->perm = dupload(h, A.perm);
+  h->iperm = dupload(h, A.iperm);
+  DevFronts F{};
+  F.k = dupload(h, A.f_k);
+  F.m = dupload(h, A.f_m);
+  F.block = dupload(h, A.f_block);
+  F.row0 = dupload(h, A.f_row0);
+  F.arena = dupload(h, A.f_arena);
+  F.idx_off = dupload(h, A.f_idx);
+  F.upd = dupload(h, A.f_upd);
+  F.rel_off = dupload(h, A.f_rel);
+  F.cbeg = dupload(h, A.f_cbeg);
+  F.cend = dupload(h, A.f_cend);
+  F.children = dupload(h, A.children);
+  F.idx = dupload(h, A.idx);
+  F.rel = dupload(h, A.rel);
+  h->F = F;
+  h->parent = dupload(h, A.f_parent);
+  h->level_fronts = dupload(h, A.level_fronts);
+  h->ea_list = dupload(h, A.ea_list);
+  // largest update block per extend-add launch
+  const int S = A.max_children;
+  h->ea_maxr.assign((size_t)A.nlevels * S, 0);
+  for (size_t q = 0; q + 1 < A.ea_ptr.size(); ++q)
+    for (int32_t i = A.ea_ptr[q]; i < A.ea_ptr[q + 1]; ++i) {
+      const int32_t c = A.ea_list[i];
+      h->ea_maxr[q] = std::max(h->ea_maxr[q], A.f_m[c] - A.f_k[c]);
+    }
+  const size_t fs = prec_size(h->opt.factor_prec);
+  h->arena = dalloc_bytes(h, A.arena_size * (int64_t)fs);
+  h->updv = dalloc_bytes(h, std::max<int64_t>(A.upd_size, 1) * (int64_t)fs);
+  h->w = dalloc_bytes(h, n * (int64_t)fs);
+  h->rownorm = dalloc<double>(h, n);
+  h->derr = dalloc<long long>(h, 3);
+  CK(cudaMallocHost((void**)&h->herr, 3 * sizeof(long long)));
+  // R~
+  h->nrt = (int64_t)A.rt_col.size();
+  h->rt_rowptr = dupload(h, A.rt_rowptr);
+  h->rt_col = dupload(h, A.rt_col);
+  h->rt_rhscol = dupload(h, A.rt_rhscol);
+  h->rt_rownew = dupload(h, A.rt_rownew);
+  h->rt_src = dupload(h, A.rt_src);
+  h->rt_val = dalloc<double>(h, h->nrt);
+  // reduced system
+  h->c = dupload(h, A.c);
+  h->c_rownew = dupload(h, A.c_rownew);
+  std::vector<int32_t> qblock(m);
+  std::vector<int64_t> ncols(A.p);
+  for (int32_t b = 0; b < A.p; ++b) {
+    for (int64_t q = A.gq0[b]; q < A.gq1[b]; ++q) qblock[q] = b;
+    ncols[b] = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
+  }
+  h->qblock = dupload(h, qblock);
+  h->gq0 = dupload(h, A.gq0);
+  h->gcol_ptr = dupload(h, A.gcol_ptr);
+  h->ghat_off = dupload(h, A.ghat_off);
+  h->gcols = dupload(h, A.gcols);
+  h->block_ncols = dupload(h, ncols);
+  h->ghat = dalloc_bytes(h, std::max<int64_t>(A.ghat_entries, 1) * (int64_t)prec_size(h->opt.ghat_prec));
+  // spike panels: NR right-hand sides per pass
+  if (m > 0) {
+    int64_t nr = h->opt.rhs_chunk > 0 ? h->opt.rhs_chunk : 1024;
+    nr = std::min<int64_t>(nr, ((A.max_rhs + 31) / 32) * 32);
+    const int64_t budget = (int64_t)12 << 30;  // bytes for the two panels
+    while (nr > 32 && (n + A.upd_size) * nr * (int64_t)fs > budget) nr /= 2;
+    h->NR = (int32_t)std::max<int64_t>(32, (nr / 32) * 32);
+    h->X = dalloc_bytes(h, n * h->NR * (int64_t)fs);
+    h->U = dalloc_bytes(h, std::max<int64_t>(A.upd_size, 1) * h->NR * (int64_t)fs);
+  }
+  // segments
+  h->nseg = A.nsys;
+  h->Sn = make_segview(h, A.sys_row_ptr);
+  h->Sm = make_segview(h, A.sys_c_ptr);
+  // workspaces
+  double** outer[] = {&h->o_r, &h->o_rhat, &h->o_p, &h->o_v, &h->o_phat, &h->o_s,
+                      &h->o_shat, &h->o_t, &h->o_xt, &h->o_tmp, &h->pc_g, &h->pc_t,
+                      &h->io_f, &h->io_x};
+  for (double** pp : outer) *pp = dalloc<double>(h, n);
+  h->pc_ghat = dalloc<double>(h, m);
+  h->pc_zhat = dalloc<double>(h, m);
+  h->first_zhat = dalloc<double>(h, m);
+  h->first_ghat = dalloc<double>(h, m);
+  h->guess = dalloc<double>(h, m);
+  const size_t is = prec_size(h->opt.inner_prec);
+  void** inner[] = {&h->i_g, &h->i_z, &h->i_r, &h->i_rh, &h->i_p, &h->i_v, &h->i_s, &h->i_t};
+  for (void** pp : inner) *pp = dalloc_bytes(h, std::max<int64_t>(m, 1) * (int64_t)is);
+  h->sc_out = dalloc<KScal>(h, h->nseg);
+  h->sc_in = dalloc<KScal>(h, h->nseg);
+  CK(cudaMallocHost((void**)&h->hsc_out, sizeof(KScal) * h->nseg));
+  CK(cudaMallocHost((void**)&h->hsc_in, sizeof(KScal) * h->nseg));
+  h->hsc = h->hsc_out;
+  h->partial = dalloc<double>(h, 3 * (int64_t)std::max(h->Sn.nchunks, h->Sm.nchunks) + 3);
+}
+
+bool valid_options(const ddps_options& o, std::string& why) {
+  if (o.factor_prec != DDPS_FP64 && o.factor_prec != DDPS_FP32) {
+    why = "factor_prec must be FP64 or FP32";
+    return false;
+  }
+  if (o.ghat_prec < DDPS_FP64 || o.ghat_prec > DDPS_BF16) {
+    why = "ghat_prec must be FP64, FP32 or BF16";
+    return false;
+  }
+  if (o.inner_prec != DDPS_FP64 && o.inner_prec != DDPS_FP32) {
+    why = "inner_prec must be FP64 or FP32";
+    return false;
+  }
+  if (o.ghat_prec == DDPS_FP64 && o.inner_prec != DDPS_FP64) {
+    why = "an FP64 G^ needs FP64 inner vectors";
+    return false;
+  }
+  if (o.spike_prec != o.factor_prec) {
+    why = "spike_prec must equal factor_prec (the spike panel is solved with the block factors)";
+    return false;
+  }
+  if (o.factor_prec == DDPS_FP32 && o.ghat_prec == DDPS_FP64) {
+    why = "an FP64 G^ cannot be formed from FP32 factors";
+    return false;
+  }
+  if (!(o.tol_out > 0) || !(o.tol_in > 0) || o.maxit_out < 1 || o.maxit_in < 1 || o.pivot_tol < 0) {
+    why = "tolerances must be positive and iteration caps at least 1";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+// ABI
+// ===========================================================================
+extern "C" {
+
+void ddps_default_options(ddps_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->drop_mode = DDPS_DROP_NONE;
+  o->drop_tol = 0.0;
+  o->factor_prec = DDPS_FP64;
+  o->spike_prec = DDPS_FP64;
+  o->ghat_prec = DDPS_FP64;
+  o->inner_prec = DDPS_FP64;
+  o->tol_out = 1e-10;
+  o->maxit_out = 1000;
+  o->tol_in = 1e-4;
+  o->maxit_in = 100;
+  o->pivot_tol = 1e-14;
+  o->leaf_size = 0;
+  o->rhs_chunk = 0;
+  o->verbose = 0;
+}
+
+ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                         int32_t p, const int64_t* block_ptr, int32_t nsys,
+                         const int32_t* sys_block_ptr, const double* values,
+                         const ddps_options* opt, ddps_handle** out) {
+  if (!out) {
+    g_last_error = "ddps_analyze: out is NULL";
+    return DDPS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  ddps_handle* h = new (std::nothrow) ddps_handle();
+  if (!h) {
+    g_last_error = "ddps_analyze: host allocation failed";
+    return DDPS_ERR_OUT_OF_MEMORY;
+  }
+  try {
+    if (opt)
+      h->opt = *opt;
+    else
+      ddps_default_options(&h->opt);
+    std::string why;
+    if (!valid_options(h->opt, why)) throw Fail{DDPS_ERR_INVALID_ARG, "ddps_analyze: " + why};
+    std::string e = analyze(n, nnz, rowptr, colind, p, block_ptr, nsys, sys_block_ptr, values,
+                            h->opt, h->A);
+    if (!e.empty()) throw Fail{DDPS_ERR_INVALID_ARG, e};
+    build_device(h, rowptr, colind);
+    CK(cudaDeviceSynchronize());
+  } catch (const Fail& f) {
+    ddps_status st = fail(h, f);
+    ddps_destroy(h);
+    return st;
+  } catch (const std::exception& ex) {
+    g_last_error = std::string("ddps_analyze: ") + ex.what();
+    ddps_destroy(h);
+    return DDPS_ERR_INVALID_ARG;
+  }
+  *out = h;
+  return DDPS_OK;
+}
+
+ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream) {
+  if (!h || !values) return DDPS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  try {
+    h->factored = false;
+    CK(cudaMemcpyAsync(h->vals, values, h->A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int fp = h->opt.factor_prec, gp = h->opt.ghat_prec;
+    if (fp == DDPS_FP64) {
+      if (gp == DDPS_FP64)
+        factor_impl<double, double>(h, s);
+      else if (gp == DDPS_FP32)
+        factor_impl<double, float>(h, s);
+      else
+        factor_impl<double, __nv_bfloat16>(h, s);
+    } else {
+      if (gp == DDPS_FP32)
+        factor_impl<float, float>(h, s);
+      else
+        factor_impl<float, __nv_bfloat16>(h, s);
+    }
+    h->factored = true;
+  } catch (const Fail& f) {
+    return fail(h, f);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, void* stream,
+                       ddps_solve_info* info) {
+  if (!h || !f || !x) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) {
+    h->err = "ddps_solve: call ddps_factor first";
+    return DDPS_ERR_STATE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    ddps_status st = solve_impl(h, f, x, as_stream(stream), info);
+    if (info)
+      info->ms_solve =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+}
+
+ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, void* stream,
+                            ddps_solve_info* info) {
+  if (!h || !f_host || !x_host) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) {
+    h->err = "ddps_solve_host: call ddps_factor first";
+    return DDPS_ERR_STATE;
+  }
+  cudaStream_t s = as_stream(stream);
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    const size_t bytes = h->A.n * sizeof(double);
+    CK(cudaMemcpyAsync(h->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
+    ddps_status st = solve_impl(h, h->io_f, h->io_x, s, info);
+    CK(cudaMemcpyAsync(x_host, h->io_x, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info)
+      info->ms_solve =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+}
+
+ddps_status ddps_set_reduced_guess(ddps_handle* h, const double* zhat0, void* stream) {
+  if (!h) return DDPS_ERR_INVALID_ARG;
+  try {
+    if (!zhat0) {
+      h->has_guess = false;
+      return DDPS_OK;
+    }
+    const int64_t m = (int64_t)h->A.c.size();
+    if (m > 0)
+      CK(cudaMemcpyAsync(h->guess, zhat0, m * sizeof(double), cudaMemcpyDeviceToDevice,
+                         as_stream(stream)));
+    h->has_guess = m > 0;
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_reduced_solution(ddps_handle* h, double* zhat, double* ghat, void* stream) {
+  if (!h) return DDPS_ERR_INVALID_ARG;
+  try {
+    const int64_t m = (int64_t)h->A.c.size();
+    cudaStream_t s = as_stream(stream);
+    if (zhat && m) CK(cudaMemcpyAsync(zhat, h->first_zhat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (ghat && m) CK(cudaMemcpyAsync(ghat, h->first_ghat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* stream) {
+  if (!h || !y || !g) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    block_solve(h, y, g, as_stream(stream));
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream) {
+  if (!h || (!h->A.c.empty() && (!v || !w))) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    cudaStream_t s = as_stream(stream);
+    const int gp = h->opt.ghat_prec;
+    if (h->A.c.empty()) return DDPS_OK;
+    if (gp == DDPS_FP64)
+      ghat_matvec<double, double>(h, v, w, s);
+    else if (gp == DDPS_FP32)
+      ghat_matvec<float, double>(h, v, w, s);
+    else
+      ghat_matvec<__nv_bfloat16, double>(h, v, w, s);
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_precond_apply(ddps_handle* h, const double* y, double* z, void* stream) {
+  if (!h || !y || !z) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    h->stat_inner = 0;
+    precond_apply(h, y, z, as_stream(stream), false);
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_spmv(ddps_handle* h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    launch_spmv(h->rowptr, h->colind, h->vals, h->A.n, x, y, as_stream(stream));
+    h->launches++;
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_sizes(const ddps_handle* h, ddps_sizes* s) {
+  if (!h || !s) return DDPS_ERR_INVALID_ARG;
+  const Analysis& A = h->A;
+  s->n = A.n;
+  s->nnz = A.nnz;
+  s->nsys = A.nsys;
+  s->nblocks = A.p;
+  s->m = (int64_t)A.c.size();
+  s->nnz_rt = (int64_t)A.rt_col.size();
+  s->nfronts = (int64_t)A.f_k.size();
+  s->nlevels = A.nlevels;
+  s->factor_entries = A.arena_size;
+  s->factor_lu_entries = A.factor_lu_entries;
+  s->ghat_entries = A.ghat_entries;
+  s->max_front = A.max_front;
+  s->max_rhs = A.max_rhs;
+  s->device_bytes = h->bytes;
+  s->factor_flops = A.factor_flops;
+  s->spike_flops = A.spike_flops;
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_interface(const ddps_handle* h, int64_t* c) {
+  if (!h || (!c && !h->A.c.empty())) return DDPS_ERR_INVALID_ARG;
+  if (!h->A.c.empty()) std::memcpy(c, h->A.c.data(), h->A.c.size() * sizeof(int64_t));
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_ghat_layout(const ddps_handle* h, int32_t b, int64_t* q0, int64_t* q1,
+                                 int64_t* ncols, int64_t* cols) {
+  if (!h || b < 0 || b >= h->A.p) return DDPS_ERR_INVALID_ARG;
+  const Analysis& A = h->A;
+  if (q0) *q0 = A.gq0[b];
+  if (q1) *q1 = A.gq1[b];
+  const int64_t nc = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
+  if (ncols) *ncols = nc;
+  if (cols)
+    for (int64_t j = 0; j < nc; ++j) cols[j] = A.gcols[A.gcol_ptr[b] + j];
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* stream) {
+  if (!h || b < 0 || b >= h->A.p || !dst) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    const Analysis& A = h->A;
+    const int64_t cnt = A.ghat_off[b + 1] - A.ghat_off[b];
+    if (cnt == 0) return DDPS_OK;
+    cudaStream_t s = as_stream(stream);
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, cnt * sizeof(double)));
+    const int gp = h->opt.ghat_prec;
+    if (gp == DDPS_FP64)
+      CK(cudaMemcpyAsync(tmp, (const double*)h->ghat + A.ghat_off[b], cnt * sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+    else if (gp == DDPS_FP32)
+      convert<double, float>(cnt, (const float*)h->ghat + A.ghat_off[b], tmp, s);
+    else {
+      std::vector<uint16_t> raw(cnt);
+      CK(cudaMemcpyAsync(raw.data(), (const __nv_bfloat16*)h->ghat + A.ghat_off[b], cnt * 2,
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int64_t i = 0; i < cnt; ++i) {
+        uint32_t bits = (uint32_t)raw[i] << 16;
+        float fv;
+        std::memcpy(&fv, &bits, 4);
+        dst[i] = fv;
+      }
+      cudaFree(tmp);
+      return DDPS_OK;
+    }
+    CK(cudaMemcpyAsync(dst, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
+ddps_status ddps_destroy(ddps_handle* h) {
+  if (!h) return DDPS_OK;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->herr) cudaFreeHost(h->herr);
+  if (h->hsc_out) cudaFreeHost(h->hsc_out);
+  if (h->hsc_in) cudaFreeHost(h->hsc_in);
+  delete h;
+  return DDPS_OK;
+}
+
+const char* ddps_last_error(const ddps_handle* h) {
+  if (h) return h->err.c_str();
+  return g_last_error.c_str();
+}
+
+const char* ddps_status_string(ddps_status s) {
+  switch (s) {
+    case DDPS_OK: return "DDPS_OK";
+    case DDPS_ERR_INVALID_ARG: return "DDPS_ERR_INVALID_ARG";
+    case DDPS_ERR_SINGULAR_BLOCK: return "DDPS_ERR_SINGULAR_BLOCK";
+    case DDPS_ERR_NOT_CONVERGED: return "DDPS_ERR_NOT_CONVERGED";
+    case DDPS_ERR_OUT_OF_MEMORY: return "DDPS_ERR_OUT_OF_MEMORY";
+    case DDPS_ERR_CUDA: return "DDPS_ERR_CUDA";
+    case DDPS_ERR_TIMEOUT: return "DDPS_ERR_TIMEOUT";
+    case DDPS_ERR_STATE: return "DDPS_ERR_STATE";
+  }
+  return "unknown status";
+}
+
+int64_t ddps_launch_count(const ddps_handle* h) { return h ? h->launches : 0; }
+
+ddps_status ddps_symbolic(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                          int32_t p, const int64_t* block_ptr, int32_t nsys,
+                          const int32_t* sys_block_ptr, const double* values,
+                          const ddps_options* opt, ddps_sizes* sizes, int32_t* perm, int64_t* c) {
+  ddps_options o;
+  if (opt)
+    o = *opt;
+  else
+    ddps_default_options(&o);
+  Analysis A;
+  std::string e = analyze(n, nnz, rowptr, colind, p, block_ptr, nsys, sys_block_ptr, values, o, A);
+  if (!e.empty()) {
+    g_last_error = e;
+    return DDPS_ERR_INVALID_ARG;
+  }
+  if (sizes) {
+    std::memset(sizes, 0, sizeof(*sizes));
+    sizes->n = A.n;
+    sizes->nnz = A.nnz;
+    sizes->nsys = A.nsys;
+    sizes->nblocks = A.p;
+    sizes->m = (int64_t)A.c.size();
+    sizes->nnz_rt = (int64_t)A.rt_col.size();
+    sizes->nfronts = (int64_t)A.f_k.size();
+    sizes->nlevels = A.nlevels;
+    sizes->factor_entries = A.arena_size;
+    sizes->factor_lu_entries = A.factor_lu_entries;
+    sizes->ghat_entries = A.ghat_entries;
+    sizes->max_front = A.max_front;
+    sizes->max_rhs = A.max_rhs;
+    sizes->factor_flops = A.factor_flops;
+    sizes->spike_flops = A.spike_flops;
+  }
+  if (perm) std::memcpy(perm, A.perm.data(), n * sizeof(int32_t));
+  if (c && !A.c.empty()) std::memcpy(c, A.c.data(), A.c.size() * sizeof(int64_t));
+  return DDPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,445 @@
+// Numeric preprocessing of DDPS on the device: Fig. 2 step 2 (exact LU of
+// every diagonal block, here a multifrontal LU without pivoting over the
+// nested-dissection order) and Fig. 2 step 4 (spikes G = D~^-1 R~, keeping the
+// rows that lie in c, i.e. the off-identity part of G^ = I(c,c) + G(c,c),
+// stored as one dense row-major array per partition as Sec. 3 describes).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "launch.h"
+
+namespace ddps {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <typename T>
+__device__ __forceinline__ T from_double(double v) {
+  return (T)v;
+}
+
+// ---------------------------------------------------------------------------
+// Assembly of the original entries of every A_ii into its fronts.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_assemble(const double* __restrict__ values, const int64_t* __restrict__ amap,
+                           int64_t nnz, T* __restrict__ arena) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t dst = amap[e];
+    if (dst >= 0) arena[dst] = from_double<T>(values[e]);
+  }
+}
+
+// max |a_ij| over the D-part of each row, stored at the row's new index; the
+// pivot threshold of a front row is pivot_tol times this value.
+__global__ void k_row_absmax(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ amap,
+                             const double* __restrict__ values, const int32_t* __restrict__ iperm,
+                             int64_t n, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (amap[e] >= 0) mx = fmax(mx, fabs(values[e]));
+    out[iperm[i]] = mx;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Extend-add: parent front += child's Schur complement (its trailing r x r
+// block), one child per parent per launch so that no two writers meet.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_extend_add_p(DevFronts F, const int32_t* __restrict__ parent,
+                               const int32_t* __restrict__ child_list, T* __restrict__ arena) {
+  const int32_t c = child_list[blockIdx.x];
+  const int32_t kc = F.k[c], mc = F.m[c];
+  const int32_t r = mc - kc;
+  if (r <= 0) return;
+  const int32_t p = parent[c];
+  const int32_t mp = F.m[p];
+  const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
+  const T* __restrict__ C = arena + F.arena[c];
+  T* __restrict__ P = arena + F.arena[p];
+  const int64_t rr = (int64_t)r * r;
+  for (int64_t t = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; t < rr;
+       t += (int64_t)gridDim.y * blockDim.x) {
+    const int32_t i = (int32_t)(t % r), j = (int32_t)(t / r);
+    P[rel[i] + (int64_t)rel[j] * mp] += C[(kc + i) + (int64_t)(kc + j) * mc];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Partial LU of a front (no pivoting): the first k columns/rows become
+// L11\U11, L21 and U12; the trailing r x r block becomes the Schur complement
+// passed to the parent.  One CTA per front; blocked right-looking with panel
+// width NB and 64 x 64 shared-memory tiles for the trailing update.
+// ---------------------------------------------------------------------------
+constexpr int NB = 32;
+constexpr int TT = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_front_lu(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena,
+               const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  T* __restrict__ A = arena + F.arena[f];
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x;
+  __shared__ T Ls[NB][NB + 1];
+  __shared__ T Lt[TT][NB + 1];
+  __shared__ T Ut[NB][TT + 1];
+  for (int j0 = 0; j0 < k; j0 += NB) {
+    const int jb = min(NB, k - j0);
+    // (1) panel j0 .. j0+jb-1 over all rows below the diagonal
+    for (int j = j0; j < j0 + jb; ++j) {
+      T piv = A[j + (int64_t)j * m];
+      const double thr = pivot_tol * rownorm[row0 + j];
+      if (!(fabs((double)piv) > thr)) {
+        const double rep = thr > 0.0 ? thr : 1e-300;
+        piv = (T)((double)piv < 0.0 ? -rep : rep);
+        if (tid == 0) {
+          if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+            err[1] = f;
+            err[2] = row0 + j;
+          }
+          A[j + (int64_t)j * m] = piv;
+        }
+      }
+      const T inv = T(1) / piv;
+      for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
+      __syncthreads();
+      const int nr = m - (j + 1);
+      const int nc = j0 + jb - (j + 1);
+      for (int t = tid; t < nr * nc; t += blockDim.x) {
+        const int i = j + 1 + t % nr;
+        const int c = j + 1 + t / nr;
+        A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * A[j + (int64_t)c * m];
+      }
+      __syncthreads();
+    }
+    const int t0 = j0 + jb;
+    if (t0 >= m) break;
+    // (2) U12 = L11^-1 A12 for the columns right of the panel
+    for (int t = tid; t < jb * jb; t += blockDim.x) {
+      const int r = t % jb, q = t / jb;
+      Ls[r][q] = A[j0 + r + (int64_t)(j0 + q) * m];
+    }
+    __syncthreads();
+    for (int c = t0 + tid; c < m; c += blockDim.x) {
+      T x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+        T s = x[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) s -= Ls[r][q] * x[q];
+        x[r] = s;
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
+    }
+    __syncthreads();
+    // (3) trailing update A22 -= L21 U12 over TT x TT tiles
+    const int nt = m - t0;
+    const int ntiles = (nt + TT - 1) / TT;
+    for (int tile = 0; tile < ntiles * ntiles; ++tile) {
+      const int ti = tile % ntiles, tj = tile / ntiles;
+      const int rb = t0 + ti * TT, cb = t0 + tj * TT;
+      for (int t = tid; t < TT * NB; t += blockDim.x) {
+        const int r = t % TT, q = t / TT;
+        Lt[r][q] = (rb + r < m && q < jb) ? A[rb + r + (int64_t)(j0 + q) * m] : T(0);
+        const int q2 = t % NB, c2 = t / NB;
+        Ut[q2][c2] = (cb + c2 < m && q2 < jb) ? A[j0 + q2 + (int64_t)(cb + c2) * m] : T(0);
+      }
+      __syncthreads();
+      const int tr = tid % 16, tc = tid / 16;
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 8
+      for (int q = 0; q < NB; ++q) {
+        T lv[4], uv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = Lt[tr + 16 * a][q];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) uv[b] = Ut[q][tc + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = cb + tc + 16 * b;
+        if (c >= m) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = rb + tr + 16 * a;
+          if (r < m) A[r + (int64_t)c * m] -= acc[a][b];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spike right-hand sides: column j of block b's panel is R~_b(:, c_b[j]).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_spike_rhs(const int32_t* __restrict__ rt_rownew, const int32_t* __restrict__ rt_rhscol,
+                            const int64_t* __restrict__ rt_src, int64_t nrt,
+                            const double* __restrict__ values, int64_t j0, int32_t NR,
+                            T* __restrict__ X) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nrt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = rt_rhscol[e] - j0;
+    if (j >= 0 && j < NR) X[(int64_t)rt_rownew[e] * NR + j] = (T)values[rt_src[e]];
+  }
+}
+
+// Multi-RHS forward substitution, one front per CTA row, 32 panel columns per
+// CTA (one per lane); warps stride over front rows.  The panel holds the
+// right-hand sides on entry and L^-1 of them on the pivot rows on exit; the
+// front's update rows go to U for the parent to extend-add.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd_multi(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
+                const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR, T* __restrict__ X,
+                T* __restrict__ U) {
+  const int32_t f = list[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  const int64_t ncols = block_ncols[F.block[f]] - j0;
+  if ((int64_t)blockIdx.y * 32 >= ncols || blockIdx.y * 32 >= NR) return;
+  const bool act = col < NR && col < ncols;
+  const int32_t k = F.k[f], m = F.m[f], r = m - k;
+  const T* __restrict__ A = arena + F.arena[f];
+  T* __restrict__ Xf = X + F.row0[f] * NR;
+  T* __restrict__ Uf = U + F.upd[f] * NR;
+  for (int i = warp; i < r; i += nw)
+    if (act) Uf[(int64_t)i * NR + col] = T(0);
+  __syncthreads();
+  for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
+    const int32_t c = F.children[ci];
+    const int32_t rc = F.m[c] - F.k[c];
+    const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
+    const T* __restrict__ Uc = U + F.upd[c] * NR;
+    for (int i = warp; i < rc; i += nw) {
+      if (!act) continue;
+      const int32_t pr = rel[i];
+      const T v = Uc[(int64_t)i * NR + col];
+      if (pr < k)
+        Xf[(int64_t)pr * NR + col] += v;
+      else
+        Uf[(int64_t)(pr - k) * NR + col] += v;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < k; ++j) {
+    const T yj = act ? Xf[(int64_t)j * NR + col] : T(0);
+    const T* __restrict__ Lj = A + (int64_t)j * m;
+    for (int i = j + 1 + warp; i < m; i += nw) {
+      if (!act) continue;
+      const T l = Lj[i];
+      if (i < k)
+        Xf[(int64_t)i * NR + col] -= l * yj;
+      else
+        Uf[(int64_t)(i - k) * NR + col] -= l * yj;
+    }
+    __syncthreads();
+  }
+}
+
+// Multi-RHS backward substitution: x_piv = U11^-1 (y_piv - U12 x_upd), where
+// x_upd are final values of ancestor pivots, read from the panel.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_bwd_multi(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
+                const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR, T* __restrict__ X) {
+  const int32_t f = list[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  const int64_t ncols = block_ncols[F.block[f]] - j0;
+  if ((int64_t)blockIdx.y * 32 >= ncols || blockIdx.y * 32 >= NR) return;
+  const bool act = col < NR && col < ncols;
+  const int32_t k = F.k[f], m = F.m[f], r = m - k;
+  const T* __restrict__ A = arena + F.arena[f];
+  const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
+  T* __restrict__ Xf = X + F.row0[f] * NR;
+  if (act) {
+    for (int i = warp; i < k; i += nw) {
+      T acc = Xf[(int64_t)i * NR + col];
+      for (int j = 0; j < r; ++j) acc -= A[i + (int64_t)(k + j) * m] * X[(int64_t)idx[k + j] * NR + col];
+      Xf[(int64_t)i * NR + col] = acc;
+    }
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T* __restrict__ Uj = A + (int64_t)j * m;
+    const T xj = act ? Xf[(int64_t)j * NR + col] / Uj[j] : T(0);
+    __syncthreads();
+    if (act) {
+      if (warp == (j % nw)) Xf[(int64_t)j * NR + col] = xj;
+      for (int i = warp; i < j; i += nw) Xf[(int64_t)i * NR + col] -= Uj[i] * xj;
+    }
+    __syncthreads();
+  }
+}
+
+// G^ rows of every block from the solved panel, converted to the storage type.
+template <typename T, typename TG>
+__global__ void k_ghat_extract(const int32_t* __restrict__ qblock, const int32_t* __restrict__ c_rownew,
+                               const int64_t* __restrict__ gq0, const int64_t* __restrict__ gcol_ptr,
+                               const int64_t* __restrict__ ghat_off, int64_t m, int64_t j0, int32_t NR,
+                               const T* __restrict__ X, TG* __restrict__ ghat) {
+  const int64_t total = m * NR;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / NR;
+    const int32_t jj = (int32_t)(t % NR);
+    const int32_t b = qblock[q];
+    const int64_t ncol = gcol_ptr[b + 1] - gcol_ptr[b];
+    const int64_t j = j0 + jj;
+    if (j >= ncol) continue;
+    const T v = X[(int64_t)c_rownew[q] * NR + jj];
+    ghat[ghat_off[b] + (q - gq0[b]) * ncol + j] = (TG)(float)v;
+  }
+}
+
+template <>
+__global__ void k_ghat_extract<double, double>(const int32_t* __restrict__ qblock,
+                                               const int32_t* __restrict__ c_rownew,
+                                               const int64_t* __restrict__ gq0,
+                                               const int64_t* __restrict__ gcol_ptr,
+                                               const int64_t* __restrict__ ghat_off, int64_t m,
+                                               int64_t j0, int32_t NR, const double* __restrict__ X,
+                                               double* __restrict__ ghat) {
+  const int64_t total = m * NR;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / NR;
+    const int32_t jj = (int32_t)(t % NR);
+    const int32_t b = qblock[q];
+    const int64_t ncol = gcol_ptr[b + 1] - gcol_ptr[b];
+    const int64_t j = j0 + jj;
+    if (j >= ncol) continue;
+    ghat[ghat_off[b] + (q - gq0[b]) * ncol + j] = X[(int64_t)c_rownew[q] * NR + jj];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_assemble(const double* values, const int64_t* amap, int64_t nnz, T* arena,
+                     cudaStream_t s) {
+  k_assemble<T><<<grid_for(nnz, kThreads), kThreads, 0, s>>>(values, amap, nnz, arena);
+}
+
+void launch_row_absmax(const int32_t* rowptr, const int64_t* amap, const double* values,
+                       const int32_t* iperm, int64_t n, double* rownorm_new, cudaStream_t s) {
+  k_row_absmax<<<grid_for(n, kThreads), kThreads, 0, s>>>(rowptr, amap, values, iperm, n,
+                                                           rownorm_new);
+}
+
+template <typename T>
+void launch_extend_add_p(DevFronts F, const int32_t* parent, const int32_t* child_list,
+                         int32_t nchild, int32_t max_r, T* arena, cudaStream_t s) {
+  if (nchild <= 0) return;
+  int64_t per = (int64_t)max_r * max_r;
+  int gy = (int)std::min<int64_t>((per + kThreads - 1) / kThreads, 64);
+  if (gy < 1) gy = 1;
+  dim3 grid(nchild, gy);
+  k_extend_add_p<T><<<grid, kThreads, 0, s>>>(F, parent, child_list, arena);
+}
+
+template <typename T>
+void launch_front_lu(DevFronts F, const int32_t* list, int32_t nf, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
+  if (nf <= 0) return;
+  k_front_lu<T><<<nf, kThreads, 0, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
+}
+
+template <typename T>
+void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const int64_t* rt_src,
+                      int64_t nrt, const double* values, int64_t j0, int32_t NR, T* X,
+                      cudaStream_t s) {
+  if (nrt <= 0) return;
+  k_spike_rhs<T><<<grid_for(nrt, kThreads), kThreads, 0, s>>>(rt_rownew, rt_rhscol, rt_src, nrt,
+                                                               values, j0, NR, X);
+}
+
+template <typename T>
+void launch_fwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
+                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, T* U,
+                      cudaStream_t s) {
+  if (nf <= 0) return;
+  dim3 grid(nf, (NR + 31) / 32);
+  k_fwd_multi<T><<<grid, kThreads, 0, s>>>(F, list, arena, block_ncols, j0, NR, X, U);
+}
+
+template <typename T>
+void launch_bwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
+                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, cudaStream_t s) {
+  if (nf <= 0) return;
+  dim3 grid(nf, (NR + 31) / 32);
+  k_bwd_multi<T><<<grid, kThreads, 0, s>>>(F, list, arena, block_ncols, j0, NR, X);
+}
+
+template <typename T, typename TG>
+void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
+                         const int64_t* gcol_ptr, const int64_t* ghat_off, int64_t m, int64_t j0,
+                         int32_t NR, const T* X, TG* ghat, cudaStream_t s) {
+  if (m <= 0) return;
+  k_ghat_extract<T, TG><<<grid_for(m * NR, kThreads), kThreads, 0, s>>>(
+      qblock, c_rownew, gq0, gcol_ptr, ghat_off, m, j0, NR, X, ghat);
+}
+
+#define DDPS_INST_T(T)                                                                          \
+  template void launch_assemble<T>(const double*, const int64_t*, int64_t, T*, cudaStream_t);  \
+  template void launch_extend_add_p<T>(DevFronts, const int32_t*, const int32_t*, int32_t,     \
+                                       int32_t, T*, cudaStream_t);                             \
+  template void launch_front_lu<T>(DevFronts, const int32_t*, int32_t, T*, const double*,      \
+                                   double, long long*, cudaStream_t);                          \
+  template void launch_spike_rhs<T>(const int32_t*, const int32_t*, const int64_t*, int64_t,   \
+                                    const double*, int64_t, int32_t, T*, cudaStream_t);        \
+  template void launch_fwd_multi<T>(DevFronts, const int32_t*, int32_t, const T*,              \
+                                    const int64_t*, int64_t, int32_t, T*, T*, cudaStream_t);   \
+  template void launch_bwd_multi<T>(DevFronts, const int32_t*, int32_t, const T*,              \
+                                    const int64_t*, int64_t, int32_t, T*, cudaStream_t);
+
+DDPS_INST_T(double)
+DDPS_INST_T(float)
+
+#define DDPS_INST_TG(T, TG)                                                                     \
+  template void launch_ghat_extract<T, TG>(const int32_t*, const int32_t*, const int64_t*,     \
+                                           const int64_t*, const int64_t*, int64_t, int64_t,    \
+                                           int32_t, const T*, TG*, cudaStream_t);
+
+DDPS_INST_TG(double, double)
+DDPS_INST_TG(double, float)
+DDPS_INST_TG(float, float)
+DDPS_INST_TG(float, __nv_bfloat16)
+DDPS_INST_TG(double, __nv_bfloat16)
+
+}  // namespace ddps

@@ -1,0 +1,70 @@
+// Segmented vector operations of the BiCGStab loops (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ddps {
+
+// Chunked view of a vector split into segments (one segment per system).
+// Chunks never cross a segment boundary.
+struct SegView {
+  const int64_t* chunk_beg;
+  const int64_t* chunk_end;
+  const int32_t* chunk_seg;
+  const int32_t* seg_chunk_ptr;  // nseg+1
+  int32_t nchunks;
+  int32_t nseg;
+};
+
+// One reduction: op 0 = dot(x, y), 1 = 2-norm of x, 2 = inf-norm of x; the
+// result for segment s goes to out[s].
+struct RedSpec {
+  const void* x;
+  const void* y;
+  int op;
+  int stride;   // out is written at out[s * stride]
+  double* out;
+};
+
+// BiCGStab scalars of one segment.
+struct KScal {
+  double rho, rho_old, alpha, omega, beta, sigma, ts, tt;
+  double ref;         // reference norm of the stopping test
+  double nrm;         // last residual norm
+  double nrm2;        // second norm slot (true residual)
+  int32_t active;     // still iterating
+  int32_t half_done;  // converged at the half step of the current iteration
+  int32_t breakdown;
+  int32_t flag;       // scratch mask for masked updates
+};
+static_assert(sizeof(KScal) % sizeof(double) == 0, "KScal must be a whole number of doubles");
+constexpr int kScalStride = (int)(sizeof(KScal) / sizeof(double));
+
+template <typename T>
+void seg_reduce(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2, double* partial,
+                cudaStream_t s);
+template <typename T>
+void update_p(const SegView& S, const KScal* sc, const T* r, T* p, const T* v, cudaStream_t s);
+template <typename T>
+void update_s(const SegView& S, const KScal* sc, const T* r, const T* v, T* out, cudaStream_t s);
+template <typename T>
+void update_xr(const SegView& S, const KScal* sc, int half, T* x, const T* phat, const T* shat,
+               T* r, const T* sv, const T* t, cudaStream_t s);
+template <typename T>
+void vec_sub(const SegView& S, const KScal* sc, int all, const T* a, const T* b, T* dst,
+             cudaStream_t s);
+template <typename TD, typename TS>
+void convert(int64_t n, const TS* src, TD* dst, cudaStream_t s);
+// dst = a + alpha_s * b on segments whose flag is set (b may be null: dst = a)
+template <typename T>
+void masked_axpy(const SegView& S, const KScal* sc, T* dst, const T* a, const T* b, cudaStream_t s);
+// dst = 0 on segments whose flag is set
+template <typename T>
+void masked_zero(const SegView& S, const KScal* sc, T* dst, cudaStream_t s);
+void sc_beta(int nseg, KScal* sc, int first, cudaStream_t s);
+void sc_alpha(int nseg, KScal* sc, cudaStream_t s);
+void sc_omega(int nseg, KScal* sc, cudaStream_t s);
+
+}  // namespace ddps

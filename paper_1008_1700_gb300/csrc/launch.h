@@ -1,0 +1,89 @@
+// Device-side views and kernel launchers shared by the library's translation
+// units (internal, not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+namespace ddps {
+
+// Multifrontal structure of all blocks, resident on the device.
+struct DevFronts {
+  const int32_t* k;        // pivots per front
+  const int32_t* m;        // front order
+  const int32_t* block;    // owning block
+  const int64_t* row0;     // new index of the first pivot
+  const int64_t* arena;    // offset of the m x m column-major front
+  const int64_t* idx_off;  // offset into idx
+  const int64_t* upd;      // offset of the update vector / update rows
+  const int64_t* rel_off;  // offset into rel (-1 for roots)
+  const int32_t* cbeg;     // children list range
+  const int32_t* cend;
+  const int32_t* children;
+  const int32_t* idx;      // front row lists (new indices)
+  const int32_t* rel;      // child update row -> parent front position
+};
+
+// Error record written by kernels: [0] = code (0 none, 1 small pivot, 2 timeout),
+// [1] = front, [2] = new row index.
+struct DevError {
+  long long* rec;
+};
+
+// ---- factor.cu --------------------------------------------------------------
+template <typename T>
+void launch_assemble(const double* values, const int64_t* amap, int64_t nnz, T* arena,
+                     cudaStream_t s);
+void launch_row_absmax(const int32_t* rowptr, const int64_t* amap, const double* values,
+                       const int32_t* iperm, int64_t n, double* rownorm_new, cudaStream_t s);
+template <typename T>
+void launch_extend_add_p(DevFronts F, const int32_t* parent, const int32_t* child_list,
+                         int32_t nchild, int32_t max_r, T* arena, cudaStream_t s);
+template <typename T>
+void launch_front_lu(DevFronts F, const int32_t* list, int32_t nf, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
+// multi-RHS spike solves on a row-major panel X (n x NR) and update rows U (upd_size x NR)
+template <typename T>
+void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const int64_t* rt_src,
+                      int64_t nrt, const double* values, int64_t j0, int32_t NR, T* X,
+                      cudaStream_t s);
+template <typename T>
+void launch_fwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
+                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, T* U,
+                      cudaStream_t s);
+template <typename T>
+void launch_bwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
+                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, cudaStream_t s);
+template <typename T, typename TG>
+void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
+                         const int64_t* gcol_ptr, const int64_t* ghat_off, int64_t m, int64_t j0,
+                         int32_t NR, const T* X, TG* ghat, cudaStream_t s);
+
+// ---- solve.cu ---------------------------------------------------------------
+template <typename T>
+void launch_permute_in(const double* y, const int32_t* perm, int64_t n, T* w, cudaStream_t s);
+template <typename T>
+void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, cudaStream_t s);
+template <typename T>
+void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
+                 T* w, T* u, cudaStream_t s);
+template <typename T>
+void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
+                 T* w, cudaStream_t s);
+void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
+                 const double* x, double* y, cudaStream_t s);
+// y_out = y - R~ zhat (R~ rows over original indices, reduced columns)
+void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
+                        int64_t n, const double* y, const double* zhat, double* out,
+                        cudaStream_t s);
+template <typename TG, typename TI>
+void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,
+                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int32_t* gcols,
+                        int64_t m, const TI* v, TI* w, cudaStream_t s);
+void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s);
+void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_t nrt,
+                             double* rt_val, cudaStream_t s);
+
+}  // namespace ddps

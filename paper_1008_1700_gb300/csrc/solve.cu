@@ -1,0 +1,303 @@
+// Solve-phase kernels of DDPS: the block solves of Fig. 3 (6.1 and the
+// retrieval 6.5 written as z = D~^-1 (y - R~ z^)), the products with A (outer
+// Krylov, Fig. 2 step 6) and with R~, and the reduced product w = G^ v of 6.3.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "launch.h"
+
+namespace ddps {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 32) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <typename T>
+__global__ void k_permute_in(const double* __restrict__ y, const int32_t* __restrict__ perm,
+                             int64_t n, T* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = (T)y[perm[i]];
+}
+
+template <typename T>
+__global__ void k_permute_out(const T* __restrict__ w, const int32_t* __restrict__ perm, int64_t n,
+                              double* __restrict__ g) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    g[perm[i]] = (double)w[i];
+}
+
+// Forward substitution with L (unit lower) for one front per CTA.  The front
+// vector t (m entries, shared memory) starts with the pivot entries of w and
+// zeros, receives the children's update vectors, is solved column by column;
+// the pivots go back to w and the update entries to u (for the parent).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
+           T* __restrict__ w, T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const T* __restrict__ A = arena + F.arena[f];
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) t[i] = i < k ? w[row0 + i] : T(0);
+  __syncthreads();
+  for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
+    const int32_t c = F.children[ci];
+    const int32_t rc = F.m[c] - F.k[c];
+    const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
+    const T* __restrict__ uc = u + F.upd[c];
+    for (int i = tid; i < rc; i += blockDim.x) t[rel[i]] += uc[i];
+    __syncthreads();
+  }
+  for (int j = 0; j < k; ++j) {
+    const T yj = t[j];
+    const T* __restrict__ Lj = A + (int64_t)j * m;
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) t[i] -= Lj[i] * yj;
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += blockDim.x) {
+    if (i < k)
+      w[row0 + i] = t[i];
+    else
+      u[F.upd[f] + (i - k)] = t[i];
+  }
+}
+
+// Backward substitution for one front per CTA: x_piv = U11^-1 (y_piv - U12 x_upd),
+// x_upd read from w (ancestor pivots, already final).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_bwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
+           T* __restrict__ w) {
+  extern __shared__ unsigned char smem_raw[];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f], r = m - k;
+  const T* __restrict__ A = arena + F.arena[f];
+  const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x;
+  T* xu = t + k;
+  for (int j = tid; j < r; j += blockDim.x) xu[j] = w[idx[k + j]];
+  __syncthreads();
+  for (int i = tid; i < k; i += blockDim.x) {
+    T acc = w[row0 + i];
+    for (int j = 0; j < r; ++j) acc -= A[i + (int64_t)(k + j) * m] * xu[j];
+    t[i] = acc;
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T* __restrict__ Uj = A + (int64_t)j * m;
+    const T xj = t[j] / Uj[j];
+    __syncthreads();
+    if (tid == (j % blockDim.x)) t[j] = xj;
+    for (int i = tid; i < j; i += blockDim.x) t[i] -= Uj[i] * xj;
+    __syncthreads();
+  }
+  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = t[i];
+}
+
+// y = A x, CSR, four lanes per row.
+__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                       const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
+                       double* __restrict__ y) {
+  const int sub = threadIdx.x & 3;
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2; row < n;
+       row += ((int64_t)gridDim.x * blockDim.x) >> 2) {
+    double s = 0.0;
+    for (int32_t e = rowptr[row] + sub; e < rowptr[row + 1]; e += 4) s += vals[e] * x[colind[e]];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (sub == 0) y[row] = s;
+  }
+}
+
+// out = y - R~ zhat
+__global__ void k_rt_residual(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, int64_t n,
+                              const double* __restrict__ y, const double* __restrict__ zhat,
+                              double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = y[i];
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s -= val[e] * zhat[col[e]];
+    out[i] = s;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v) {
+  return (float)v;
+}
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+template <typename TG>
+struct Acc {
+  using type = float;
+};
+template <>
+struct Acc<double> {
+  using type = double;
+};
+
+// w = v + G(c,c) v: one warp per reduced row; the row's coupling columns are
+// gathered from v.  FP32 accumulation for FP32/BF16 storage, FP64 for FP64.
+template <typename TG, typename TI>
+__global__ void k_ghat_matvec(const TG* __restrict__ ghat, const int32_t* __restrict__ qblock,
+                              const int64_t* __restrict__ gq0, const int64_t* __restrict__ gcol_ptr,
+                              const int64_t* __restrict__ ghat_off,
+                              const int32_t* __restrict__ gcols, int64_t m,
+                              const TI* __restrict__ v, TI* __restrict__ w) {
+  using AT = typename Acc<TG>::type;
+  const int lane = threadIdx.x & 31;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < m;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t b = qblock[q];
+    const int64_t c0 = gcol_ptr[b];
+    const int64_t nc = gcol_ptr[b + 1] - c0;
+    const TG* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * nc;
+    const int32_t* __restrict__ cols = gcols + c0;
+    AT s = 0;
+    for (int64_t j = lane; j < nc; j += 32) s += (AT)to_f(row[j]) * (AT)v[cols[j]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[q] = (TI)((AT)v[q] + s);
+  }
+}
+
+template <>
+__global__ void k_ghat_matvec<double, double>(const double* __restrict__ ghat,
+                                              const int32_t* __restrict__ qblock,
+                                              const int64_t* __restrict__ gq0,
+                                              const int64_t* __restrict__ gcol_ptr,
+                                              const int64_t* __restrict__ ghat_off,
+                                              const int32_t* __restrict__ gcols, int64_t m,
+                                              const double* __restrict__ v,
+                                              double* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < m;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t b = qblock[q];
+    const int64_t c0 = gcol_ptr[b];
+    const int64_t nc = gcol_ptr[b + 1] - c0;
+    const double* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * nc;
+    const int32_t* __restrict__ cols = gcols + c0;
+    double s = 0;
+    for (int64_t j = lane; j < nc; j += 32) s += row[j] * v[cols[j]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[q] = v[q] + s;
+  }
+}
+
+__global__ void k_gather(const double* __restrict__ src, const int64_t* __restrict__ idx, int64_t m,
+                         double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+}  // namespace
+
+template <typename T>
+void launch_permute_in(const double* y, const int32_t* perm, int64_t n, T* w, cudaStream_t s) {
+  k_permute_in<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(y, perm, n, w);
+}
+template <typename T>
+void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, cudaStream_t s) {
+  k_permute_out<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(w, perm, n, g);
+}
+
+template <typename T>
+void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
+                 T* w, T* u, cudaStream_t s) {
+  if (nf <= 0) return;
+  size_t sm = (size_t)max_m * sizeof(T);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_fwd1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_fwd1<T><<<nf, kThreads, sm, s>>>(F, list, arena, w, u);
+}
+template <typename T>
+void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
+                 T* w, cudaStream_t s) {
+  if (nf <= 0) return;
+  size_t sm = (size_t)max_m * sizeof(T);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_bwd1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_bwd1<T><<<nf, kThreads, sm, s>>>(F, list, arena, w);
+}
+
+void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
+                 const double* x, double* y, cudaStream_t s) {
+  k_spmv<<<grid_for(n * 4, kThreads), kThreads, 0, s>>>(rowptr, colind, vals, n, x, y);
+}
+
+void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
+                        int64_t n, const double* y, const double* zhat, double* out,
+                        cudaStream_t s) {
+  k_rt_residual<<<grid_for(n, kThreads), kThreads, 0, s>>>(rt_rowptr, rt_col, rt_val, n, y, zhat,
+                                                            out);
+}
+
+template <typename TG, typename TI>
+void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,
+                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int32_t* gcols,
+                        int64_t m, const TI* v, TI* w, cudaStream_t s) {
+  if (m <= 0) return;
+  k_ghat_matvec<TG, TI><<<grid_for(m * 32, kThreads), kThreads, 0, s>>>(
+      ghat, qblock, gq0, gcol_ptr, ghat_off, gcols, m, v, w);
+}
+
+void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s) {
+  if (m <= 0) return;
+  k_gather<<<grid_for(m, kThreads), kThreads, 0, s>>>(src, idx, m, dst);
+}
+
+void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_t nrt,
+                             double* rt_val, cudaStream_t s) {
+  if (nrt <= 0) return;
+  k_gather<<<grid_for(nrt, kThreads), kThreads, 0, s>>>(values, rt_src, nrt, rt_val);
+}
+
+#define DDPS_INST_S(T)                                                                          \
+  template void launch_permute_in<T>(const double*, const int32_t*, int64_t, T*, cudaStream_t); \
+  template void launch_permute_out<T>(const T*, const int32_t*, int64_t, double*, cudaStream_t);\
+  template void launch_fwd1<T>(DevFronts, const int32_t*, int32_t, int32_t, const T*, T*, T*,   \
+                               cudaStream_t);                                                   \
+  template void launch_bwd1<T>(DevFronts, const int32_t*, int32_t, int32_t, const T*, T*,       \
+                               cudaStream_t);
+DDPS_INST_S(double)
+DDPS_INST_S(float)
+
+template void launch_ghat_matvec<double, double>(const double*, const int32_t*, const int64_t*,
+                                                 const int64_t*, const int64_t*, const int32_t*,
+                                                 int64_t, const double*, double*, cudaStream_t);
+template void launch_ghat_matvec<float, double>(const float*, const int32_t*, const int64_t*,
+                                                const int64_t*, const int64_t*, const int32_t*,
+                                                int64_t, const double*, double*, cudaStream_t);
+template void launch_ghat_matvec<float, float>(const float*, const int32_t*, const int64_t*,
+                                               const int64_t*, const int64_t*, const int32_t*,
+                                               int64_t, const float*, float*, cudaStream_t);
+template void launch_ghat_matvec<__nv_bfloat16, float>(const __nv_bfloat16*, const int32_t*,
+                                                       const int64_t*, const int64_t*,
+                                                       const int64_t*, const int32_t*, int64_t,
+                                                       const float*, float*, cudaStream_t);
+template void launch_ghat_matvec<__nv_bfloat16, double>(const __nv_bfloat16*, const int32_t*,
+                                                        const int64_t*, const int64_t*,
+                                                        const int64_t*, const int32_t*, int64_t,
+                                                        const double*, double*, cudaStream_t);
+
+}  // namespace ddps

@@ -30,3 +30,10 @@ def read_golden(name):
                 continue
             sections[cur].append([float(t) for t in line.split()])
     return {k: np.array(v if len(v) > 1 else v[0]) for k, v in sections.items()}
+
+
+def pytest_sessionstart(session):
+    # The native library is built in-tree; compile it if it is missing or stale
+    # (nvcc cross-compiles without a GPU).
+    from paper_1008_1700_gb300.build import build
+    build()

@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs: the worked example of Sec. 3, every step of Fig. 3,
+the spikes G^ element by element and the full solve, for FP64 and the
+mixed-precision forms."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from conftest import read_golden
+from gpu_helpers import dev, host, make_solver, relerr
+from oracle.ddps_oracle import DDPSOracle
+from paper_1008_1700_gb300 import native as N
+
+pytestmark = pytest.mark.gpu
+
+FP64 = dict(factor_prec=N.DDPS_FP64, spike_prec=N.DDPS_FP64, ghat_prec=N.DDPS_FP64,
+            inner_prec=N.DDPS_FP64)
+MIXED = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
+             inner_prec=N.DDPS_FP32)
+MIXED_BF16 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_BF16,
+                  inner_prec=N.DDPS_FP32)
+
+
+def test_worked_example_on_gpu():
+    gold = read_golden("worked_example_9x9.txt")
+    P = W.worked_example(gold["A"], gold["block_ptr"].astype(np.int64), gold["f"])
+    S = make_solver(P, tol_out=1e-14, tol_in=1e-14, maxit_in=20, **FP64)
+    assert list(S.interface() + 1) == [1, 2, 5, 9]
+    Gh = np.eye(4)
+    for b in range(3):
+        q0, q1, cols = S.ghat_layout(b)
+        Gh[q0:q1][:, cols] += S.ghat_block(b)
+    assert np.max(np.abs(Gh - gold["Ghat"])) <= 5e-5
+    g = host(S.block_solve(dev(np.ones(9))))
+    assert np.max(np.abs(g - gold["g"])) <= 5e-5
+    x, info = S.solve(dev(np.ones(9)))
+    assert info["status"] == "DDPS_OK" and info["outer_iterations"] <= 1.0
+    assert np.max(np.abs(host(x) - gold["x"])) <= 5e-5
+
+
+PROBLEMS = {
+    "cd2d_24_p3": (lambda: W.small_convdiff_2d(24, 3), None),
+    "cd2d_cfg1": (lambda: W.cfg1(), None),
+    "cd3d_12_slabs": (lambda: W.small_convdiff_3d(12, [3, 5, 4]), None),
+    "randdd_301_p7": (lambda: W.small_random_dd(301, 7, seed=9), None),
+    "band_3000_abs": (lambda: W.small_random_band(3000, 5, 200, seed=2), ("abs", 1e-4)),
+    "band_2500_col": (lambda: W.small_random_band(2500, 4, 150, seed=3), ("column", 0.6)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(PROBLEMS))
+def case(request):
+    make, drop = PROBLEMS[request.param]
+    P = make()
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=drop)
+    return request.param, P, drop, o
+
+
+def test_ghat_matches_oracle_elementwise(case):
+    name, P, drop, o = case
+    S = make_solver(P, drop, **FP64)
+    assert np.array_equal(S.interface(), o.c)
+    for b, ob in enumerate(o.blk):
+        q0, q1, cols = S.ghat_layout(b)
+        assert (q0, q1) == (ob["q0"], ob["q1"])
+        assert np.array_equal(cols, ob["pos_i"])
+        if (q1 - q0) * len(cols) == 0:
+            continue
+        Gg = S.ghat_block(b)
+        scale = max(np.max(np.abs(ob["Ghat"])), 1e-300)
+        assert np.max(np.abs(Gg - ob["Ghat"])) <= 1e-11 * scale, (name, b)
+
+
+def test_block_solve_and_reduced_matvec(case):
+    name, P, drop, o = case
+    S = make_solver(P, drop, **FP64)
+    y = np.random.default_rng(1).standard_normal(P.n)
+    assert relerr(host(S.block_solve(dev(y))), o.block_solve(y)) <= 1e-12
+    if o.m:
+        v = np.random.default_rng(2).standard_normal(o.m)
+        assert relerr(host(S.reduced_matvec(dev(v))), o.reduced_matvec(v)) <= 1e-12
+    yt = dev(y)
+    assert relerr(host(S.spmv(yt)), o.A @ y) <= 1e-14
+
+
+def test_precond_apply_direct_mode(case):
+    """With a tight inner tolerance Fig. 3 returns P^-1 y; both sides agree."""
+    name, P, drop, o = case
+    S = make_solver(P, drop, tol_in=1e-13, maxit_in=500, **FP64)
+    y = np.random.default_rng(3).standard_normal(P.n)
+    z = host(S.precond_apply(dev(y)))
+    zo, _ = o.precond(y, mode="direct")
+    assert relerr(z, zo) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+def test_full_solve_parity(case, prec):
+    name, P, drop, o = case
+    opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16}[prec]
+    S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **opts)
+    x, info = S.solve(dev(P.f))
+    assert info["status"] == "DDPS_OK", info
+    x = host(x)
+    xo, oinfo = o.solve(P.f, tol=1e-12, eps_in=1e-6, maxit_in=200)
+    A = o.A
+    assert np.max(np.abs(P.f - A @ x)) / np.max(np.abs(P.f)) <= 1e-12
+    assert info["relres_inf"] <= 1e-12
+    assert relerr(x, xo) <= 1e-8
+
+
+def test_solve_is_deterministic():
+    P = W.small_convdiff_3d(12, [3, 5, 4])
+    S = make_solver(P, tol_out=1e-10, **MIXED)
+    f = dev(P.f)
+    x1, _ = S.solve(f)
+    x1 = host(x1).copy()
+    x2, _ = S.solve(f)
+    assert np.array_equal(x1, host(x2))
+
+
+def test_solve_host_buffers():
+    P = W.small_convdiff_2d(20, 4)
+    S = make_solver(P, tol_out=1e-12, tol_in=1e-10, **FP64)
+    x, info = S.solve_host(P.f)
+    assert info["status"] == "DDPS_OK"
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr)
+    xo, _ = o.solve(P.f, tol=1e-12, eps_in=1e-10)
+    assert relerr(x, xo) <= 1e-9
+
+
+def test_batched_equals_per_system():
+    """Independent systems stacked in one handle give each system's own result."""
+    from paper_1008_1700_gb300 import Solver
+    probs = [W.small_convdiff_2d(N, 4, seed=k) for k, N in enumerate([16, 21, 32, 19])]
+    S = Solver.from_systems([(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs],
+                            tol_out=1e-12, tol_in=1e-8, **MIXED)
+    S.factor(dev(S.values_host))
+    x, info = S.solve(dev(np.concatenate([p.f for p in probs])))
+    assert info["status"] == "DDPS_OK"
+    x = host(x)
+    for k, p in enumerate(probs):
+        xk = x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]]
+        o = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr)
+        xo, _ = o.solve(p.f, tol=1e-12, eps_in=1e-8)
+        assert relerr(xk, xo) <= 1e-8, k
+        assert np.max(np.abs(p.f - o.A @ xk)) / np.max(np.abs(p.f)) <= 1e-12
+
+
+def test_singular_block_is_reported():
+    P = W.small_convdiff_2d(10, 2)
+    vals = P.values.copy()
+    # zero the whole row 3 inside its diagonal block: A_11 becomes singular
+    r0, r1 = P.rowptr[3], P.rowptr[4]
+    vals[r0:r1] = 0.0
+    S = make_solver(W.small_convdiff_2d(10, 2))
+    with pytest.raises(N.DDPSError, match="SINGULAR_BLOCK"):
+        S.factor(dev(vals))
+
+
+def test_not_converged_is_reported():
+    P = W.small_convdiff_2d(24, 6)
+    S = make_solver(P, tol_out=1e-14, maxit_out=1, tol_in=1e-1, maxit_in=1)
+    x, info = S.solve(dev(P.f))
+    assert info["status"] == "DDPS_ERR_NOT_CONVERGED"
+    assert info["relres_inf"] > 1e-14 and np.isfinite(info["relres_inf"])
+
+
+def test_reduced_guess_exact_and_rejected():
+    P = W.small_convdiff_2d(24, 3)
+    S = make_solver(P, tol_out=1e-10, tol_in=1e-8, **FP64)
+    x, info0 = S.solve(dev(P.f))
+    zhat, ghat = S.reduced_solution()
+    # the exact reduced solution as guess: the first inner solve needs no iteration
+    S.set_reduced_guess(zhat)
+    x1, info1 = S.solve(dev(P.f))
+    assert info1["guess_used"] == 1 and info1["first_inner_iters"] < info0["first_inner_iters"]
+    assert info1["status"] == "DDPS_OK"
+    # a guess worse than zero is rejected and the solve still converges
+    S.set_reduced_guess(zhat * -50.0)
+    x2, info2 = S.solve(dev(P.f))
+    assert info2["guess_used"] == 0 and info2["status"] == "DDPS_OK"
+    S.set_reduced_guess(None)

@@ -1,0 +1,83 @@
+"""CPU checks of the native library: it loads, exports every entry point the
+header declares, and its host-side symbolic analysis (Fig. 2 steps 1, 3, 5
+and the nested-dissection layout) agrees with the oracle.  No GPU calls."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.ddps_oracle import DDPSOracle
+from paper_1008_1700_gb300 import native as N
+from paper_1008_1700_gb300.solver import stack_systems
+
+
+def test_library_exports_every_declared_symbol():
+    declared = N._declared_names()
+    assert "ddps_analyze" in declared and "ddps_solve" in declared
+    lib = N.load()
+    missing = [d for d in declared if not hasattr(lib, d)]
+    assert missing == []
+
+
+CASES = [
+    (lambda: W.cfg1(), None),
+    (lambda: W.small_convdiff_3d(10, [3, 4, 3]), None),
+    (lambda: W.small_random_band(3000, 5, 200, seed=2), ("abs", 1e-4)),
+    (lambda: W.small_random_band(3000, 5, 200, seed=3), ("column", 0.6)),
+    (lambda: W.small_random_dd(301, 7, seed=9), None),
+]
+
+
+def _opts(drop):
+    if drop is None:
+        return N.default_options()
+    mode = N.DDPS_DROP_ABS if drop[0] == "abs" else N.DDPS_DROP_COLUMN
+    return N.default_options(drop_mode=mode, drop_tol=drop[1])
+
+
+@pytest.mark.parametrize("make,drop", CASES)
+def test_symbolic_matches_oracle(make, drop):
+    P = make()
+    sizes, perm, c = N.ddps_symbolic(P.rowptr, P.colind, P.block_ptr, values=P.values,
+                                     options=_opts(drop))
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=drop, spikes=False)
+    # Fig. 2 step 5: the same interface set
+    assert np.array_equal(c, o.c)
+    assert sizes["m"] == o.m and sizes["nnz_rt"] == o.Rt.nnz
+    # G^ layout: block rows in c times coupling columns
+    assert sizes["ghat_entries"] == sum((b["q1"] - b["q0"]) * len(b["c_i"]) for b in o.blk)
+    # the ordering permutes rows inside their own block only
+    assert np.array_equal(np.sort(perm), np.arange(P.n))
+    blk_of = np.searchsorted(P.block_ptr, np.arange(P.n), side="right") - 1
+    assert np.array_equal(blk_of[perm], blk_of)
+
+
+def test_symbolic_rejects_bad_input():
+    P = W.small_random_dd(40, 2, seed=1)
+    bad = P.colind.copy()
+    bad[3] = P.n + 5
+    with pytest.raises(N.DDPSError, match="INVALID_ARG"):
+        N.ddps_symbolic(P.rowptr, bad, P.block_ptr)
+    with pytest.raises(N.DDPSError, match="INVALID_ARG"):
+        N.ddps_symbolic(P.rowptr, P.colind, np.array([0, 30, 20, 40]))
+    with pytest.raises(N.DDPSError, match="INVALID_ARG"):  # drop rule without values
+        N.ddps_symbolic(P.rowptr, P.colind, P.block_ptr,
+                        options=N.default_options(drop_mode=N.DDPS_DROP_ABS, drop_tol=1e-3))
+
+
+def test_stack_systems_and_cross_system_entries():
+    a = W.small_convdiff_2d(6, 2)
+    b = W.small_random_dd(30, 3, seed=4)
+    rp, ci, v, bp, sbp, srp = stack_systems([(a.rowptr, a.colind, a.values, a.block_ptr),
+                                             (b.rowptr, b.colind, b.values, b.block_ptr)])
+    assert list(sbp) == [0, 2, 5] and list(srp) == [0, 36, 66]
+    sizes, perm, c = N.ddps_symbolic(rp, ci, bp, sbp)
+    ca = DDPSOracle(a.n, a.rowptr, a.colind, a.values, a.block_ptr, spikes=False).c
+    cb = DDPSOracle(b.n, b.rowptr, b.colind, b.values, b.block_ptr, spikes=False).c
+    assert np.array_equal(c, np.concatenate([ca, cb + a.n]))
+    # an entry coupling the two systems is rejected
+    ci2 = ci.copy()
+    ci2[rp[1] - 1] = 40  # row 0 of system a pointing into system b
+    ci2[rp[0]:rp[1]] = np.sort(ci2[rp[0]:rp[1]])
+    with pytest.raises(N.DDPSError, match="couples two systems"):
+        N.ddps_symbolic(rp, ci2, bp, sbp)
