@@ -1,0 +1,458 @@
+#!/usr/bin/env python
+"""Throughput benchmark of GPU DDPS: solves per second at true relative
+residual ||f - A x||_inf / ||f||_inf <= 1e-10.
+
+Workload (default): 3-D 7-point convection-diffusion on a 64^3 grid, one
+convection constant per axis ~ U[0, 50] (seeded), 16 z-slab blocks of 3-5
+planes, f = A x_true with x_true ~ U[-1, 1] (seed 0).  One step = one whole
+DDPS pass over one system: ddps_factor (Fig. 2 steps 1-5: split, block LU,
+spikes, G^) + ddps_solve (Fig. 2 step 6: outer BiCGStab with the Fig. 3
+preconditioner).  The symbolic analysis depends only on the sparsity
+pattern; it runs once before the timed region and is reported as
+``analyze_ms``.
+
+Forms: ``mixed`` = FP32 block factors, spikes, G^ and inner vectors, FP64
+outer Krylov (the headline), ``fp64`` = plain FP64 DDPS.
+
+Under torchrun every rank solves its own copy of the workload (the systems
+are independent; no collective on the data path) and ``value`` counts the
+solves of all ranks over the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at rel. residual 1e-10, mixed/batched/learned vs plain FP64 DDPS on GB300"
+UNIT = "solves/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cd3d_64_slabs16",
+                    choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8"])
+    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="steps of the plain-FP64 comparison run (0 skips it)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# workload and solver settings
+# ----------------------------------------------------------------------------
+
+def make_workload(name):
+    import workloads as W
+    if name == "cd3d_64_slabs16":
+        return W.cfg2()
+    if name == "cd2d_64_p4":
+        return W.cfg1()
+    if name == "cd3d_48_slabs8":
+        return W.cfg5(1)
+    raise ValueError(name)
+
+
+def form_options(form):
+    from paper_1008_1700_gb300 import native as N
+    base = dict(tol_out=1e-10, maxit_out=1000, tol_in=1e-4, maxit_in=100)
+    if form == "mixed":
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
+                    inner_prec=N.DDPS_FP32)
+    else:
+        base.update(factor_prec=N.DDPS_FP64, spike_prec=N.DDPS_FP64, ghat_prec=N.DDPS_FP64,
+                    inner_prec=N.DDPS_FP64)
+    return base
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "sm_max_mhz": float(pk.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per kernel class (bytes for memory-bound, flops for ALU-bound)
+# ----------------------------------------------------------------------------
+
+def algorithmic_work(sizes, P, form, steps, prof):
+    """Per class: (kind, total algorithmic amount over the timed region)."""
+    sf = 4 if form == "mixed" else 8
+    si = sf
+    n, nnz, m = sizes["n"], sizes["nnz"], sizes["m"]
+    out = {}
+    # per factor: Fig. 2 steps 2 and 4
+    out["front_lu"] = ("flops", sizes["factor_flops"] * steps)
+    out["spike_fwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
+    out["spike_bwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
+    out["assemble"] = ("bytes", (nnz * (8 + 8) + sizes["factor_entries"] * sf) * steps)
+    out["ghat_extract"] = ("bytes", sizes["ghat_entries"] * (sf + sf) * steps)
+    # per call of the solve phase
+    calls = {k: v[1] for k, v in prof.items()}
+    out["block_solve"] = ("bytes", (sizes["factor_lu_entries"] * sf + n * 16) * calls["block_solve"])
+    out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sf + 2 * m * si) * calls["ghat_matvec"])
+    out["spmv"] = ("bytes", (nnz * 12 + (n + 1) * 4 + n * 16) * calls["spmv"])
+    return out
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (bench's CPU-baseline leg and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(P, nblocks=4, ncols=1024):
+    """Times the oracle's Fig. 2 steps 1-5 on `nblocks` blocks with `ncols`
+    spike columns each and scales to every block and column.  The solve phase
+    (Fig. 2 step 6) is not included, so the scaled time is a lower bound on the
+    oracle's seconds per solve."""
+    import numpy as np
+    from oracle.ddps_oracle import csr, factor_blocks, interface_columns, split_block_rows
+
+    t0 = time.perf_counter()
+    A = csr(P.n, P.rowptr, P.colind, P.values)
+    D, R = split_block_rows(A, P.block_ptr)
+    interface_columns(R)
+    t_split = time.perf_counter() - t0
+    bp = P.block_ptr
+    est = t_split
+    per_block = []
+    for i in range(min(nblocks, P.p)):
+        t1 = time.perf_counter()
+        lu = factor_blocks([D[i]])[0]
+        t_lu = time.perf_counter() - t1
+        Ri = R[bp[i]:bp[i + 1], :]
+        ci = np.unique(Ri.indices)
+        k = min(ncols, len(ci))
+        t2 = time.perf_counter()
+        if k:
+            cols = Ri.tocsc()[:, ci[:k]]
+            lu.solve(cols.toarray())
+        t_sp = time.perf_counter() - t2
+        per_block.append(t_lu + (t_sp * len(ci) / k if k else 0.0))
+    est += statistics.mean(per_block) * P.p
+    wall = time.perf_counter() - t0
+    return est, wall
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(th) if th else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P = make_workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(P, nblocks=2, ncols=256)
+    ests, walls = [], []
+    for _ in range(args.steps):
+        e, w = oracle_sample(P, nblocks=2, ncols=256)
+        ests.append(e)
+        walls.append(w)
+    sec = statistics.mean(ests)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "oracle Fig. 2 steps 1-5 on 2 of the blocks with 256 spike "
+                                   "columns each, scaled to all blocks and columns; solve phase "
+                                   "not counted (per step wall %.1f s)" % statistics.mean(walls)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1008_1700_gb300 import Solver, native as N
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    P = make_workload(args.workload)
+    opts = form_options(args.form)
+    t0 = time.perf_counter()
+    S = Solver(P.rowptr, P.colind, P.block_ptr, **opts)
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    sizes = S.sizes
+    vals = torch.tensor(P.values, device="cuda")
+    f = torch.tensor(P.f, device="cuda")
+    x = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.factor(vals)
+        _, info = S.solve(f, x)
+        return info
+
+    info = None
+    for _ in range(args.warmup):
+        info = step()
+    S.set_profiling((1 << len(N.PROF_CLASSES)) - 1)
+    S.profile(reset=True)
+    launches0 = S.launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = S.profile(reset=True)
+    launches = S.launch_count() - launches0
+    S.set_profiling(0)
+    ms_max = max_over_ranks(ms)
+    value = world * args.steps / (ms_max / 1e3)
+
+    # accuracy of the last step against the known solution and the residual
+    xh = x.cpu().numpy()
+    err_xtrue = float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))
+    relres = max(i["relres_inf"] for i in infos)
+    converged = all(i["status"] == "DDPS_OK" for i in infos)
+
+    # roofline of the dominant kernel class
+    peaks = load_peaks()
+    work = algorithmic_work(sizes, P, args.form, args.steps, prof)
+    total_prof = sum(v[0] for v in prof.values())
+    kern = {}
+    for cls, (kms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        kind, amount = work.get(cls, ("bytes", 0.0))
+        rate = amount / (kms / 1e3) if kms > 0 else 0.0
+        kern[cls] = {"ms": round(kms, 3), "groups": cnt, "share": round(kms / ms, 4),
+                     "achieved": round(rate / (1e9 if kind == "bytes" else 1e12), 3),
+                     "unit": "GB/s" if kind == "bytes" else "TFLOP/s"}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    dk = kern[dom]
+    sm_mhz = peaks["sm_max_mhz"]
+    if dk["unit"] == "GB/s":
+        peak = peaks["hbm_gbs"]
+        bound = "hbm"
+        peak_note = f"{peaks['source']} HBM copy bandwidth"
+    else:
+        # FP32 (mixed) or FP64 (plain) SIMT: 152 SMs x lanes x 2 flops x max SM clock
+        lanes = 128 if args.form == "mixed" else 2
+        peak = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+        bound = "alu"
+        peak_note = ("FP32 SIMT: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz if args.form == "mixed"
+                     else "FP64: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz)
+    roof = {"kernel": dom, "bound": bound, "achieved": dk["achieved"], "peak": round(peak, 2),
+            "unit": dk["unit"], "frac": round(dk["achieved"] / peak, 4), "traffic": None,
+            "peak_source": peak_note}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.form == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
+                   "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
+                   "form": args.form, "parallelism": f"replicas{world}",
+                   "l2": "working set (G^ %.1f GB) larger than L2" %
+                         (sizes["ghat_entries"] * (4 if args.form == "mixed" else 8) / 1e9),
+                   "tol_out": opts["tol_out"], "tol_in": opts["tol_in"]},
+        "analyze_ms": round(analyze_ms, 1),
+        "accuracy": {"relres_inf": relres, "rel_err_vs_xtrue": err_xtrue, "converged": converged,
+                     "outer_iterations": infos[-1]["outer_iterations"],
+                     "inner_iterations": infos[-1]["inner_iterations"]},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roof,
+        "kernels": kern,
+    }
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    if not args.no_e2e:
+        vals_h = torch.tensor(P.values).pin_memory()
+        f_h = np.ascontiguousarray(P.f)
+        x_h = np.empty_like(f_h)
+        vals_d2 = torch.empty_like(vals)
+
+        def e2e_step():
+            vals_d2.copy_(vals_h, non_blocking=True)
+            S.factor(vals_d2)
+            N.ddps_solve_host(S.h, f_h, x_h)
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(a0.elapsed_time(a1))
+        line["e2e"] = {"value": world * args.steps / (ems / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(P.nnz * 8 + P.n * 8),
+                       "d2h_bytes_per_step": int(P.n * 8)}
+
+    # plain FP64 DDPS on the same GPU and workload (the comparison the metric names)
+    if args.form == "mixed" and args.fp64_steps > 0:
+        S64 = Solver(P.rowptr, P.colind, P.block_ptr, **form_options("fp64"))
+        x64 = torch.empty_like(f)
+        S64.factor(vals)
+        S64.solve(f, x64)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        i64 = None
+        for _ in range(args.fp64_steps):
+            S64.factor(vals)
+            _, i64 = S64.solve(f, x64)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        fms = max_over_ranks(b0.elapsed_time(b1))
+        v64 = world * args.fp64_steps / (fms / 1e3)
+        line["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": fms / args.fp64_steps,
+                              "relres_inf": i64["relres_inf"],
+                              "outer_iterations": i64["outer_iterations"]}
+        line["speedup_vs_plain_fp64"] = value / v64
+        S64.close()
+
+    # CPU oracle, bounded sample, rank 0 only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, wall = oracle_sample(P, nblocks=4, ncols=1024)
+        line["cpu_baseline"] = {
+            "value": 1.0 / est, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+            "sample": "oracle Fig. 2 steps 1-5 on 4 of the %d blocks with 1024 spike columns "
+                      "each, scaled to all blocks and columns (%.1f s wall); the solve phase is "
+                      "not counted, so this overstates the oracle's solves/s" % (P.p, wall)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    S.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -202,6 +202,30 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
  * counter, read without synchronising). */
 int64_t ddps_launch_count(const ddps_handle* h);
 
+/* Kernel classes timed by ddps_set_profiling. */
+enum {
+  DDPS_PROF_ASSEMBLE = 0,      /* scatter of A's values into the fronts, pivot thresholds */
+  DDPS_PROF_EXTEND_ADD = 1,    /* child Schur complements added into parent fronts */
+  DDPS_PROF_FRONT_LU = 2,      /* partial LU of the fronts (Fig. 2 step 2) */
+  DDPS_PROF_SPIKE_FWD = 3,     /* multi-RHS forward substitution (Fig. 2 step 4) */
+  DDPS_PROF_SPIKE_BWD = 4,     /* multi-RHS backward substitution (Fig. 2 step 4) */
+  DDPS_PROF_GHAT_EXTRACT = 5,  /* rows of the spikes in c written into G^ */
+  DDPS_PROF_BLOCK_SOLVE = 6,   /* g = D~^-1 y (6.1 and the retrieval) */
+  DDPS_PROF_GHAT_MATVEC = 7,   /* w = G^ v (6.3) */
+  DDPS_PROF_SPMV = 8,          /* y = A x (outer Krylov) */
+  DDPS_PROF_CLASSES = 9
+};
+
+/* Enables CUDA-event timing of the kernel classes whose bit (1 << class) is
+ * set in mask (0 disables).  Every timed launch group is bracketed by an event
+ * pair on the stream it runs on. */
+ddps_status ddps_set_profiling(ddps_handle* h, int32_t mask);
+
+/* Totals since the last reset: ms[c] (host double[DDPS_PROF_CLASSES]) and
+ * count[c] (host int64[DDPS_PROF_CLASSES], launch groups timed); either may be
+ * NULL.  Waits for the recorded events.  reset != 0 clears the totals. */
+ddps_status ddps_get_profile(ddps_handle* h, double* ms, int64_t* count, int32_t reset);
+
 /* Host-only symbolic analysis: runs the analysis of ddps_analyze without any
  * device work and reports its sizes (may be NULL), the new-to-old row
  * permutation of the nested-dissection orders (host int32[n], may be NULL)

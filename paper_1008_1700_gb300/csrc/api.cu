@@ -78,10 +78,14 @@ struct ddps_handle {
   int32_t *c_rownew = nullptr, *qblock = nullptr, *gcols = nullptr;
   int64_t *gq0 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr, *block_ncols = nullptr;
   void* ghat = nullptr;
-  // spike panels
+  // spike panels: X (n x NR) and the fronts' working rows (sum of m x NR)
   void* X = nullptr;
   void* U = nullptr;
   int32_t NR = 0;
+  int32_t max_k = 0;
+  // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
+  int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
+  std::vector<int32_t> tk_ptr, tr_ptr;
   // segments
   SegView Sn{}, Sm{};
   int32_t nseg = 0;
@@ -105,6 +109,17 @@ struct ddps_handle {
   bool has_guess = false;
   double *first_zhat = nullptr, *first_ghat = nullptr;
   bool factored = false;
+  // per-class CUDA-event timing (ddps_set_profiling)
+  int32_t prof_mask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_recs;
+  double prof_ms[DDPS_PROF_CLASSES] = {};
+  int64_t prof_cnt[DDPS_PROF_CLASSES] = {};
   // statistics of the current solve
   int64_t stat_inner = 0, stat_precond = 0;
   double stat_first_inner = 0;
@@ -112,6 +127,47 @@ struct ddps_handle {
 };
 
 namespace {
+
+cudaEvent_t next_event(ddps_handle* h) {
+  if (h->ev_next == h->ev_pool.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_next++];
+}
+
+// Records a CUDA-event pair around the launches of one kernel class when that
+// class is enabled in the profiling mask.
+struct Prof {
+  ddps_handle* h;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  Prof(ddps_handle* hh, int c, cudaStream_t st) : h(hh), cls(c), s(st) {
+    if (h->prof_mask & (1 << cls)) {
+      cudaEvent_t a = next_event(h);
+      b = next_event(h);
+      CK(cudaEventRecord(a, s));
+      h->prof_recs.push_back({cls, a, b});
+    }
+  }
+  ~Prof() {
+    if (b) cudaEventRecord(b, s);
+  }
+};
+
+void prof_collect(ddps_handle* h) {
+  for (auto& r : h->prof_recs) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(r.b));
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof_ms[r.cls] += ms;
+    h->prof_cnt[r.cls] += 1;
+  }
+  h->prof_recs.clear();
+  h->ev_next = 0;
+}
 
 template <typename T>
 T* dalloc(ddps_handle* h, int64_t count) {
@@ -179,8 +235,11 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
   T* arena = (T*)h->arena;
   CK(cudaMemsetAsync(arena, 0, (size_t)A.arena_size * sizeof(T), s));
   CK(cudaMemsetAsync(h->derr, 0, 3 * sizeof(long long), s));
-  launch_assemble<T>(h->vals, h->amap, A.nnz, arena, s);
-  launch_row_absmax(h->rowptr, h->amap, h->vals, h->iperm, A.n, h->rownorm, s);
+  {
+    Prof pr(h, DDPS_PROF_ASSEMBLE, s);
+    launch_assemble<T>(h->vals, h->amap, A.nnz, arena, s);
+    launch_row_absmax(h->rowptr, h->amap, h->vals, h->iperm, A.n, h->rownorm, s);
+  }
   h->launches += 2;
   const int S = A.max_children;
   for (int L = A.nlevels - 1; L >= 0; --L) {
@@ -188,36 +247,48 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       const int64_t q = (int64_t)L * S + sl;
       const int32_t cnt = A.ea_ptr[q + 1] - A.ea_ptr[q];
       if (cnt > 0) {
+        Prof pr(h, DDPS_PROF_EXTEND_ADD, s);
         launch_extend_add_p<T>(h->F, h->parent, h->ea_list + A.ea_ptr[q], cnt, h->ea_maxr[q], arena, s);
         h->launches++;
       }
     }
     const int32_t nf = A.level_ptr[L + 1] - A.level_ptr[L];
+    Prof pr(h, DDPS_PROF_FRONT_LU, s);
     launch_front_lu<T>(h->F, h->level_fronts + A.level_ptr[L], nf, arena, h->rownorm,
                        h->opt.pivot_tol, h->derr, s);
-    h->launches++;
+    launch_tri_inverse<T>(h->F, h->level_fronts + A.level_ptr[L], nf, h->max_k, arena, s);
+    h->launches += 2;
   }
   launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
   h->launches++;
   const int64_t m = (int64_t)A.c.size();
   if (m > 0) {
     T* X = (T*)h->X;
-    T* U = (T*)h->U;
+    T* Tb = (T*)h->U;
     const int32_t NR = h->NR;
     for (int64_t j0 = 0; j0 < A.max_rhs; j0 += NR) {
       CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
       launch_spike_rhs<T>(h->rt_rownew, h->rt_rhscol, h->rt_src, h->nrt, h->vals, j0, NR, X, s);
       h->launches++;
       for (int L = A.nlevels - 1; L >= 0; --L) {
-        launch_fwd_multi<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                            arena, h->block_ncols, j0, NR, X, U, s);
-        h->launches++;
+        Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
+        launch_spike_gather<T>(h->F, h->level_fronts + A.level_ptr[L],
+                               A.level_ptr[L + 1] - A.level_ptr[L], h->block_ncols, j0, NR, X, Tb, s);
+        launch_spike_gemm<T>(OP_FWD_LINV, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
+                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        launch_spike_gemm<T>(OP_FWD_L21, h->F, h->tr_front + h->tr_ptr[L], h->tr_m0 + h->tr_ptr[L],
+                             h->tr_ptr[L + 1] - h->tr_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        h->launches += 3;
       }
       for (int L = 0; L < A.nlevels; ++L) {
-        launch_bwd_multi<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                            arena, h->block_ncols, j0, NR, X, s);
-        h->launches++;
+        Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
+        launch_spike_gemm<T>(OP_BWD_U12, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
+                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        launch_spike_gemm<T>(OP_BWD_UINV, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
+                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        h->launches += 2;
       }
+      Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
       launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, m, j0, NR,
                                  X, (TG*)h->ghat, s);
       h->launches++;
@@ -245,6 +316,7 @@ void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s
   T* w = (T*)h->w;
   T* u = (T*)h->updv;
   const T* arena = (const T*)h->arena;
+  Prof pr(h, DDPS_PROF_BLOCK_SOLVE, s);
   launch_permute_in<T>(y, h->perm, A.n, w, s);
   for (int L = A.nlevels - 1; L >= 0; --L)
     launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
@@ -265,6 +337,7 @@ void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
 
 template <typename TG, typename TI>
 void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
+  Prof pr(h, DDPS_PROF_GHAT_MATVEC, s);
   launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
                              h->gcols, (int64_t)h->A.c.size(), v, w, s);
   h->launches++;
@@ -462,6 +535,7 @@ ddps_status solve_impl(ddps_handle* h, const double* f, double* x, cudaStream_t 
   const int ns = h->nseg;
   KScal* sc = h->sc_out;
   auto spmv = [&](const double* in, double* out) {
+    Prof pr(h, DDPS_PROF_SPMV, s);
     launch_spmv(h->rowptr, h->colind, h->vals, n, in, out, s);
     h->launches++;
   };
@@ -691,10 +765,37 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     int64_t nr = h->opt.rhs_chunk > 0 ? h->opt.rhs_chunk : 1024;
     nr = std::min<int64_t>(nr, ((A.max_rhs + 31) / 32) * 32);
     const int64_t budget = (int64_t)12 << 30;  // bytes for the two panels
-    while (nr > 32 && (n + A.upd_size) * nr * (int64_t)fs > budget) nr /= 2;
+    while (nr > 32 && (n + (int64_t)A.idx.size()) * nr * (int64_t)fs > budget) nr /= 2;
     h->NR = (int32_t)std::max<int64_t>(32, (nr / 32) * 32);
     h->X = dalloc_bytes(h, n * h->NR * (int64_t)fs);
-    h->U = dalloc_bytes(h, std::max<int64_t>(A.upd_size, 1) * h->NR * (int64_t)fs);
+    h->U = dalloc_bytes(h, std::max<int64_t>((int64_t)A.idx.size(), 1) * h->NR * (int64_t)fs);
+  }
+  for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
+  {
+    const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();
+    std::vector<int32_t> kf, km, rf, rm;
+    h->tk_ptr.assign(1, 0);
+    h->tr_ptr.assign(1, 0);
+    for (int L = 0; L < A.nlevels; ++L) {
+      for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+        const int32_t f = A.level_fronts[q];
+        const int32_t kk = A.f_k[f], rr = A.f_m[f] - A.f_k[f];
+        for (int32_t m0 = 0; m0 < kk; m0 += BM) {
+          kf.push_back(f);
+          km.push_back(m0);
+        }
+        for (int32_t m0 = 0; m0 < rr; m0 += BM) {
+          rf.push_back(f);
+          rm.push_back(m0);
+        }
+      }
+      h->tk_ptr.push_back((int32_t)kf.size());
+      h->tr_ptr.push_back((int32_t)rf.size());
+    }
+    h->tk_front = dupload(h, kf);
+    h->tk_m0 = dupload(h, km);
+    h->tr_front = dupload(h, rf);
+    h->tr_m0 = dupload(h, rm);
   }
   // segments
   h->nseg = A.nsys;
@@ -1059,6 +1160,7 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
 
 ddps_status ddps_destroy(ddps_handle* h) {
   if (!h) return DDPS_OK;
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->herr) cudaFreeHost(h->herr);
   if (h->hsc_out) cudaFreeHost(h->hsc_out);
@@ -1087,6 +1189,30 @@ const char* ddps_status_string(ddps_status s) {
 }
 
 int64_t ddps_launch_count(const ddps_handle* h) { return h ? h->launches : 0; }
+
+ddps_status ddps_set_profiling(ddps_handle* h, int32_t mask) {
+  if (!h) return DDPS_ERR_INVALID_ARG;
+  h->prof_mask = mask;
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_profile(ddps_handle* h, double* ms, int64_t* count, int32_t reset) {
+  if (!h) return DDPS_ERR_INVALID_ARG;
+  try {
+    prof_collect(h);
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  for (int c = 0; c < DDPS_PROF_CLASSES; ++c) {
+    if (ms) ms[c] = h->prof_ms[c];
+    if (count) count[c] = h->prof_cnt[c];
+    if (reset) {
+      h->prof_ms[c] = 0;
+      h->prof_cnt[c] = 0;
+    }
+  }
+  return DDPS_OK;
+}
 
 ddps_status ddps_symbolic(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
                           int32_t p, const int64_t* block_ptr, int32_t nsys,

@@ -213,93 +213,41 @@ __global__ void k_spike_rhs(const int32_t* __restrict__ rt_rownew, const int32_t
   }
 }
 
-// Multi-RHS forward substitution, one front per CTA row, 32 panel columns per
-// CTA (one per lane); warps stride over front rows.  The panel holds the
-// right-hand sides on entry and L^-1 of them on the pivot rows on exit; the
-// front's update rows go to U for the parent to extend-add.
+// In-place inversion of the diagonal block of each front after its partial
+// LU: the strictly lower part (unit L11) becomes that of L11^-1 and the upper
+// part with the diagonal becomes U11^-1.  The triangular solves of the block
+// solves and of the spikes then become products with these inverses.
+//   L^-1(i,j) = -( L(i,j) + sum_{j<l<i} L^-1(i,l) L(l,j) ),  columns j descending;
+//   U^-1(i,j) = -( sum_{i<=l<j} U^-1(i,l) U(l,j) ) / U(j,j),  columns j ascending.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_fwd_multi(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
-                const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR, T* __restrict__ X,
-                T* __restrict__ U) {
+    k_tri_inverse(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena) {
+  extern __shared__ unsigned char smem_raw[];
+  T* v = reinterpret_cast<T*>(smem_raw);
   const int32_t f = list[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const int col = blockIdx.y * 32 + lane;
-  const int64_t ncols = block_ncols[F.block[f]] - j0;
-  if ((int64_t)blockIdx.y * 32 >= ncols || blockIdx.y * 32 >= NR) return;
-  const bool act = col < NR && col < ncols;
-  const int32_t k = F.k[f], m = F.m[f], r = m - k;
-  const T* __restrict__ A = arena + F.arena[f];
-  T* __restrict__ Xf = X + F.row0[f] * NR;
-  T* __restrict__ Uf = U + F.upd[f] * NR;
-  for (int i = warp; i < r; i += nw)
-    if (act) Uf[(int64_t)i * NR + col] = T(0);
-  __syncthreads();
-  for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
-    const int32_t c = F.children[ci];
-    const int32_t rc = F.m[c] - F.k[c];
-    const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
-    const T* __restrict__ Uc = U + F.upd[c] * NR;
-    for (int i = warp; i < rc; i += nw) {
-      if (!act) continue;
-      const int32_t pr = rel[i];
-      const T v = Uc[(int64_t)i * NR + col];
-      if (pr < k)
-        Xf[(int64_t)pr * NR + col] += v;
-      else
-        Uf[(int64_t)(pr - k) * NR + col] += v;
+  const int32_t k = F.k[f], m = F.m[f];
+  T* __restrict__ A = arena + F.arena[f];
+  const int tid = threadIdx.x;
+  for (int j = k - 2; j >= 0; --j) {
+    for (int i = j + 1 + tid; i < k; i += blockDim.x) v[i] = A[i + (int64_t)j * m];
+    __syncthreads();
+    for (int i = j + 1 + tid; i < k; i += blockDim.x) {
+      T s = v[i];
+      for (int l = j + 1; l < i; ++l) s += A[i + (int64_t)l * m] * v[l];
+      A[i + (int64_t)j * m] = -s;
     }
     __syncthreads();
   }
   for (int j = 0; j < k; ++j) {
-    const T yj = act ? Xf[(int64_t)j * NR + col] : T(0);
-    const T* __restrict__ Lj = A + (int64_t)j * m;
-    for (int i = j + 1 + warp; i < m; i += nw) {
-      if (!act) continue;
-      const T l = Lj[i];
-      if (i < k)
-        Xf[(int64_t)i * NR + col] -= l * yj;
-      else
-        Uf[(int64_t)(i - k) * NR + col] -= l * yj;
-    }
+    for (int i = tid; i <= j; i += blockDim.x) v[i] = A[i + (int64_t)j * m];
     __syncthreads();
-  }
-}
-
-// Multi-RHS backward substitution: x_piv = U11^-1 (y_piv - U12 x_upd), where
-// x_upd are final values of ancestor pivots, read from the panel.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_bwd_multi(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
-                const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR, T* __restrict__ X) {
-  const int32_t f = list[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const int col = blockIdx.y * 32 + lane;
-  const int64_t ncols = block_ncols[F.block[f]] - j0;
-  if ((int64_t)blockIdx.y * 32 >= ncols || blockIdx.y * 32 >= NR) return;
-  const bool act = col < NR && col < ncols;
-  const int32_t k = F.k[f], m = F.m[f], r = m - k;
-  const T* __restrict__ A = arena + F.arena[f];
-  const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
-  T* __restrict__ Xf = X + F.row0[f] * NR;
-  if (act) {
-    for (int i = warp; i < k; i += nw) {
-      T acc = Xf[(int64_t)i * NR + col];
-      for (int j = 0; j < r; ++j) acc -= A[i + (int64_t)(k + j) * m] * X[(int64_t)idx[k + j] * NR + col];
-      Xf[(int64_t)i * NR + col] = acc;
+    const T d = v[j];
+    for (int i = tid; i < j; i += blockDim.x) {
+      T s = T(0);
+      for (int l = i; l < j; ++l) s += A[i + (int64_t)l * m] * v[l];
+      A[i + (int64_t)j * m] = -s / d;
     }
-  }
-  __syncthreads();
-  for (int j = k - 1; j >= 0; --j) {
-    const T* __restrict__ Uj = A + (int64_t)j * m;
-    const T xj = act ? Xf[(int64_t)j * NR + col] / Uj[j] : T(0);
-    __syncthreads();
-    if (act) {
-      if (warp == (j % nw)) Xf[(int64_t)j * NR + col] = xj;
-      for (int i = warp; i < j; i += nw) Xf[(int64_t)i * NR + col] -= Uj[i] * xj;
-    }
+    if (tid == 0) A[j + (int64_t)j * m] = T(1) / d;
     __syncthreads();
   }
 }
@@ -390,20 +338,13 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 }
 
 template <typename T>
-void launch_fwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
-                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, T* U,
-                      cudaStream_t s) {
+void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
+                        cudaStream_t s) {
   if (nf <= 0) return;
-  dim3 grid(nf, (NR + 31) / 32);
-  k_fwd_multi<T><<<grid, kThreads, 0, s>>>(F, list, arena, block_ncols, j0, NR, X, U);
-}
-
-template <typename T>
-void launch_bwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
-                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, cudaStream_t s) {
-  if (nf <= 0) return;
-  dim3 grid(nf, (NR + 31) / 32);
-  k_bwd_multi<T><<<grid, kThreads, 0, s>>>(F, list, arena, block_ncols, j0, NR, X);
+  const size_t sm = (size_t)std::max(max_k, 1) * sizeof(T);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_tri_inverse<T><<<nf, kThreads, sm, s>>>(F, list, arena);
 }
 
 template <typename T, typename TG>
@@ -423,10 +364,8 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
                                    double, long long*, cudaStream_t);                          \
   template void launch_spike_rhs<T>(const int32_t*, const int32_t*, const int64_t*, int64_t,   \
                                     const double*, int64_t, int32_t, T*, cudaStream_t);        \
-  template void launch_fwd_multi<T>(DevFronts, const int32_t*, int32_t, const T*,              \
-                                    const int64_t*, int64_t, int32_t, T*, T*, cudaStream_t);   \
-  template void launch_bwd_multi<T>(DevFronts, const int32_t*, int32_t, const T*,              \
-                                    const int64_t*, int64_t, int32_t, T*, cudaStream_t);
+  template void launch_tri_inverse<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,         \
+                                      cudaStream_t);
 
 DDPS_INST_T(double)
 DDPS_INST_T(float)

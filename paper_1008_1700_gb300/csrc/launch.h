@@ -50,12 +50,23 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
                       int64_t nrt, const double* values, int64_t j0, int32_t NR, T* X,
                       cudaStream_t s);
 template <typename T>
-void launch_fwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
-                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, T* U,
-                      cudaStream_t s);
+void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
+                        cudaStream_t s);
+
+// ---- spike.cu: multi-RHS forward/backward substitution as per-level GEMMs ----
+// Panel X (n x NR, row-major) holds the right-hand sides and receives the
+// solution on every pivot row; Tb (sum of front orders x NR) holds each
+// front's working rows (pivot part, then its update rows for the parent).
+enum SpikeOp { OP_FWD_LINV = 0, OP_FWD_L21 = 1, OP_BWD_U12 = 2, OP_BWD_UINV = 3 };
 template <typename T>
-void launch_bwd_multi(DevFronts F, const int32_t* list, int32_t nf, const T* arena,
-                      const int64_t* block_ncols, int64_t j0, int32_t NR, T* X, cudaStream_t s);
+int spike_tile_m();
+template <typename T>
+void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
+                         int64_t j0, int32_t NR, const T* X, T* Tb, cudaStream_t s);
+template <typename T>
+void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
+                       int32_t ntiles, const T* arena, const int64_t* block_ncols, int64_t j0,
+                       int32_t NR, T* X, T* Tb, cudaStream_t s);
 template <typename T, typename TG>
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, int64_t m, int64_t j0,

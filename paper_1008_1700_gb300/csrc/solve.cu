@@ -36,18 +36,20 @@ __global__ void k_permute_out(const T* __restrict__ w, const int32_t* __restrict
     g[perm[i]] = (double)w[i];
 }
 
-// Forward substitution with L (unit lower) for one front per CTA.  The front
-// vector t (m entries, shared memory) starts with the pivot entries of w and
-// zeros, receives the children's update vectors, is solved column by column;
-// the pivots go back to w and the update entries to u (for the parent).
+// Forward substitution for one front per CTA, with the inverse of the unit
+// lower diagonal block formed at factor time.  The front vector t (shared
+// memory) starts with the pivot entries of w and zeros and receives the
+// children's update vectors; then y = L11^-1 t(piv) goes back to w and the
+// update entries t(upd) - L21 y go to u for the parent.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_fwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
            T* __restrict__ w, T* __restrict__ u) {
   extern __shared__ unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);
+  T* t = reinterpret_cast<T*>(smem_raw);  // m entries
   const int32_t f = list[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
+  T* y = t + m;                           // k entries
   const T* __restrict__ A = arena + F.arena[f];
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
@@ -61,22 +63,22 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = tid; i < rc; i += blockDim.x) t[rel[i]] += uc[i];
     __syncthreads();
   }
-  for (int j = 0; j < k; ++j) {
-    const T yj = t[j];
-    const T* __restrict__ Lj = A + (int64_t)j * m;
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) t[i] -= Lj[i] * yj;
-    __syncthreads();
+  for (int i = tid; i < k; i += blockDim.x) {
+    T s = t[i];
+    for (int j = 0; j < i; ++j) s += A[i + (int64_t)j * m] * t[j];
+    y[i] = s;
   }
-  for (int i = tid; i < m; i += blockDim.x) {
-    if (i < k)
-      w[row0 + i] = t[i];
-    else
-      u[F.upd[f] + (i - k)] = t[i];
+  __syncthreads();
+  for (int i = k + tid; i < m; i += blockDim.x) {
+    T s = t[i];
+    for (int j = 0; j < k; ++j) s -= A[i + (int64_t)j * m] * y[j];
+    u[F.upd[f] + (i - k)] = s;
   }
+  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = y[i];
 }
 
-// Backward substitution for one front per CTA: x_piv = U11^-1 (y_piv - U12 x_upd),
-// x_upd read from w (ancestor pivots, already final).
+// Backward substitution for one front per CTA: x_piv = U11^-1 (y_piv - U12 x_upd)
+// with the inverse formed at factor time; x_upd are ancestor pivots of w.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_bwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
@@ -98,15 +100,11 @@ __global__ void __launch_bounds__(kThreads)
     t[i] = acc;
   }
   __syncthreads();
-  for (int j = k - 1; j >= 0; --j) {
-    const T* __restrict__ Uj = A + (int64_t)j * m;
-    const T xj = t[j] / Uj[j];
-    __syncthreads();
-    if (tid == (j % blockDim.x)) t[j] = xj;
-    for (int i = tid; i < j; i += blockDim.x) t[i] -= Uj[i] * xj;
-    __syncthreads();
+  for (int i = tid; i < k; i += blockDim.x) {
+    T s = T(0);
+    for (int j = i; j < k; ++j) s += A[i + (int64_t)j * m] * t[j];
+    w[row0 + i] = s;
   }
-  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = t[i];
 }
 
 // y = A x, CSR, four lanes per row.
@@ -227,7 +225,7 @@ template <typename T>
 void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, T* u, cudaStream_t s) {
   if (nf <= 0) return;
-  size_t sm = (size_t)max_m * sizeof(T);
+  size_t sm = (size_t)2 * max_m * sizeof(T);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_fwd1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_fwd1<T><<<nf, kThreads, sm, s>>>(F, list, arena, w, u);
 }

@@ -95,6 +95,8 @@ def load():
         "ddps_last_error": (C.c_char_p, [_p]),
         "ddps_status_string": (C.c_char_p, [_i32]),
         "ddps_launch_count": (_i64, [_p]),
+        "ddps_set_profiling": (_i32, [_p, _i32]),
+        "ddps_get_profile": (_i32, [_p, _p, _p, _i32]),
         "ddps_symbolic": (_i32, [_i64, _i64, _p, _p, _i32, _p, _i32, _p, _p,
                                  C.POINTER(ddps_options), C.POINTER(ddps_sizes), _p, _p]),
         "ddps_mlp_param_count": (_i64, [_i32, _i32, _i32, _i32]),
@@ -279,6 +281,22 @@ def ddps_get_ghat_block(h, b, stream=None):
 
 def ddps_launch_count(h):
     return int(load().ddps_launch_count(h))
+
+
+PROF_CLASSES = ["assemble", "extend_add", "front_lu", "spike_fwd", "spike_bwd", "ghat_extract",
+                "block_solve", "ghat_matvec", "spmv"]
+
+
+def ddps_set_profiling(h, mask):
+    _check(load().ddps_set_profiling(h, int(mask)), h)
+
+
+def ddps_get_profile(h, reset=True):
+    """{class: (milliseconds, launch groups)} since the last reset."""
+    ms = np.zeros(len(PROF_CLASSES))
+    cnt = np.zeros(len(PROF_CLASSES), dtype=np.int64)
+    _check(load().ddps_get_profile(h, _ptr(ms), _ptr(cnt), 1 if reset else 0), h)
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_CLASSES)}
 
 
 def ddps_destroy(h):

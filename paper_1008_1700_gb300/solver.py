@@ -120,6 +120,12 @@ class Solver:
     def ghat_block(self, b):
         return N.ddps_get_ghat_block(self.h, b)
 
+    def set_profiling(self, mask):
+        N.ddps_set_profiling(self.h, mask)
+
+    def profile(self, reset=True):
+        return N.ddps_get_profile(self.h, reset)
+
     def launch_count(self):
         return N.ddps_launch_count(self.h)
 
