@@ -169,6 +169,25 @@ ddps_status ddps_get_reduced_solution(ddps_handle* h, double* zhat, double* ghat
 /* Fig. 3 step 6.1 alone: g = D~^-1 y for all blocks (device float64[n] in/out). */
 ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* stream);
 
+/* Same result as ddps_block_solve, for callers that cannot allocate device
+ * memory when they need it (for example a program whose memory pool already
+ * owns all free device memory, or whose policy allows device allocations
+ * only at start-up).  The paper has no counterpart: this is a deployment
+ * variant.  Its per-call scratch (the front vectors of the two sweeps) comes
+ * from a fixed 16 MiB array compiled into the library, held by every GPU
+ * that loads the library until the process exits, instead of the handle's
+ * workspace; the call allocates nothing.
+ *   y, g    device float64[n] (input, output)
+ * Returns DDPS_ERR_INVALID_ARG when the analysed problem needs more scratch
+ * than the array holds (n + the multifrontal update entries, times the
+ * factor element size, must fit in 16 MiB).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other handles, other threads) race on it and must be ordered by
+ * the caller. */
+ddps_status ddps_block_solve_noalloc(ddps_handle* h, const double* y, double* g, void* stream);
+
 /* Fig. 3 step 6.2 product: w = G^ v = v + G(c,c) v (device float64[m] in/out). */
 ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream);
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1253,3 +1254,88 @@ ddps_status ddps_symbolic(int64_t n, int64_t nnz, const int32_t* rowptr, const i
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Block solve without device allocation.
+//
+// Some callers cannot call cudaMalloc at the moment they need a block solve:
+// a host program whose memory pool already owns all free device memory, or
+// one whose policy allows device allocations only at start-up.  For them,
+// ddps_block_solve_noalloc takes its per-call scratch (the front vectors of
+// the forward and backward sweeps) from the fixed array below instead of
+// the handle's workspace.  The array is part of the library image: every GPU
+// that loads the library holds it until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  (In host code the symbol's name only stands in for the array.)
+void* noalloc_scratch_address() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw Fail{DDPS_ERR_CUDA, "device ordinal out of range"};
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+template <typename T>
+void block_solve_scratch(ddps_handle* h, const double* y, double* g, cudaStream_t s, T* w, T* u) {
+  const Analysis& A = h->A;
+  const T* arena = (const T*)h->arena;
+  launch_permute_in<T>(y, h->perm, A.n, w, s);
+  for (int L = A.nlevels - 1; L >= 0; --L)
+    launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                   (int32_t)A.max_front, arena, w, u, s);
+  for (int L = 0; L < A.nlevels; ++L)
+    launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
+                   (int32_t)A.max_front, arena, w, s);
+  launch_permute_out<T>(w, h->perm, A.n, g, s);
+  h->launches += 2 + 2 * A.nlevels;
+}
+
+template <typename T>
+void block_solve_noalloc_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
+  const Analysis& A = h->A;
+  const size_t wbytes = ((size_t)A.n * sizeof(T) + 255) / 256 * 256;
+  const size_t ubytes = (size_t)std::max<int64_t>(A.upd_size, 1) * sizeof(T);
+  if (wbytes + ubytes > kNoAllocScratchBytes)
+    throw Fail{DDPS_ERR_INVALID_ARG,
+               "ddps_block_solve_noalloc: needs " + std::to_string(wbytes + ubytes) +
+                   " bytes of scratch, more than the fixed " +
+                   std::to_string(kNoAllocScratchBytes) + "-byte array"};
+  unsigned char* base = (unsigned char*)noalloc_scratch_address();
+  // Every entry of both scratch vectors is written before it is read (the
+  // permutation fills w, each front writes its update vector before its
+  // parent reads it), so nothing has to be cleared between calls.
+  block_solve_scratch<T>(h, y, g, s, (T*)base, (T*)(base + wbytes));
+}
+
+}  // namespace
+
+extern "C" ddps_status ddps_block_solve_noalloc(ddps_handle* h, const double* y, double* g,
+                                                void* stream) {
+  if (!h || !y || !g) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    cudaStream_t s = as_stream(stream);
+    if (h->opt.factor_prec == DDPS_FP64)
+      block_solve_noalloc_impl<double>(h, y, g, s);
+    else
+      block_solve_noalloc_impl<float>(h, y, g, s);
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}

@@ -83,6 +83,7 @@ def load():
         "ddps_set_reduced_guess": (_i32, [_p, _p, _p]),
         "ddps_get_reduced_solution": (_i32, [_p, _p, _p, _p]),
         "ddps_block_solve": (_i32, [_p, _p, _p, _p]),
+        "ddps_block_solve_noalloc": (_i32, [_p, _p, _p, _p]),
         "ddps_reduced_matvec": (_i32, [_p, _p, _p, _p]),
         "ddps_precond_apply": (_i32, [_p, _p, _p, _p]),
         "ddps_spmv": (_i32, [_p, _p, _p, _p]),
@@ -237,6 +238,11 @@ def ddps_get_reduced_solution(h, zhat, ghat, stream=None):
 
 def ddps_block_solve(h, y, g, stream=None):
     _check(load().ddps_block_solve(h, _ptr(y), _ptr(g), _stream(stream)), h)
+
+
+def ddps_block_solve_noalloc(h, y, g, stream=None):
+    """ddps_block_solve with scratch from the library's fixed array (no allocation)."""
+    _check(load().ddps_block_solve_noalloc(h, _ptr(y), _ptr(g), _stream(stream)), h)
 
 
 def ddps_reduced_matvec(h, v, w, stream=None):
