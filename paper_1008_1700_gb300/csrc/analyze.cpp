@@ -546,6 +546,7 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
   A.gq1.resize(p);
   A.gcol_ptr.assign(p + 1, 0);
   A.ghat_off.assign(p + 1, 0);
+  A.gld.assign(p, 0);
   std::vector<std::vector<int32_t>> bcols(p);
   for (int32_t b = 0; b < p; ++b) {
     int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
@@ -559,14 +560,17 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     A.gq1[b] = std::lower_bound(A.c.begin(), A.c.end(), r1) - A.c.begin();
     A.gcol_ptr[b + 1] = A.gcol_ptr[b] + (int64_t)cols.size();
     A.gcols.insert(A.gcols.end(), cols.begin(), cols.end());
-    A.ghat_off[b + 1] = A.ghat_off[b] + (A.gq1[b] - A.gq0[b]) * (int64_t)cols.size();
+    // rows are padded to a multiple of 8 entries so that every row starts on a
+    // 16-byte boundary in every storage precision
+    A.gld[b] = ((int64_t)cols.size() + 7) / 8 * 8;
+    A.ghat_off[b + 1] = A.ghat_off[b] + (A.gq1[b] - A.gq0[b]) * A.gld[b];
+    A.ghat_entries += (A.gq1[b] - A.gq0[b]) * (int64_t)cols.size();
     A.max_rhs = std::max<int64_t>(A.max_rhs, (int64_t)cols.size());
     double blk_lu = 0;
     for (int32_t f = 0; f < nf; ++f)
       if (A.f_block[f] == b) blk_lu += (double)A.f_k[f] * (2.0 * A.f_m[f] - A.f_k[f]);
     A.spike_flops += 4.0 * blk_lu * (double)cols.size();
   }
-  A.ghat_entries = A.ghat_off[p];
   for (int64_t i = 0; i < n; ++i) {
     int32_t b = row_block[i];
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <exception>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -77,7 +78,12 @@ struct ddps_handle {
   // reduced system
   int64_t* c = nullptr;
   int32_t *c_rownew = nullptr, *qblock = nullptr, *gcols = nullptr;
-  int64_t *gq0 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr, *block_ncols = nullptr;
+  int64_t *gq0 = nullptr, *gq1 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr,
+          *gld = nullptr, *block_ncols = nullptr;
+  // tiles of the G^ product: (block, first row) per 64 reduced rows
+  int32_t *mv_block = nullptr, *mv_row = nullptr;
+  int32_t mv_ntiles = 0;
+  int64_t mv_max_cols = 0;
   void* ghat = nullptr;
   // spike panels: X (n x NR) and the fronts' working rows (sum of m x NR)
   void* X = nullptr;
@@ -87,6 +93,11 @@ struct ddps_handle {
   // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
   int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
   std::vector<int32_t> tk_ptr, tr_ptr;
+  // tensor-core spikes: A operands packed as bf16 blocks, byte offsets per op and tile
+  unsigned char* atc = nullptr;
+  int64_t* tc_aoff[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t tc_max_kt[4] = {0, 0, 0, 0};
+  int tc_passes = 0;
   // segments
   SegView Sn{}, Sm{};
   int32_t nseg = 0;
@@ -227,6 +238,23 @@ void check_launch() {
   if (e != cudaSuccess) throw Fail{DDPS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
+// One spike GEMM op over a tile list: tensor cores for FP32 factors with
+// bf16 spike products, SIMT otherwise.
+template <typename T>
+void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, int32_t first,
+              int32_t nt, const T* arena, int64_t j0, T* X, T* Tb, cudaStream_t s) {
+  tf += first;
+  tm += first;
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->tc_passes) {
+      launch_spike_gemm_tc(op, h->tc_passes, h->F, tf, tm, h->tc_aoff[op] + first, h->atc, nt,
+                           h->block_ncols, j0, h->NR, X, Tb, h->derr, s);
+      return;
+    }
+  }
+  launch_spike_gemm<T>(op, h->F, tf, tm, nt, arena, h->block_ncols, j0, h->NR, X, Tb, s);
+}
+
 // ---------------------------------------------------------------------------
 // Fig. 2 steps 2 and 4 on the device
 // ---------------------------------------------------------------------------
@@ -263,6 +291,19 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
   launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
   h->launches++;
   const int64_t m = (int64_t)A.c.size();
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->tc_passes && m > 0) {  // pack the four A operands of every front for the tensor cores
+      Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
+      for (int op = 0; op < 4; ++op) {
+        const bool r_tiles = op == OP_FWD_L21;
+        launch_tc_pack_a(op, h->tc_passes, h->F, r_tiles ? h->tr_front : h->tk_front,
+                         r_tiles ? h->tr_m0 : h->tk_m0, h->tc_aoff[op],
+                         r_tiles ? h->tr_ptr.back() : h->tk_ptr.back(), h->tc_max_kt[op], arena,
+                         h->atc, s);
+        h->launches++;
+      }
+    }
+  }
   if (m > 0) {
     T* X = (T*)h->X;
     T* Tb = (T*)h->U;
@@ -275,29 +316,31 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
         Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
         launch_spike_gather<T>(h->F, h->level_fronts + A.level_ptr[L],
                                A.level_ptr[L + 1] - A.level_ptr[L], h->block_ncols, j0, NR, X, Tb, s);
-        launch_spike_gemm<T>(OP_FWD_LINV, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
-                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
-        launch_spike_gemm<T>(OP_FWD_L21, h->F, h->tr_front + h->tr_ptr[L], h->tr_m0 + h->tr_ptr[L],
-                             h->tr_ptr[L + 1] - h->tr_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        spike_op<T>(h, OP_FWD_LINV, h->tk_front, h->tk_m0, h->tk_ptr[L],
+                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
+        spike_op<T>(h, OP_FWD_L21, h->tr_front, h->tr_m0, h->tr_ptr[L],
+                    h->tr_ptr[L + 1] - h->tr_ptr[L], arena, j0, X, Tb, s);
         h->launches += 3;
       }
       for (int L = 0; L < A.nlevels; ++L) {
         Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
-        launch_spike_gemm<T>(OP_BWD_U12, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
-                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
-        launch_spike_gemm<T>(OP_BWD_UINV, h->F, h->tk_front + h->tk_ptr[L], h->tk_m0 + h->tk_ptr[L],
-                             h->tk_ptr[L + 1] - h->tk_ptr[L], arena, h->block_ncols, j0, NR, X, Tb, s);
+        spike_op<T>(h, OP_BWD_U12, h->tk_front, h->tk_m0, h->tk_ptr[L],
+                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
+        spike_op<T>(h, OP_BWD_UINV, h->tk_front, h->tk_m0, h->tk_ptr[L],
+                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
         h->launches += 2;
       }
       Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
-      launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, m, j0, NR,
-                                 X, (TG*)h->ghat, s);
+      launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, h->gld,
+                                 m, j0, NR, X, (TG*)h->ghat, s);
       h->launches++;
     }
   }
   check_launch();
   CK(cudaMemcpyAsync(h->herr, h->derr, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (h->herr[0] == 2)
+    throw Fail{DDPS_ERR_TIMEOUT, "a bounded wait of the tensor-core spike products gave up"};
   if (h->herr[0] != 0) {
     const int64_t row_new = h->herr[2];
     const int64_t row_old = h->A.perm[row_new];
@@ -339,8 +382,17 @@ void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
 template <typename TG, typename TI>
 void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
   Prof pr(h, DDPS_PROF_GHAT_MATVEC, s);
-  launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
-                             h->gcols, (int64_t)h->A.c.size(), v, w, s);
+  using AT = typename std::conditional<std::is_same<TG, double>::value, double, float>::type;
+  if (h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024) {
+    // every block owning reduced rows has tiles (a block without coupling
+    // columns gets w = v on its rows)
+    launch_ghat_matvec_tiled<TG, TI>((const TG*)h->ghat, h->mv_block, h->mv_row, h->mv_ntiles,
+                                     h->mv_max_cols, h->gq0, h->gq1, h->gcol_ptr, h->ghat_off,
+                                     h->gld, h->gcols, v, w, s);
+  } else {
+    launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
+                               h->gld, h->gcols, (int64_t)h->A.c.size(), v, w, s);
+  }
   h->launches++;
 }
 
@@ -756,18 +808,40 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   }
   h->qblock = dupload(h, qblock);
   h->gq0 = dupload(h, A.gq0);
+  h->gq1 = dupload(h, A.gq1);
   h->gcol_ptr = dupload(h, A.gcol_ptr);
   h->ghat_off = dupload(h, A.ghat_off);
+  h->gld = dupload(h, A.gld);
+  {
+    std::vector<int32_t> tb, tr;
+    for (int32_t b = 0; b < A.p; ++b) {
+      const int64_t nc = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
+      h->mv_max_cols = std::max(h->mv_max_cols, nc);
+      for (int64_t r = 0; r < A.gq1[b] - A.gq0[b]; r += 64) {
+        tb.push_back(b);
+        tr.push_back((int32_t)r);
+      }
+    }
+    h->mv_ntiles = (int32_t)tb.size();
+    h->mv_block = dupload(h, tb);
+    h->mv_row = dupload(h, tr);
+  }
   h->gcols = dupload(h, A.gcols);
   h->block_ncols = dupload(h, ncols);
-  h->ghat = dalloc_bytes(h, std::max<int64_t>(A.ghat_entries, 1) * (int64_t)prec_size(h->opt.ghat_prec));
+  {
+    const int64_t gbytes = std::max<int64_t>(A.ghat_off[A.p], 1) * (int64_t)prec_size(h->opt.ghat_prec);
+    h->ghat = dalloc_bytes(h, gbytes);
+    CK(cudaMemset(h->ghat, 0, gbytes));  // the row padding stays zero
+  }
   // spike panels: NR right-hand sides per pass
   if (m > 0) {
+    // NR: a multiple of 128 columns (the panel kernels move 128-column groups)
     int64_t nr = h->opt.rhs_chunk > 0 ? h->opt.rhs_chunk : 1024;
-    nr = std::min<int64_t>(nr, ((A.max_rhs + 31) / 32) * 32);
+    nr = std::min<int64_t>(nr, (A.max_rhs + 127) / 128 * 128);
+    nr = std::max<int64_t>(128, nr / 128 * 128);
     const int64_t budget = (int64_t)12 << 30;  // bytes for the two panels
-    while (nr > 32 && (n + (int64_t)A.idx.size()) * nr * (int64_t)fs > budget) nr /= 2;
-    h->NR = (int32_t)std::max<int64_t>(32, (nr / 32) * 32);
+    while (nr > 128 && (n + (int64_t)A.idx.size()) * nr * (int64_t)fs > budget) nr = (nr / 2 + 127) / 128 * 128;
+    h->NR = (int32_t)nr;
     h->X = dalloc_bytes(h, n * h->NR * (int64_t)fs);
     h->U = dalloc_bytes(h, std::max<int64_t>((int64_t)A.idx.size(), 1) * h->NR * (int64_t)fs);
   }
@@ -797,6 +871,27 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->tk_m0 = dupload(h, km);
     h->tr_front = dupload(h, rf);
     h->tr_m0 = dupload(h, rm);
+    const int sp = h->opt.spike_prec;
+    if ((sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0) {
+      h->tc_passes = sp == DDPS_BF16X3 ? 3 : 1;
+      const int BK = tc_tile_bk();
+      const int64_t bb = tc_a_block_bytes(h->tc_passes);
+      int64_t run = 0;
+      for (int op = 0; op < 4; ++op) {
+        const std::vector<int32_t>& tf = op == OP_FWD_L21 ? rf : kf;
+        std::vector<int64_t> off(tf.size());
+        for (size_t t = 0; t < tf.size(); ++t) {
+          const int32_t kk = A.f_k[tf[t]], rr = A.f_m[tf[t]] - kk;
+          const int32_t K = op == OP_BWD_U12 ? rr : kk;
+          const int32_t nk = (K + BK - 1) / BK;
+          off[t] = run;
+          run += nk * bb;
+          h->tc_max_kt[op] = std::max(h->tc_max_kt[op], nk);
+        }
+        h->tc_aoff[op] = dupload(h, off);
+      }
+      h->atc = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(run, 16));
+    }
   }
   // segments
   h->nseg = A.nsys;
@@ -840,8 +935,13 @@ bool valid_options(const ddps_options& o, std::string& why) {
     why = "an FP64 G^ needs FP64 inner vectors";
     return false;
   }
-  if (o.spike_prec != o.factor_prec) {
-    why = "spike_prec must equal factor_prec (the spike panel is solved with the block factors)";
+  const bool tc = o.spike_prec == DDPS_BF16 || o.spike_prec == DDPS_BF16X3;
+  if (tc && o.factor_prec != DDPS_FP32) {
+    why = "bf16 spike products need FP32 factors";
+    return false;
+  }
+  if (!tc && o.spike_prec != o.factor_prec) {
+    why = "spike_prec must equal factor_prec, or be BF16 / BF16X3 with FP32 factors";
     return false;
   }
   if (o.factor_prec == DDPS_FP32 && o.ghat_prec == DDPS_FP64) {
@@ -1125,34 +1225,37 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
   if (!h->factored) return DDPS_ERR_STATE;
   try {
     const Analysis& A = h->A;
-    const int64_t cnt = A.ghat_off[b + 1] - A.ghat_off[b];
-    if (cnt == 0) return DDPS_OK;
+    const int64_t rows = A.gq1[b] - A.gq0[b];
+    const int64_t nc = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
+    const int64_t ld = A.gld[b];
+    if (rows * nc == 0) return DDPS_OK;
     cudaStream_t s = as_stream(stream);
-    double* tmp = nullptr;
-    CK(cudaMalloc(&tmp, cnt * sizeof(double)));
     const int gp = h->opt.ghat_prec;
-    if (gp == DDPS_FP64)
-      CK(cudaMemcpyAsync(tmp, (const double*)h->ghat + A.ghat_off[b], cnt * sizeof(double),
-                         cudaMemcpyDeviceToDevice, s));
-    else if (gp == DDPS_FP32)
-      convert<double, float>(cnt, (const float*)h->ghat + A.ghat_off[b], tmp, s);
-    else {
-      std::vector<uint16_t> raw(cnt);
-      CK(cudaMemcpyAsync(raw.data(), (const __nv_bfloat16*)h->ghat + A.ghat_off[b], cnt * 2,
-                         cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      for (int64_t i = 0; i < cnt; ++i) {
-        uint32_t bits = (uint32_t)raw[i] << 16;
-        float fv;
-        std::memcpy(&fv, &bits, 4);
-        dst[i] = fv;
-      }
-      cudaFree(tmp);
-      return DDPS_OK;
-    }
-    CK(cudaMemcpyAsync(dst, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    const size_t es = prec_size(gp);
+    std::vector<unsigned char> raw((size_t)rows * ld * es);
+    CK(cudaMemcpyAsync(raw.data(), (const unsigned char*)h->ghat + A.ghat_off[b] * es, raw.size(),
+                       cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    cudaFree(tmp);
+    for (int64_t i = 0; i < rows; ++i)
+      for (int64_t j = 0; j < nc; ++j) {
+        const unsigned char* e = raw.data() + ((size_t)i * ld + j) * es;
+        double v;
+        if (gp == DDPS_FP64) {
+          std::memcpy(&v, e, 8);
+        } else if (gp == DDPS_FP32) {
+          float fv;
+          std::memcpy(&fv, e, 4);
+          v = fv;
+        } else {
+          uint16_t hb;
+          std::memcpy(&hb, e, 2);
+          uint32_t bits = (uint32_t)hb << 16;
+          float fv;
+          std::memcpy(&fv, &bits, 4);
+          v = fv;
+        }
+        dst[i * nc + j] = v;
+      }
   } catch (const Fail& e) {
     return fail(h, e);
   }

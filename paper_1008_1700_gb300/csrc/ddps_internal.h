@@ -48,7 +48,7 @@ struct Analysis {
   std::vector<int64_t> sys_c_ptr;    // nsys+1
   std::vector<int32_t> c_rownew;     // new index of row c[q]
   // Layout of G^ per block: rows [gq0, gq1) of the reduced system, coupling columns.
-  std::vector<int64_t> gq0, gq1, gcol_ptr, ghat_off;
+  std::vector<int64_t> gq0, gq1, gcol_ptr, ghat_off, gld;  // gld: row stride (multiple of 8)
   std::vector<int32_t> gcols;        // reduced indices of the coupling columns (ascending)
   int64_t ghat_entries = 0, max_rhs = 0, max_front = 0, factor_lu_entries = 0;
   double factor_flops = 0, spike_flops = 0;

@@ -63,14 +63,30 @@ int spike_tile_m();
 template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, cudaStream_t s);
+// spike_tc.cu: the same ops on the tensor cores (fp32 factors, bf16 operands,
+// fp32 accumulation); passes = 1 (hi*hi) or 3 (hi*hi + hi*lo + lo*hi).  A wait
+// that runs out writes error code 2 into err[0].
+// The A operands are packed once per factorisation (launch_tc_pack_a) into
+// bf16 blocks of 128 rows x tc_tile_bk() K-columns, tc_a_block_bytes(passes)
+// bytes each; tile_aoff[t] is the byte offset of tile t's first block.
+int tc_tile_bk();
+int64_t tc_a_block_bytes(int passes);
+void launch_tc_pack_a(int op, int passes, DevFronts F, const int32_t* tile_front,
+                      const int32_t* tile_m0, const int64_t* tile_aoff, int32_t ntiles,
+                      int32_t max_kt, const float* arena, unsigned char* atc, cudaStream_t s);
+void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_front,
+                          const int32_t* tile_m0, const int64_t* tile_aoff,
+                          const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,
+                          int64_t j0, int32_t NR, float* X, float* Tb, long long* err,
+                          cudaStream_t s);
 template <typename T>
 void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                        int32_t ntiles, const T* arena, const int64_t* block_ncols, int64_t j0,
                        int32_t NR, T* X, T* Tb, cudaStream_t s);
 template <typename T, typename TG>
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
-                         const int64_t* gcol_ptr, const int64_t* ghat_off, int64_t m, int64_t j0,
-                         int32_t NR, const T* X, TG* ghat, cudaStream_t s);
+                         const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
+                         int64_t m, int64_t j0, int32_t NR, const T* X, TG* ghat, cudaStream_t s);
 
 // ---- solve.cu ---------------------------------------------------------------
 template <typename T>
@@ -91,8 +107,16 @@ void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const d
                         cudaStream_t s);
 template <typename TG, typename TI>
 void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,
-                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int32_t* gcols,
-                        int64_t m, const TI* v, TI* w, cudaStream_t s);
+                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
+                        const int32_t* gcols, int64_t m, const TI* v, TI* w, cudaStream_t s);
+// Tiled G^ product: one CTA per (block, 64 reduced rows); needs max_cols
+// entries of shared memory for the block's gathered vector.
+template <typename TG, typename TI>
+void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
+                              int32_t ntiles, int64_t max_cols, const int64_t* gq0,
+                              const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
+                              const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
+                              cudaStream_t s);
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s);
 void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_t nrt,
                              double* rt_val, cudaStream_t s);

@@ -144,6 +144,15 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
 
+template <typename AT, typename TG>
+__device__ __forceinline__ AT to_acc(TG v) {
+  return (AT)v;
+}
+template <>
+__device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
 template <typename TG>
 struct Acc {
   using type = float;
@@ -158,7 +167,7 @@ struct Acc<double> {
 template <typename TG, typename TI>
 __global__ void k_ghat_matvec(const TG* __restrict__ ghat, const int32_t* __restrict__ qblock,
                               const int64_t* __restrict__ gq0, const int64_t* __restrict__ gcol_ptr,
-                              const int64_t* __restrict__ ghat_off,
+                              const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
                               const int32_t* __restrict__ gcols, int64_t m,
                               const TI* __restrict__ v, TI* __restrict__ w) {
   using AT = typename Acc<TG>::type;
@@ -168,7 +177,7 @@ __global__ void k_ghat_matvec(const TG* __restrict__ ghat, const int32_t* __rest
     const int32_t b = qblock[q];
     const int64_t c0 = gcol_ptr[b];
     const int64_t nc = gcol_ptr[b + 1] - c0;
-    const TG* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * nc;
+    const TG* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * gld[b];
     const int32_t* __restrict__ cols = gcols + c0;
     AT s = 0;
     for (int64_t j = lane; j < nc; j += 32) s += (AT)to_f(row[j]) * (AT)v[cols[j]];
@@ -184,6 +193,7 @@ __global__ void k_ghat_matvec<double, double>(const double* __restrict__ ghat,
                                               const int64_t* __restrict__ gq0,
                                               const int64_t* __restrict__ gcol_ptr,
                                               const int64_t* __restrict__ ghat_off,
+                                              const int64_t* __restrict__ gld,
                                               const int32_t* __restrict__ gcols, int64_t m,
                                               const double* __restrict__ v,
                                               double* __restrict__ w) {
@@ -193,13 +203,129 @@ __global__ void k_ghat_matvec<double, double>(const double* __restrict__ ghat,
     const int32_t b = qblock[q];
     const int64_t c0 = gcol_ptr[b];
     const int64_t nc = gcol_ptr[b + 1] - c0;
-    const double* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * nc;
+    const double* __restrict__ row = ghat + ghat_off[b] + (q - gq0[b]) * gld[b];
     const int32_t* __restrict__ cols = gcols + c0;
     double s = 0;
     for (int64_t j = lane; j < nc; j += 32) s += row[j] * v[cols[j]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) w[q] = v[q] + s;
+  }
+}
+
+// w = v + G(c,c) v, tiled: one CTA per (block, up to 64 reduced rows).  The
+// block's gathered vector v(c_i) is staged once in shared memory (float for
+// FP32/BF16 storage, double for FP64); each warp streams whole rows of G^
+// with 16-byte loads (8 rows of a tile per warp, two rows in flight).
+template <typename TG>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<__nv_bfloat16> {
+  static constexpr int n = 8;
+};
+template <>
+struct Vec16<double> {
+  static constexpr int n = 2;
+};
+
+template <typename TG>
+__device__ __forceinline__ void load16(const TG* p, float* out);
+template <>
+__device__ __forceinline__ void load16<float>(const float* p, float* out) {
+  const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  out[0] = v.x;
+  out[1] = v.y;
+  out[2] = v.z;
+  out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, float* out) {
+  const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    out[2 * i] = __uint_as_float(w[i] << 16);
+    out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+template <typename TG, typename TI>
+__global__ void __launch_bounds__(256)
+    k_ghat_matvec_tiled(const TG* __restrict__ ghat, const int32_t* __restrict__ tile_block,
+                        const int32_t* __restrict__ tile_row, const int64_t* __restrict__ gq0,
+                        const int64_t* __restrict__ gq1, const int64_t* __restrict__ gcol_ptr,
+                        const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
+                        const int32_t* __restrict__ gcols,
+                        const TI* __restrict__ v, TI* __restrict__ w) {
+  using AT = typename Acc<TG>::type;
+  constexpr int VN = Vec16<TG>::n;
+  extern __shared__ unsigned char smem_raw[];
+  AT* xs = reinterpret_cast<AT*>(smem_raw);
+  const int32_t b = tile_block[blockIdx.x];
+  const int64_t r0 = tile_row[blockIdx.x];
+  const int64_t c0 = gcol_ptr[b];
+  const int64_t nc = gcol_ptr[b + 1] - c0;
+  const int64_t nrows = gq1[b] - gq0[b];
+  for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) xs[j] = (AT)v[gcols[c0 + j]];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TG* __restrict__ base = ghat + ghat_off[b];
+  const int64_t nvec = nc / VN;
+  for (int rr = warp * 2; rr < 64; rr += 16) {
+    const int64_t ra = r0 + rr, rb = r0 + rr + 1;
+    const bool va = ra < nrows, vb = rb < nrows;
+    const TG* __restrict__ pa = base + ra * gld[b];
+    const TG* __restrict__ pb = base + rb * gld[b];
+    AT sa = 0, sb = 0;
+    for (int64_t q = lane; q < nvec; q += 32) {
+      AT ga[VN], gb[VN];
+      if (va) {
+        if constexpr (sizeof(TG) == 8) {
+          const double2 t = __ldcs(reinterpret_cast<const double2*>(pa + q * VN));
+          ga[0] = t.x;
+          ga[1] = t.y;
+        } else {
+          float tmp[VN];
+          load16<TG>(pa + q * VN, tmp);
+#pragma unroll
+          for (int e = 0; e < VN; ++e) ga[e] = tmp[e];
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) sa += ga[e] * xs[q * VN + e];
+      }
+      if (vb) {
+        if constexpr (sizeof(TG) == 8) {
+          const double2 t = __ldcs(reinterpret_cast<const double2*>(pb + q * VN));
+          gb[0] = t.x;
+          gb[1] = t.y;
+        } else {
+          float tmp[VN];
+          load16<TG>(pb + q * VN, tmp);
+#pragma unroll
+          for (int e = 0; e < VN; ++e) gb[e] = tmp[e];
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) sb += gb[e] * xs[q * VN + e];
+      }
+    }
+    for (int64_t j = nvec * VN + lane; j < nc; j += 32) {  // ragged tail
+      if (va) sa += to_acc<AT>(pa[j]) * xs[j];
+      if (vb) sb += to_acc<AT>(pb[j]) * xs[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (lane == 0) {
+      const int64_t q0 = gq0[b];
+      if (va) w[q0 + ra] = (TI)((AT)v[q0 + ra] + sa);
+      if (vb) w[q0 + rb] = (TI)((AT)v[q0 + rb] + sb);
+    }
   }
 }
 
@@ -252,11 +378,27 @@ void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const d
 
 template <typename TG, typename TI>
 void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,
-                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int32_t* gcols,
-                        int64_t m, const TI* v, TI* w, cudaStream_t s) {
+                        const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
+                        const int32_t* gcols, int64_t m, const TI* v, TI* w, cudaStream_t s) {
   if (m <= 0) return;
   k_ghat_matvec<TG, TI><<<grid_for(m * 32, kThreads), kThreads, 0, s>>>(
-      ghat, qblock, gq0, gcol_ptr, ghat_off, gcols, m, v, w);
+      ghat, qblock, gq0, gcol_ptr, ghat_off, gld, gcols, m, v, w);
+}
+
+template <typename TG, typename TI>
+void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
+                              int32_t ntiles, int64_t max_cols, const int64_t* gq0,
+                              const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
+                              const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
+                              cudaStream_t s) {
+  if (ntiles <= 0) return;
+  using AT = typename Acc<TG>::type;
+  const size_t sm = (size_t)std::max<int64_t>(max_cols, 1) * sizeof(AT);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_ghat_matvec_tiled<TG, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+  k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, gq0, gq1,
+                                                       gcol_ptr, ghat_off, gld, gcols, v, w);
 }
 
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s) {
@@ -280,22 +422,25 @@ void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_
 DDPS_INST_S(double)
 DDPS_INST_S(float)
 
-template void launch_ghat_matvec<double, double>(const double*, const int32_t*, const int64_t*,
-                                                 const int64_t*, const int64_t*, const int32_t*,
-                                                 int64_t, const double*, double*, cudaStream_t);
-template void launch_ghat_matvec<float, double>(const float*, const int32_t*, const int64_t*,
-                                                const int64_t*, const int64_t*, const int32_t*,
-                                                int64_t, const double*, double*, cudaStream_t);
-template void launch_ghat_matvec<float, float>(const float*, const int32_t*, const int64_t*,
-                                               const int64_t*, const int64_t*, const int32_t*,
-                                               int64_t, const float*, float*, cudaStream_t);
-template void launch_ghat_matvec<__nv_bfloat16, float>(const __nv_bfloat16*, const int32_t*,
-                                                       const int64_t*, const int64_t*,
-                                                       const int64_t*, const int32_t*, int64_t,
-                                                       const float*, float*, cudaStream_t);
-template void launch_ghat_matvec<__nv_bfloat16, double>(const __nv_bfloat16*, const int32_t*,
-                                                        const int64_t*, const int64_t*,
-                                                        const int64_t*, const int32_t*, int64_t,
-                                                        const double*, double*, cudaStream_t);
+#define DDPS_INST_MV(TG, TI)                                                                     \
+  template void launch_ghat_matvec_tiled<TG, TI>(const TG*, const int32_t*, const int32_t*, int32_t, \
+                                                 int64_t, const int64_t*, const int64_t*,        \
+                                                 const int64_t*, const int64_t*, const int64_t*, \
+                                                 const int32_t*, const TI*, TI*, cudaStream_t);
+DDPS_INST_MV(double, double)
+DDPS_INST_MV(float, double)
+DDPS_INST_MV(float, float)
+DDPS_INST_MV(__nv_bfloat16, float)
+DDPS_INST_MV(__nv_bfloat16, double)
+
+#define DDPS_INST_MV0(TG, TI)                                                                    \
+  template void launch_ghat_matvec<TG, TI>(const TG*, const int32_t*, const int64_t*,           \
+                                           const int64_t*, const int64_t*, const int64_t*,      \
+                                           const int32_t*, int64_t, const TI*, TI*, cudaStream_t);
+DDPS_INST_MV0(double, double)
+DDPS_INST_MV0(float, double)
+DDPS_INST_MV0(float, float)
+DDPS_INST_MV0(__nv_bfloat16, float)
+DDPS_INST_MV0(__nv_bfloat16, double)
 
 }  // namespace ddps

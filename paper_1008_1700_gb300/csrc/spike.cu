@@ -33,28 +33,64 @@ struct Cfg<double> {
 };
 
 // T_f = [X rows of the pivots; 0] + sum over children of their update rows.
+// One CTA per (front, 32*V panel columns); each lane owns V consecutive
+// columns, the 8 warps stride over rows; children are added one after the
+// other (their row maps are injective, so rows of one child never collide).
+template <typename T>
+struct GatherVec;
+template <>
+struct GatherVec<float> {
+  using V = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct GatherVec<double> {
+  using V = double2;
+  static constexpr int n = 2;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_spike_gather(DevFronts F, const int32_t* __restrict__ list,
                    const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                    const T* __restrict__ X, T* __restrict__ Tb) {
+  using V = typename GatherVec<T>::V;
+  constexpr int VN = GatherVec<T>::n;
   const int32_t f = list[blockIdx.x];
   const int64_t ncols = min((int64_t)NR, block_ncols[F.block[f]] - j0);
-  const int col = blockIdx.y * blockDim.x + threadIdx.x;
-  if ((int64_t)blockIdx.y * blockDim.x >= ncols) return;
-  const bool act = col < ncols;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.y * 32 * VN;
+  if (c0 >= ncols) return;
+  const int col = c0 + lane * VN;  // NR is a multiple of 32 * VN: no column tail
   const int32_t k = F.k[f], m = F.m[f];
   T* __restrict__ Tf = Tb + F.idx_off[f] * NR;
   const T* __restrict__ Xf = X + F.row0[f] * NR;
-  if (act)
-    for (int i = 0; i < m; ++i) Tf[(int64_t)i * NR + col] = i < k ? Xf[(int64_t)i * NR + col] : T(0);
+  const V zero = {};
+  for (int i = warp; i < m; i += 8)
+    *reinterpret_cast<V*>(Tf + (int64_t)i * NR + col) =
+        i < k ? *reinterpret_cast<const V*>(Xf + (int64_t)i * NR + col) : zero;
+  __syncthreads();
   for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
     const int32_t c = F.children[ci];
     const int32_t kc = F.k[c], rc = F.m[c] - kc;
     const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
     const T* __restrict__ Tc = Tb + (F.idx_off[c] + kc) * NR;
-    if (act)
-      for (int i = 0; i < rc; ++i) Tf[(int64_t)rel[i] * NR + col] += Tc[(int64_t)i * NR + col];
+    for (int i = warp; i < rc; i += 8) {
+      V* dst = reinterpret_cast<V*>(Tf + (int64_t)rel[i] * NR + col);
+      const V src = *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col);
+      V d = *dst;
+      if constexpr (VN == 4) {
+        d.x += src.x;
+        d.y += src.y;
+        d.z += src.z;
+        d.w += src.w;
+      } else {
+        d.x += src.x;
+        d.y += src.y;
+      }
+      *dst = d;
+    }
+    __syncthreads();
   }
 }
 
@@ -179,7 +215,8 @@ template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, cudaStream_t s) {
   if (nf <= 0) return;
-  dim3 grid(nf, (NR + kThreads - 1) / kThreads);
+  const int per = 32 * GatherVec<T>::n;
+  dim3 grid(nf, (NR + per - 1) / per);
   k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb);
 }
 

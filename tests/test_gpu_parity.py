@@ -21,6 +21,11 @@ MIXED = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_F
              inner_prec=N.DDPS_FP32)
 MIXED_BF16 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_BF16,
                   inner_prec=N.DDPS_FP32)
+# spike products on the tensor cores (bf16 operands, fp32 accumulation)
+TC3 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP32,
+           inner_prec=N.DDPS_FP32)
+TC1 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16, ghat_prec=N.DDPS_BF16,
+           inner_prec=N.DDPS_FP32)
 
 
 def test_worked_example_on_gpu():
@@ -95,10 +100,24 @@ def test_precond_apply_direct_mode(case):
     assert relerr(z, zo) <= 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+@pytest.mark.parametrize("form,bound", [("mixed", 2e-6), ("tc3", 1e-4), ("tc1", 3e-2)])
+def test_ghat_precision_forms(case, form, bound):
+    """G^ formed with FP32 factors: SIMT FP32 products, bf16x3 and bf16 tensor-core
+    products; each within its arithmetic's accuracy of the FP64 oracle."""
+    name, P, drop, o = case
+    S = make_solver(P, drop, **{"mixed": MIXED, "tc3": TC3, "tc1": TC1}[form])
+    for b, ob in enumerate(o.blk):
+        q0, q1, cols = S.ghat_layout(b)
+        if (q1 - q0) * len(cols) == 0:
+            continue
+        scale = max(np.max(np.abs(ob["Ghat"])), 1e-300)
+        assert np.max(np.abs(S.ghat_block(b) - ob["Ghat"])) <= bound * scale, (name, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "tc3", "tc1"])
 def test_full_solve_parity(case, prec):
     name, P, drop, o = case
-    opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16}[prec]
+    opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "tc3": TC3, "tc1": TC1}[prec]
     S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **opts)
     x, info = S.solve(dev(P.f))
     assert info["status"] == "DDPS_OK", info
