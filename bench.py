@@ -11,8 +11,10 @@ preconditioner).  The symbolic analysis depends only on the sparsity
 pattern; it runs once before the timed region and is reported as
 ``analyze_ms``.
 
-Forms: ``mixed`` = FP32 block factors, spikes, G^ and inner vectors, FP64
-outer Krylov (the headline), ``fp64`` = plain FP64 DDPS.
+Forms: ``mixed`` = FP32 block factors and spike solves with the spike
+products on the tensor cores (bf16x3 operands, fp32 accumulation), FP32 G^
+and inner vectors, FP64 outer Krylov (the headline); ``mixed_simt`` = the
+same with FP32 SIMT spike products; ``fp64`` = plain FP64 DDPS.
 
 Under torchrun every rank solves its own copy of the workload (the systems
 are independent; no collective on the data path) and ``value`` counts the
@@ -45,7 +47,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cd3d_64_slabs16",
                     choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8"])
-    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64"], default="mixed")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="steps of the plain-FP64 comparison run (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -72,6 +74,11 @@ def form_options(form):
     from paper_1008_1700_gb300 import native as N
     base = dict(tol_out=1e-10, maxit_out=1000, tol_in=1e-4, maxit_in=100)
     if form == "mixed":
+        # FP32 block factors and spike solves, spike products on the tensor cores
+        # (bf16x3 operands, fp32 accumulation), FP32 G^ and inner vectors, FP64 outer
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP32,
+                    inner_prec=N.DDPS_FP32)
+    elif form == "mixed_simt":
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
                     inner_prec=N.DDPS_FP32)
     else:
@@ -86,9 +93,12 @@ def load_peaks():
         with open(path) as fh:
             pk = json.load(fh)
         return {"hbm_gbs": float(pk["hbm_gbs"]), "sm_max_mhz": float(pk.get("sm_max_mhz", 2070.0)),
+                "bf16_tflops": float(pk.get("bf16_tflops", 1900.0)),
+                "bf16_tflops_sustained": float(pk.get("bf16_tflops_sustained", 1700.0)),
                 "source": "measured"}
     except Exception:
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
 # ----------------------------------------------------------------------------
@@ -150,7 +160,7 @@ class ClockSampler:
 
 def algorithmic_work(sizes, P, form, steps, prof):
     """Per class: (kind, total algorithmic amount over the timed region)."""
-    sf = 4 if form == "mixed" else 8
+    sf = 8 if form == "fp64" else 4
     si = sf
     n, nnz, m = sizes["n"], sizes["nnz"], sizes["m"]
     out = {}
@@ -347,13 +357,19 @@ def run_ours(args):
         peak = peaks["hbm_gbs"]
         bound = "hbm"
         peak_note = f"{peaks['source']} HBM copy bandwidth"
+    elif args.form == "mixed" and dom in ("spike_fwd", "spike_bwd"):
+        # bf16 tensor-core products (3 passes per algorithmic product): sustained bf16 peak
+        peak = peaks["bf16_tflops_sustained"]
+        bound = "tensor"
+        peak_note = (f"{peaks['source']} sustained dense bf16 (cuBLAS); achieved counts the "
+                     "algorithmic flops once, the tensor cores run 3 bf16 passes")
     else:
         # FP32 (mixed) or FP64 (plain) SIMT: 152 SMs x lanes x 2 flops x max SM clock
-        lanes = 128 if args.form == "mixed" else 2
+        lanes = 2 if args.form == "fp64" else 128
         peak = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
         bound = "alu"
-        peak_note = ("FP32 SIMT: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz if args.form == "mixed"
-                     else "FP64: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz)
+        peak_note = ("FP64: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz if args.form == "fp64"
+                     else "FP32 SIMT: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz)
     roof = {"kernel": dom, "bound": bound, "achieved": dk["achieved"], "peak": round(peak, 2),
             "unit": dk["unit"], "frac": round(dk["achieved"] / peak, 4), "traffic": None,
             "peak_source": peak_note}
@@ -362,12 +378,13 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.form == "mixed" else "f64", "data": "synthetic",
+        "dtype": "f64" if args.form == "fp64" else ("bf16x3+f32+f64" if args.form == "mixed" else "f32+f64"),
+        "data": "synthetic",
         "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
                    "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
                    "form": args.form, "parallelism": f"replicas{world}",
                    "l2": "working set (G^ %.1f GB) larger than L2" %
-                         (sizes["ghat_entries"] * (4 if args.form == "mixed" else 8) / 1e9),
+                         (sizes["ghat_entries"] * (8 if args.form == "fp64" else 4) / 1e9),
                    "tol_out": opts["tol_out"], "tol_in": opts["tol_in"]},
         "analyze_ms": round(analyze_ms, 1),
         "accuracy": {"relres_inf": relres, "rel_err_vs_xtrue": err_xtrue, "converged": converged,
@@ -408,7 +425,7 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(P.n * 8)}
 
     # plain FP64 DDPS on the same GPU and workload (the comparison the metric names)
-    if args.form == "mixed" and args.fp64_steps > 0:
+    if args.form != "fp64" and args.fp64_steps > 0:
         S64 = Solver(P.rowptr, P.colind, P.block_ptr, **form_options("fp64"))
         x64 = torch.empty_like(f)
         S64.factor(vals)
