@@ -192,6 +192,12 @@ ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* s
  * the caller. */
 ddps_status ddps_block_solve_noalloc(ddps_handle* h, const double* y, double* g, void* stream);
 
+/* Fig. 3 steps 6.1-6.2: the reduced right-hand side g^ = (D~^-1 y)(c) that
+ * the first preconditioner application of a solve with f = y would see
+ * (y device float64[n], ghat device float64[m]).  A predictor of z^ can
+ * use it as a feature before the solve starts. */
+ddps_status ddps_reduced_rhs(ddps_handle* h, const double* y, double* ghat, void* stream);
+
 /* Fig. 3 step 6.2 product: w = G^ v = v + G(c,c) v (device float64[m] in/out). */
 ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream);
 

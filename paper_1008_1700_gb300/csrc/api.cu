@@ -1133,6 +1133,24 @@ ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* s
   return DDPS_OK;
 }
 
+ddps_status ddps_reduced_rhs(ddps_handle* h, const double* y, double* ghat, void* stream) {
+  if (!h || !y || (!h->A.c.empty() && !ghat)) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    cudaStream_t s = as_stream(stream);
+    block_solve(h, y, h->pc_g, s);
+    const int64_t m = (int64_t)h->A.c.size();
+    if (m) {
+      launch_gather(h->pc_g, h->c, m, ghat, s);
+      h->launches++;
+    }
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
 ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream) {
   if (!h || (!h->A.c.empty() && (!v || !w))) return DDPS_ERR_INVALID_ARG;
   if (!h->factored) return DDPS_ERR_STATE;

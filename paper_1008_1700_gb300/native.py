@@ -85,6 +85,7 @@ def load():
         "ddps_block_solve": (_i32, [_p, _p, _p, _p]),
         "ddps_block_solve_noalloc": (_i32, [_p, _p, _p, _p]),
         "ddps_reduced_matvec": (_i32, [_p, _p, _p, _p]),
+        "ddps_reduced_rhs": (_i32, [_p, _p, _p, _p]),
         "ddps_precond_apply": (_i32, [_p, _p, _p, _p]),
         "ddps_spmv": (_i32, [_p, _p, _p, _p]),
         "ddps_get_sizes": (_i32, [_p, C.POINTER(ddps_sizes)]),
@@ -243,6 +244,10 @@ def ddps_block_solve(h, y, g, stream=None):
 def ddps_block_solve_noalloc(h, y, g, stream=None):
     """ddps_block_solve with scratch from the library's fixed array (no allocation)."""
     _check(load().ddps_block_solve_noalloc(h, _ptr(y), _ptr(g), _stream(stream)), h)
+
+
+def ddps_reduced_rhs(h, y, ghat, stream=None):
+    _check(load().ddps_reduced_rhs(h, _ptr(y), _ptr(ghat), _stream(stream)), h)
 
 
 def ddps_reduced_matvec(h, v, w, stream=None):

@@ -83,6 +83,12 @@ class Solver:
         N.ddps_block_solve(self.h, y, g)
         return g
 
+    def reduced_rhs(self, y):
+        import torch
+        g = torch.empty(self.m, dtype=torch.float64, device=y.device)
+        N.ddps_reduced_rhs(self.h, y, g)
+        return g
+
     def reduced_matvec(self, v):
         import torch
         w = torch.empty_like(v)
