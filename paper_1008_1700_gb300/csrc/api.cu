@@ -113,6 +113,11 @@ struct ddps_handle {
        *i_v = nullptr, *i_s = nullptr, *i_t = nullptr;
   KScal *sc_out = nullptr, *sc_in = nullptr;
   KScal* hsc = nullptr;      // pinned host scalars of the loop being run (nseg)
+  // Uploads copy hsc into a slot of this pinned ring first, so that the host
+  // may change hsc right after enqueueing an upload; the ring restarts after
+  // every synchronising download.
+  KScal* hstage = nullptr;
+  int stage_next = 0;
   KScal* hsc_out = nullptr;  // pinned, outer loop
   KScal* hsc_in = nullptr;   // pinned, inner loop
   double* partial = nullptr;
@@ -396,12 +401,21 @@ void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
   h->launches++;
 }
 
+constexpr int kStageSlots = 16;
+
 void download_sc(ddps_handle* h, const KScal* d, cudaStream_t s) {
   CK(cudaMemcpyAsync(h->hsc, d, sizeof(KScal) * h->nseg, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  h->stage_next = 0;  // every earlier upload has completed
 }
 void upload_sc(ddps_handle* h, KScal* d, cudaStream_t s) {
-  CK(cudaMemcpyAsync(d, h->hsc, sizeof(KScal) * h->nseg, cudaMemcpyHostToDevice, s));
+  if (h->stage_next == kStageSlots) {
+    CK(cudaStreamSynchronize(s));
+    h->stage_next = 0;
+  }
+  KScal* slot = h->hstage + (size_t)h->stage_next++ * h->nseg;
+  std::memcpy(slot, h->hsc, sizeof(KScal) * h->nseg);
+  CK(cudaMemcpyAsync(d, slot, sizeof(KScal) * h->nseg, cudaMemcpyHostToDevice, s));
 }
 
 RedSpec red(const void* x, const void* y, int op, double* out) { return RedSpec{x, y, op, kScalStride, out}; }
@@ -914,6 +928,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   h->sc_in = dalloc<KScal>(h, h->nseg);
   CK(cudaMallocHost((void**)&h->hsc_out, sizeof(KScal) * h->nseg));
   CK(cudaMallocHost((void**)&h->hsc_in, sizeof(KScal) * h->nseg));
+  CK(cudaMallocHost((void**)&h->hstage, sizeof(KScal) * h->nseg * kStageSlots));
   h->hsc = h->hsc_out;
   h->partial = dalloc<double>(h, 3 * (int64_t)std::max(h->Sn.nchunks, h->Sm.nchunks) + 3);
 }
@@ -1287,6 +1302,7 @@ ddps_status ddps_destroy(ddps_handle* h) {
   if (h->herr) cudaFreeHost(h->herr);
   if (h->hsc_out) cudaFreeHost(h->hsc_out);
   if (h->hsc_in) cudaFreeHost(h->hsc_in);
+  if (h->hstage) cudaFreeHost(h->hstage);
   delete h;
   return DDPS_OK;
 }

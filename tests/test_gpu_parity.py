@@ -201,3 +201,31 @@ def test_reduced_guess_exact_and_rejected():
     x2, info2 = S.solve(dev(P.f))
     assert info2["guess_used"] == 0 and info2["status"] == "DDPS_OK"
     S.set_reduced_guess(None)
+
+
+def test_batch_every_system_meets_tolerance():
+    """A batch shaped like the 256-system workload (grid sides 32..80, 8 grid-line
+    blocks each): every system's recomputed residual meets tol_out, the reported
+    worst residual agrees, and sampled systems match the oracle."""
+    from paper_1008_1700_gb300 import Solver
+    sides = np.random.default_rng(11).integers(32, 81, 12)
+    probs = [W.small_convdiff_2d(int(N), 8, seed=1000 + k) for k, N in enumerate(sides)]
+    S = Solver.from_systems([(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs],
+                            tol_out=1e-10, tol_in=1e-4, **TC3)
+    S.factor(dev(S.values_host))
+    x, info = S.solve(dev(np.concatenate([p.f for p in probs])))
+    x = host(x)
+    worst = 0.0
+    for k, p in enumerate(probs):
+        xk = x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]]
+        A = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr, spikes=False).A
+        rr = np.max(np.abs(p.f - A @ xk)) / np.max(np.abs(p.f))
+        worst = max(worst, rr)
+        assert rr <= 1e-10, (k, rr)
+    assert info["status"] == "DDPS_OK" and info["converged"] == 1
+    assert abs(info["relres_inf"] - worst) <= 1e-3 * worst + 1e-18
+    for k in (0, 7):
+        p = probs[k]
+        xo, _ = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr).solve(
+            p.f, tol=1e-12, eps_in=1e-8)
+        assert relerr(x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]], xo) <= 1e-7
