@@ -84,6 +84,10 @@ typedef struct {
   int32_t leaf_size;      /* nested-dissection leaf size of the block ordering (0 = default) */
   int32_t rhs_chunk;      /* spike right-hand sides per pass (0 = chosen from free memory) */
   int32_t verbose;        /* 1: print analysis statistics to stderr */
+  int32_t debug_wait_timeout; /* 1: the tensor-core spike products first wait (bounded, about
+                                 4096 polls) on an mbarrier that nothing arrives at, so that the
+                                 wait runs out and ddps_factor returns DDPS_ERR_TIMEOUT; tests the
+                                 failure path.  0 in normal use. */
 } ddps_options;
 
 typedef struct {

@@ -45,6 +45,12 @@ size_t prec_size(int prec) { return prec == DDPS_FP64 ? 8 : (prec == DDPS_FP32 ?
 
 }  // namespace
 
+// Fronts of one depth reordered for the LU launches: `nsmall` fronts that fit
+// the shared-memory kernel, then `nlarge` others, starting at `first`.
+struct LevelSplit {
+  int32_t first = 0, nsmall = 0, nlarge = 0, max_small_m = 0;
+};
+
 struct ddps_handle {
   std::string err;
   ddps_options opt{};
@@ -90,6 +96,9 @@ struct ddps_handle {
   void* U = nullptr;
   int32_t NR = 0;
   int32_t max_k = 0;
+  // LU launch order per depth (see LevelSplit)
+  int32_t* lu_order = nullptr;
+  std::vector<LevelSplit> split;
   // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
   int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
   std::vector<int32_t> tk_ptr, tr_ptr;
@@ -253,7 +262,7 @@ void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, int3
   if constexpr (std::is_same<T, float>::value) {
     if (h->tc_passes) {
       launch_spike_gemm_tc(op, h->tc_passes, h->F, tf, tm, h->tc_aoff[op] + first, h->atc, nt,
-                           h->block_ncols, j0, h->NR, X, Tb, h->derr, s);
+                           h->block_ncols, j0, h->NR, X, Tb, h->derr, h->opt.debug_wait_timeout, s);
       return;
     }
   }
@@ -286,12 +295,20 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
         h->launches++;
       }
     }
-    const int32_t nf = A.level_ptr[L + 1] - A.level_ptr[L];
+    // fronts of this depth, small ones (shared-memory kernel) first, then the rest
     Prof pr(h, DDPS_PROF_FRONT_LU, s);
-    launch_front_lu<T>(h->F, h->level_fronts + A.level_ptr[L], nf, arena, h->rownorm,
-                       h->opt.pivot_tol, h->derr, s);
-    launch_tri_inverse<T>(h->F, h->level_fronts + A.level_ptr[L], nf, h->max_k, arena, s);
-    h->launches += 2;
+    const LevelSplit& ls = h->split[L];
+    if (ls.nsmall > 0) {
+      launch_front_lu_small<T>(h->F, h->lu_order + ls.first, ls.nsmall, ls.max_small_m, arena,
+                               h->rownorm, h->opt.pivot_tol, h->derr, s);
+      h->launches++;
+    }
+    if (ls.nlarge > 0) {
+      launch_front_lu<T>(h->F, h->lu_order + ls.first + ls.nsmall, ls.nlarge, arena, h->rownorm,
+                         h->opt.pivot_tol, h->derr, s);
+      launch_tri_inverse<T>(h->F, h->lu_order + ls.first + ls.nsmall, ls.nlarge, h->max_k, arena, s);
+      h->launches += 2;
+    }
   }
   launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
   h->launches++;
@@ -860,6 +877,31 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->U = dalloc_bytes(h, std::max<int64_t>((int64_t)A.idx.size(), 1) * h->NR * (int64_t)fs);
   }
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
+  {
+    const int small = h->opt.factor_prec == DDPS_FP64 ? small_front_max<double>() : small_front_max<float>();
+    std::vector<int32_t> order;
+    h->split.assign(A.nlevels, LevelSplit{});
+    for (int L = 0; L < A.nlevels; ++L) {
+      LevelSplit& ls = h->split[L];
+      ls.first = (int32_t)order.size();
+      for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+        const int32_t f = A.level_fronts[q];
+        if (A.f_m[f] <= small) {
+          order.push_back(f);
+          ls.nsmall++;
+          ls.max_small_m = std::max(ls.max_small_m, A.f_m[f]);
+        }
+      }
+      for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+        const int32_t f = A.level_fronts[q];
+        if (A.f_m[f] > small) {
+          order.push_back(f);
+          ls.nlarge++;
+        }
+      }
+    }
+    h->lu_order = dupload(h, order);
+  }
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();
     std::vector<int32_t> kf, km, rf, rm;

@@ -199,6 +199,78 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Small fronts (m*m entries fit in shared memory): partial LU and the
+// inversion of the diagonal triangles done in shared memory by one CTA, then
+// written back once.  Same arithmetic as k_front_lu followed by
+// k_tri_inverse, without the round trips through global memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_front_lu_small(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena,
+                     const double* __restrict__ rownorm, double pivot_tol,
+                     long long* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  T* __restrict__ G = arena + F.arena[f];
+  T* v = A + (int64_t)m * m;  // k scratch entries for the inversion
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < m * m; t += blockDim.x) A[t] = G[t];
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    T piv = A[j + j * m];
+    const double thr = pivot_tol * rownorm[row0 + j];
+    if (!(fabs((double)piv) > thr)) {
+      const double rep = thr > 0.0 ? thr : 1e-300;
+      piv = (T)((double)piv < 0.0 ? -rep : rep);
+      if (tid == 0 && atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+        err[1] = f;
+        err[2] = row0 + j;
+      }
+    }
+    __syncthreads();  // every thread has read the pivot before it is replaced
+    if (tid == 0) A[j + j * m] = piv;
+    const T inv = T(1) / piv;
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + j * m] *= inv;
+    __syncthreads();
+    const int nr = m - (j + 1);
+    for (int t = tid; t < nr * nr; t += blockDim.x) {
+      const int i = j + 1 + t % nr;
+      const int c = j + 1 + t / nr;
+      A[i + c * m] -= A[i + j * m] * A[j + c * m];
+    }
+    __syncthreads();
+  }
+  // L11^-1 (strictly lower part, unit diagonal), columns descending
+  for (int j = k - 2; j >= 0; --j) {
+    for (int i = j + 1 + tid; i < k; i += blockDim.x) v[i] = A[i + j * m];
+    __syncthreads();
+    for (int i = j + 1 + tid; i < k; i += blockDim.x) {
+      T s2 = v[i];
+      for (int l = j + 1; l < i; ++l) s2 += A[i + l * m] * v[l];
+      A[i + j * m] = -s2;
+    }
+    __syncthreads();
+  }
+  // U11^-1 (upper part with the diagonal), columns ascending
+  for (int j = 0; j < k; ++j) {
+    for (int i = tid; i <= j; i += blockDim.x) v[i] = A[i + j * m];
+    __syncthreads();
+    const T d = v[j];
+    for (int i = tid; i < j; i += blockDim.x) {
+      T s2 = T(0);
+      for (int l = i; l < j; ++l) s2 += A[i + l * m] * v[l];
+      A[i + j * m] = -s2 / d;
+    }
+    if (tid == 0) A[j + j * m] = T(1) / d;
+    __syncthreads();
+  }
+  for (int t = tid; t < m * m; t += blockDim.x) G[t] = A[t];
+}
+
+// ---------------------------------------------------------------------------
 // Spike right-hand sides: column j of block b's panel is R~_b(:, c_b[j]).
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -340,6 +412,17 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 }
 
 template <typename T>
+void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, T* arena,
+                           const double* rownorm_new, double pivot_tol, long long* err,
+                           cudaStream_t s) {
+  if (nf <= 0) return;
+  const size_t sm = ((size_t)max_m * max_m + max_m) * sizeof(T);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_front_lu_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_front_lu_small<T><<<nf, kThreads, sm, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
+}
+
+template <typename T>
 void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                         cudaStream_t s) {
   if (nf <= 0) return;
@@ -367,7 +450,9 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
   template void launch_spike_rhs<T>(const int32_t*, const int32_t*, const int64_t*, int64_t,   \
                                     const double*, int64_t, int32_t, T*, cudaStream_t);        \
   template void launch_tri_inverse<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,         \
-                                      cudaStream_t);
+                                      cudaStream_t);                                            \
+  template void launch_front_lu_small<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,      \
+                                         const double*, double, long long*, cudaStream_t);
 
 DDPS_INST_T(double)
 DDPS_INST_T(float)

@@ -49,6 +49,15 @@ template <typename T>
 void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const int64_t* rt_src,
                       int64_t nrt, const double* values, int64_t j0, int32_t NR, T* X,
                       cudaStream_t s);
+// Fronts with m <= small_front_max<T>() are factored and inverted in shared memory.
+template <typename T>
+constexpr int small_front_max() {
+  return sizeof(T) == 8 ? 90 : 127;
+}
+template <typename T>
+void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, T* arena,
+                           const double* rownorm_new, double pivot_tol, long long* err,
+                           cudaStream_t s);
 template <typename T>
 void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                         cudaStream_t s);
@@ -78,7 +87,7 @@ void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_f
                           const int32_t* tile_m0, const int64_t* tile_aoff,
                           const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,
                           int64_t j0, int32_t NR, float* X, float* Tb, long long* err,
-                          cudaStream_t s);
+                          int inject_wait, cudaStream_t s);
 template <typename T>
 void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                        int32_t ntiles, const T* arena, const int64_t* block_ncols, int64_t j0,

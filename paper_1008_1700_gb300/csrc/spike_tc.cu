@@ -66,8 +66,9 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 // Bounded wait on an mbarrier phase; gives up early once any CTA has recorded
 // a timeout in err[0], so that a failure costs one wait, not one per CTA.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
-                                          const volatile long long* err) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                                          const volatile long long* err,
+                                          uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if ((it & 1023u) == 1023u && err[0] == 2) return false;
     uint32_t ok;
     asm volatile(
@@ -175,10 +176,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     const int32_t* __restrict__ tile_m0, const int64_t* __restrict__ tile_aoff,
                     const unsigned char* __restrict__ atc, const int64_t* __restrict__ block_ncols,
                     int64_t j0, int32_t NR, float* __restrict__ X, float* __restrict__ Tb,
-                    long long* __restrict__ err) {
+                    long long* __restrict__ err, int inject_wait) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2];
   __shared__ __align__(8) uint64_t empty[2];
+  __shared__ __align__(8) uint64_t never;  // only for inject_wait: nothing arrives here
   __shared__ uint32_t tmem_slot;
   constexpr uint32_t kAB = (PASSES == 3 ? 2u : 1u) * TC_TILE_BYTES;  // A (or B) bytes per stage
   constexpr uint32_t kStageBytes = 2 * kAB;
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&never)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -216,7 +219,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   const uint32_t sbase = smem_u32(smem);
   bool timed_out = false;
 
-  const int nk = (d.K + TC_BK - 1) / TC_BK;
+  int nk = (d.K + TC_BK - 1) / TC_BK;
+  if (inject_wait) {  // failure-path test: a short bounded wait that must run out
+    timed_out = !mbar_wait(smem_u32(&never), 0, err, 4096u);
+    if (timed_out) nk = 0;  // no tensor work: the epilogue writes C_in only
+  }
   for (int kt = 0; kt < nk; ++kt) {
     const int st = kt & 1;
     if (kt >= 2 && !timed_out)
@@ -349,32 +356,36 @@ template <int OP, int PASSES>
 void launch_one(DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                 const int64_t* tile_aoff, const unsigned char* atc, int32_t ntiles,
                 const int64_t* block_ncols, int64_t j0, int32_t NR, float* X, float* Tb,
-                long long* err, cudaStream_t s) {
+                long long* err, int inject, cudaStream_t s) {
   constexpr uint32_t stage = 2 * (PASSES == 3 ? 2u : 1u) * TC_TILE_BYTES;
   const size_t sm = 2 * stage;
   cudaFuncSetAttribute(k_spike_gemm_tc<OP, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
   dim3 grid(ntiles, (NR + TC_BN - 1) / TC_BN);
   k_spike_gemm_tc<OP, PASSES><<<grid, TC_THREADS, sm, s>>>(F, tile_front, tile_m0, tile_aoff, atc,
-                                                            block_ncols, j0, NR, X, Tb, err);
+                                                            block_ncols, j0, NR, X, Tb, err, inject);
 }
 
 template <int PASSES>
 void dispatch_gemm(int op, DevFronts F, const int32_t* tf, const int32_t* tm, const int64_t* ta,
                    const unsigned char* atc, int32_t nt, const int64_t* block_ncols, int64_t j0,
-                   int32_t NR, float* X, float* Tb, long long* err, cudaStream_t s) {
+                   int32_t NR, float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
   switch (op) {
     case OP_FWD_LINV:
-      launch_one<OP_FWD_LINV, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err, s);
+      launch_one<OP_FWD_LINV, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err,
+                                      inject, s);
       break;
     case OP_FWD_L21:
-      launch_one<OP_FWD_L21, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err, s);
+      launch_one<OP_FWD_L21, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err,
+                                     inject, s);
       break;
     case OP_BWD_U12:
-      launch_one<OP_BWD_U12, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err, s);
+      launch_one<OP_BWD_U12, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err,
+                                     inject, s);
       break;
     default:
-      launch_one<OP_BWD_UINV, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err, s);
+      launch_one<OP_BWD_UINV, PASSES>(F, tf, tm, ta, atc, nt, block_ncols, j0, NR, X, Tb, err,
+                                      inject, s);
   }
 }
 
@@ -417,14 +428,14 @@ void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_f
                           const int32_t* tile_m0, const int64_t* tile_aoff,
                           const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,
                           int64_t j0, int32_t NR, float* X, float* Tb, long long* err,
-                          cudaStream_t s) {
+                          int inject_wait, cudaStream_t s) {
   if (ntiles <= 0) return;
   if (passes == 3)
     dispatch_gemm<3>(op, F, tile_front, tile_m0, tile_aoff, atc, ntiles, block_ncols, j0, NR, X,
-                     Tb, err, s);
+                     Tb, err, inject_wait, s);
   else
     dispatch_gemm<1>(op, F, tile_front, tile_m0, tile_aoff, atc, ntiles, block_ncols, j0, NR, X,
-                     Tb, err, s);
+                     Tb, err, inject_wait, s);
 }
 
 }  // namespace ddps

@@ -229,3 +229,19 @@ def test_batch_every_system_meets_tolerance():
         xo, _ = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr).solve(
             p.f, tol=1e-12, eps_in=1e-8)
         assert relerr(x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]], xo) <= 1e-7
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure path of the tensor-core spike kernel: with debug_wait_timeout the
+    kernel waits on an mbarrier that nothing arrives at; the bounded wait runs
+    out, the kernel frees its tensor memory and returns, ddps_factor reports
+    DDPS_ERR_TIMEOUT, and the context stays usable for a normal solve."""
+    P = W.small_convdiff_2d(24, 3)
+    from paper_1008_1700_gb300 import Solver
+    S = Solver(P.rowptr, P.colind, P.block_ptr, debug_wait_timeout=1, **TC3)
+    with pytest.raises(N.DDPSError, match="TIMEOUT"):
+        S.factor(dev(P.values))
+    S.close()
+    S2 = make_solver(P, tol_out=1e-12, tol_in=1e-8, **TC3)
+    x, info = S2.solve(dev(P.f))
+    assert info["status"] == "DDPS_OK" and info["relres_inf"] <= 1e-12
