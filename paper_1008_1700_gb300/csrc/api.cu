@@ -49,6 +49,10 @@ size_t prec_size(int prec) { return prec == DDPS_FP64 ? 8 : (prec == DDPS_FP32 ?
 // the shared-memory kernel, then `nlarge` others, starting at `first`.
 struct LevelSplit {
   int32_t first = 0, nsmall = 0, nlarge = 0, max_small_m = 0;
+  // multi-CTA LU of the large fronts: per panel step p (columns 32p..32p+31),
+  // fronts [pf_ptr[p], pf_ptr[p+1]) of lu_panel_fronts and tiles
+  // [pt_ptr[p], pt_ptr[p+1]) of lu_tile_front / lu_tile_ij
+  std::vector<int64_t> pf_ptr, pt_ptr;
 };
 
 struct ddps_handle {
@@ -99,6 +103,7 @@ struct ddps_handle {
   // LU launch order per depth (see LevelSplit)
   int32_t* lu_order = nullptr;
   std::vector<LevelSplit> split;
+  int32_t *lu_panel_fronts = nullptr, *lu_tile_front = nullptr, *lu_tile_ij = nullptr;
   // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
   int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
   std::vector<int32_t> tk_ptr, tr_ptr;
@@ -304,10 +309,18 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       h->launches++;
     }
     if (ls.nlarge > 0) {
-      launch_front_lu<T>(h->F, h->lu_order + ls.first + ls.nsmall, ls.nlarge, arena, h->rownorm,
-                         h->opt.pivot_tol, h->derr, s);
+      for (size_t pstep = 0; pstep + 1 < ls.pf_ptr.size(); ++pstep) {
+        const int32_t j0 = (int32_t)pstep * kLuPanel;
+        launch_lu_panel<T>(h->F, h->lu_panel_fronts + ls.pf_ptr[pstep],
+                           (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]), j0, arena,
+                           h->rownorm, h->opt.pivot_tol, h->derr, s);
+        launch_lu_trailing<T>(h->F, h->lu_tile_front + ls.pt_ptr[pstep],
+                              h->lu_tile_ij + ls.pt_ptr[pstep],
+                              (int32_t)(ls.pt_ptr[pstep + 1] - ls.pt_ptr[pstep]), j0, arena, s);
+        h->launches += 2;
+      }
       launch_tri_inverse<T>(h->F, h->lu_order + ls.first + ls.nsmall, ls.nlarge, h->max_k, arena, s);
-      h->launches += 2;
+      h->launches++;
     }
   }
   launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
@@ -879,7 +892,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
   {
     const int small = h->opt.factor_prec == DDPS_FP64 ? small_front_max<double>() : small_front_max<float>();
-    std::vector<int32_t> order;
+    std::vector<int32_t> order, pfronts, tfront, tij;
     h->split.assign(A.nlevels, LevelSplit{});
     for (int L = 0; L < A.nlevels; ++L) {
       LevelSplit& ls = h->split[L];
@@ -892,15 +905,41 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
           ls.max_small_m = std::max(ls.max_small_m, A.f_m[f]);
         }
       }
+      int32_t kmax = 0;
       for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
         const int32_t f = A.level_fronts[q];
         if (A.f_m[f] > small) {
           order.push_back(f);
           ls.nlarge++;
+          kmax = std::max(kmax, A.f_k[f]);
         }
+      }
+      // panel steps of the large fronts
+      const int npanel = (kmax + kLuPanel - 1) / kLuPanel;
+      ls.pf_ptr.assign(1, (int64_t)pfronts.size());
+      ls.pt_ptr.assign(1, (int64_t)tfront.size());
+      for (int pstep = 0; pstep < npanel; ++pstep) {
+        const int32_t j0 = pstep * kLuPanel;
+        for (int32_t i = ls.first + ls.nsmall; i < (int32_t)order.size(); ++i) {
+          const int32_t f = order[i];
+          if (A.f_k[f] <= j0) continue;
+          pfronts.push_back(f);
+          const int32_t t0 = std::min(j0 + kLuPanel, A.f_k[f]);
+          const int32_t nt = (A.f_m[f] - t0 + kLuTile - 1) / kLuTile;
+          for (int32_t ti = 0; ti < nt; ++ti)
+            for (int32_t tj = 0; tj < nt; ++tj) {
+              tfront.push_back(f);
+              tij.push_back((ti << 16) | tj);
+            }
+        }
+        ls.pf_ptr.push_back((int64_t)pfronts.size());
+        ls.pt_ptr.push_back((int64_t)tfront.size());
       }
     }
     h->lu_order = dupload(h, order);
+    h->lu_panel_fronts = dupload(h, pfronts);
+    h->lu_tile_front = dupload(h, tfront);
+    h->lu_tile_ij = dupload(h, tij);
   }
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();

@@ -199,6 +199,126 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Large fronts, several CTAs per front: the same blocked right-looking LU as
+// k_front_lu, split into one launch per 32-column panel for the panel and
+// its U12 row panel (one CTA per front) and one launch for the trailing
+// update over 64 x 64 tiles of every front of the depth.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_lu_panel(DevFronts F, const int32_t* __restrict__ list, int32_t j0, T* __restrict__ arena,
+               const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  if (j0 >= k) return;
+  T* __restrict__ A = arena + F.arena[f];
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x;
+  __shared__ T Ls[NB][NB + 1];
+  const int jb = min(NB, k - j0);
+  for (int j = j0; j < j0 + jb; ++j) {
+    T piv = A[j + (int64_t)j * m];
+    const double thr = pivot_tol * rownorm[row0 + j];
+    if (!(fabs((double)piv) > thr)) {
+      const double rep = thr > 0.0 ? thr : 1e-300;
+      piv = (T)((double)piv < 0.0 ? -rep : rep);
+      if (tid == 0) {
+        if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+          err[1] = f;
+          err[2] = row0 + j;
+        }
+        A[j + (int64_t)j * m] = piv;
+      }
+    }
+    const T inv = T(1) / piv;
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
+    __syncthreads();
+    const int nr = m - (j + 1);
+    const int nc = j0 + jb - (j + 1);
+    for (int t = tid; t < nr * nc; t += blockDim.x) {
+      const int i = j + 1 + t % nr;
+      const int c = j + 1 + t / nr;
+      A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * A[j + (int64_t)c * m];
+    }
+    __syncthreads();
+  }
+  const int t0 = j0 + jb;
+  if (t0 >= m) return;
+  for (int t = tid; t < jb * jb; t += blockDim.x) {
+    const int r = t % jb, q = t / jb;
+    Ls[r][q] = A[j0 + r + (int64_t)(j0 + q) * m];
+  }
+  __syncthreads();
+  for (int c = t0 + tid; c < m; c += blockDim.x) {
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
+#pragma unroll
+    for (int r = 1; r < NB; ++r) {
+      T sacc = x[r];
+#pragma unroll
+      for (int q = 0; q < r; ++q) sacc -= Ls[r][q] * x[q];
+      x[r] = sacc;
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
+  }
+}
+
+// tile word: front in tile_front, (ti << 16) | tj in tile_ij, rows/cols from t0 = j0 + 32
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_lu_trailing(DevFronts F, const int32_t* __restrict__ tile_front,
+                  const int32_t* __restrict__ tile_ij, int32_t j0, T* __restrict__ arena) {
+  const int32_t f = tile_front[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const int jb = min(NB, k - j0);
+  const int t0 = j0 + jb;
+  const int ti = tile_ij[blockIdx.x] >> 16, tj = tile_ij[blockIdx.x] & 0xffff;
+  const int rb = t0 + ti * TT, cb = t0 + tj * TT;
+  T* __restrict__ A = arena + F.arena[f];
+  const int tid = threadIdx.x;
+  __shared__ T Lt[TT][NB + 1];
+  __shared__ T Ut[NB][TT + 1];
+  for (int t = tid; t < TT * NB; t += blockDim.x) {
+    const int r = t % TT, q = t / TT;
+    Lt[r][q] = (rb + r < m && q < jb) ? A[rb + r + (int64_t)(j0 + q) * m] : T(0);
+    const int q2 = t % NB, c2 = t / NB;
+    Ut[q2][c2] = (cb + c2 < m && q2 < jb) ? A[j0 + q2 + (int64_t)(cb + c2) * m] : T(0);
+  }
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = T(0);
+#pragma unroll 8
+  for (int q = 0; q < NB; ++q) {
+    T lv[4], uv[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) lv[a2] = Lt[tr + 16 * a2][q];
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) uv[b2] = Ut[q][tc + 16 * b2];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] += lv[a2] * uv[b2];
+  }
+#pragma unroll
+  for (int b2 = 0; b2 < 4; ++b2) {
+    const int c = cb + tc + 16 * b2;
+    if (c >= m) continue;
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      const int r = rb + tr + 16 * a2;
+      if (r < m) A[r + (int64_t)c * m] -= acc[a2][b2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Small fronts (m*m entries fit in shared memory): partial LU and the
 // inversion of the diagonal triangles done in shared memory by one CTA, then
 // written back once.  Same arithmetic as k_front_lu followed by
@@ -412,6 +532,20 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 }
 
 template <typename T>
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
+  if (nf <= 0) return;
+  k_lu_panel<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
+}
+
+template <typename T>
+void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
+                        int32_t ntiles, int32_t j0, T* arena, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_lu_trailing<T><<<ntiles, kThreads, 0, s>>>(F, tile_front, tile_ij, j0, arena);
+}
+
+template <typename T>
 void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, T* arena,
                            const double* rownorm_new, double pivot_tol, long long* err,
                            cudaStream_t s) {
@@ -452,7 +586,11 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
   template void launch_tri_inverse<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,         \
                                       cudaStream_t);                                            \
   template void launch_front_lu_small<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,      \
-                                         const double*, double, long long*, cudaStream_t);
+                                         const double*, double, long long*, cudaStream_t);      \
+  template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,            \
+                                   const double*, double, long long*, cudaStream_t);            \
+  template void launch_lu_trailing<T>(DevFronts, const int32_t*, const int32_t*, int32_t,      \
+                                      int32_t, T*, cudaStream_t);
 
 DDPS_INST_T(double)
 DDPS_INST_T(float)

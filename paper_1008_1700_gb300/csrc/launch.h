@@ -58,6 +58,16 @@ template <typename T>
 void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, T* arena,
                            const double* rownorm_new, double pivot_tol, long long* err,
                            cudaStream_t s);
+// Multi-CTA LU of large fronts: panel j0 (one CTA per front), then the
+// trailing update over tiles of 64 x 64 (tile_ij = (ti << 16) | tj).
+constexpr int kLuPanel = 32;
+constexpr int kLuTile = 64;
+template <typename T>
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
+template <typename T>
+void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
+                        int32_t ntiles, int32_t j0, T* arena, cudaStream_t s);
 template <typename T>
 void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                         cudaStream_t s);

@@ -220,27 +220,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   bool timed_out = false;
 
   int nk = (d.K + TC_BK - 1) / TC_BK;
-  if (inject_wait) {  // failure-path test: a short bounded wait that must run out
-    timed_out = !mbar_wait(smem_u32(&never), 0, err, 4096u);
-    if (timed_out) nk = 0;  // no tensor work: the epilogue writes C_in only
-  }
-  for (int kt = 0; kt < nk; ++kt) {
-    const int st = kt & 1;
-    if (kt >= 2 && !timed_out)
-      timed_out = !mbar_wait(smem_u32(&empty[st]), ((kt - 2) >> 1) & 1, err);
-    const uint32_t aS = sbase + st * kStageBytes;
-    if (tid == 0) {
-      mbar_expect_tx(smem_u32(&full[st]), kAB);
-      bulk_g2s(aS, apk + (int64_t)kt * kAB, kAB, smem_u32(&full[st]));
-    }
-    unsigned char* sB = smem + st * kStageBytes + kAB;
+  // B (panel rows, fp32) of one stage: each thread holds kBItems runs of 8
+  // K-consecutive values of one column in registers, loaded one stage ahead
+  constexpr int kBItems = (TC_BN * TC_BK / 8) / TC_THREADS;
+  float breg[kBItems][8];
+  const float* Bp = (OP == OP_FWD_L21 || OP == OP_BWD_U12) ? X : Tb;
+  auto load_b = [&](int kt) {
     const int k0 = kt * TC_BK;
 #pragma unroll
-    for (int q = 0; q < (TC_BN * TC_BK / 8) / TC_THREADS; ++q) {
+    for (int q = 0; q < kBItems; ++q) {
       const int e = tid + q * TC_THREADS;
       const int col = e % TC_BN, kc = e / TC_BN;
       const int gj = n0 + col;
-      float v[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int gk = k0 + kc * 8 + t;
@@ -253,14 +244,35 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             brow = row0 + gk;
           else
             brow = idx[k + gk];
-          const float* Bp = (OP == OP_FWD_L21 || OP == OP_BWD_U12) ? X : Tb;
           val = Bp[brow * NR + gj];
         }
-        v[t] = val;
+        breg[q][t] = val;
       }
-      const uint32_t off = chunk_off(col, kc);
-      store_split(sB + off, sB + TC_TILE_BYTES + off, v, PASSES == 3);
     }
+  };
+  if (inject_wait) {  // failure-path test: a short bounded wait that must run out
+    timed_out = !mbar_wait(smem_u32(&never), 0, err, 4096u);
+    if (timed_out) nk = 0;  // no tensor work: the epilogue writes C_in only
+  }
+  if (nk > 0) load_b(0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    if (kt >= 2 && !timed_out)
+      timed_out = !mbar_wait(smem_u32(&empty[st]), ((kt - 2) >> 1) & 1, err);
+    const uint32_t aS = sbase + st * kStageBytes;
+    if (tid == 0) {
+      mbar_expect_tx(smem_u32(&full[st]), kAB);
+      bulk_g2s(aS, apk + (int64_t)kt * kAB, kAB, smem_u32(&full[st]));
+    }
+    // convert the B tile loaded during the previous stage, then start loading the next one
+    unsigned char* sB = smem + st * kStageBytes + kAB;
+#pragma unroll
+    for (int q = 0; q < kBItems; ++q) {
+      const int e = tid + q * TC_THREADS;
+      const uint32_t off = chunk_off(e % TC_BN, e / TC_BN);
+      store_split(sB + off, sB + TC_TILE_BYTES + off, breg[q], PASSES == 3);
+    }
+    if (kt + 1 < nk) load_b(kt + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
