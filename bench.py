@@ -12,8 +12,9 @@ pattern; it runs once before the timed region and is reported as
 ``analyze_ms``.
 
 Forms: ``mixed`` = FP32 block factors and spike solves with the spike
-products on the tensor cores (bf16x3 operands, fp32 accumulation), FP32 G^
-and inner vectors, FP64 outer Krylov (the headline); ``mixed_simt`` = the
+products on the tensor cores (bf16x3 operands, fp32 accumulation), G^ stored
+in FP16 (products accumulate in FP32), FP32 inner vectors, FP64 outer Krylov
+(the headline); ``mixed_simt`` = the
 same with FP32 SIMT spike products; ``fp64`` = plain FP64 DDPS.
 
 Under torchrun every rank solves its own copy of the workload (the systems
@@ -75,8 +76,9 @@ def form_options(form):
     base = dict(tol_out=1e-10, maxit_out=1000, tol_in=1e-4, maxit_in=100)
     if form == "mixed":
         # FP32 block factors and spike solves, spike products on the tensor cores
-        # (bf16x3 operands, fp32 accumulation), FP32 G^ and inner vectors, FP64 outer
-        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP32,
+        # (bf16x3 operands, fp32 accumulation), FP16 G^ storage with FP32
+        # accumulation, FP32 inner vectors, FP64 outer
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
                     inner_prec=N.DDPS_FP32)
     elif form == "mixed_simt":
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
@@ -161,6 +163,7 @@ class ClockSampler:
 def algorithmic_work(sizes, P, form, steps, prof):
     """Per class: (kind, total algorithmic amount over the timed region)."""
     sf = 8 if form == "fp64" else 4
+    sg = 8 if form == "fp64" else (2 if form == "mixed" else 4)  # G^ storage
     si = sf
     n, nnz, m = sizes["n"], sizes["nnz"], sizes["m"]
     out = {}
@@ -169,11 +172,11 @@ def algorithmic_work(sizes, P, form, steps, prof):
     out["spike_fwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
     out["spike_bwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
     out["assemble"] = ("bytes", (nnz * (8 + 8) + sizes["factor_entries"] * sf) * steps)
-    out["ghat_extract"] = ("bytes", sizes["ghat_entries"] * (sf + sf) * steps)
+    out["ghat_extract"] = ("bytes", sizes["ghat_entries"] * (sf + sg) * steps)
     # per call of the solve phase
     calls = {k: v[1] for k, v in prof.items()}
     out["block_solve"] = ("bytes", (sizes["factor_lu_entries"] * sf + n * 16) * calls["block_solve"])
-    out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sf + 2 * m * si) * calls["ghat_matvec"])
+    out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sg + 2 * m * si) * calls["ghat_matvec"])
     out["spmv"] = ("bytes", (nnz * 12 + (n + 1) * 4 + n * 16) * calls["spmv"])
     return out
 
@@ -378,13 +381,14 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.form == "fp64" else ("bf16x3+f32+f64" if args.form == "mixed" else "f32+f64"),
+        "dtype": "f64" if args.form == "fp64" else ("bf16x3+f16+f32+f64" if args.form == "mixed" else "f32+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
                    "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
                    "form": args.form, "parallelism": f"replicas{world}",
                    "l2": "working set (G^ %.1f GB) larger than L2" %
-                         (sizes["ghat_entries"] * (8 if args.form == "fp64" else 4) / 1e9),
+                         (sizes["ghat_entries"] * (8 if args.form == "fp64" else
+                                                   (2 if args.form == "mixed" else 4)) / 1e9),
                    "tol_out": opts["tol_out"], "tol_in": opts["tol_in"]},
         "analyze_ms": round(analyze_ms, 1),
         "accuracy": {"relres_inf": relres, "rel_err_vs_xtrue": err_xtrue, "converged": converged,

@@ -59,7 +59,7 @@ typedef enum {
 /* BF16X3 (spike products only): each fp32 operand is split into a bf16 high
  * part and a bf16 remainder and the product is hi*hi + hi*lo + lo*hi on the
  * tensor cores with fp32 accumulation (about 16 correct bits). */
-typedef enum { DDPS_FP64 = 0, DDPS_FP32 = 1, DDPS_BF16 = 2, DDPS_BF16X3 = 3 } ddps_precision;
+typedef enum { DDPS_FP64 = 0, DDPS_FP32 = 1, DDPS_BF16 = 2, DDPS_BF16X3 = 3, DDPS_FP16 = 4 } ddps_precision;
 
 /* Fig. 2 step 3.  COLUMN: the Sec. 3 rule — in block row R_i, column k is
  * dropped when ||R_i(:,k)||_inf <= drop_tol * max_j ||R_i(:,j)||_inf.
@@ -74,7 +74,8 @@ typedef struct {
   int32_t spike_prec;     /* operands of the spike products of Fig. 2 step 4: equal to factor_prec
                              (SIMT), or, with FP32 factors, BF16 / BF16X3 (tensor cores, fp32
                              accumulation) */
-  int32_t ghat_prec;      /* FP64, FP32 or BF16 storage of G^ (Sec. 3: dense per-partition arrays) */
+  int32_t ghat_prec;      /* FP64, FP32, FP16 or BF16 storage of G^ (Sec. 3: dense per-partition
+                             arrays); FP16/BF16 products accumulate in FP32 */
   int32_t inner_prec;     /* FP64 or FP32 vectors of the inner BiCGStab on G^ (6.3) */
   double tol_out;         /* outer stop: ||f - A x||_inf <= tol_out ||f||_inf, per system */
   int32_t maxit_out;      /* outer iteration cap (Sec. 4: 1000) */

@@ -88,6 +88,9 @@ struct ddps_handle {
   // reduced system
   int64_t* c = nullptr;
   int32_t *c_rownew = nullptr, *qblock = nullptr, *gcols = nullptr;
+  int32_t* block_sys = nullptr;  // system of each block
+  int32_t* any_flag = nullptr;   // device flag: some system still iterating
+  int32_t* any_host = nullptr;   // pinned copy
   int64_t *gq0 = nullptr, *gq1 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr,
           *gld = nullptr, *block_ncols = nullptr;
   // tiles of the G^ product: (block, first row) per 64 reduced rows
@@ -415,7 +418,7 @@ void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
 }
 
 template <typename TG, typename TI>
-void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
+void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal* sc = nullptr) {
   Prof pr(h, DDPS_PROF_GHAT_MATVEC, s);
   using AT = typename std::conditional<std::is_same<TG, double>::value, double, float>::type;
   if (h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024) {
@@ -423,7 +426,7 @@ void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s) {
     // columns gets w = v on its rows)
     launch_ghat_matvec_tiled<TG, TI>((const TG*)h->ghat, h->mv_block, h->mv_row, h->mv_ntiles,
                                      h->mv_max_cols, h->gq0, h->gq1, h->gcol_ptr, h->ghat_off,
-                                     h->gld, h->gcols, v, w, s);
+                                     h->gld, h->gcols, v, w, sc, h->block_sys, s);
   } else {
     launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
                                h->gld, h->gcols, (int64_t)h->A.c.size(), v, w, s);
@@ -521,59 +524,39 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
     CK(cudaMemsetAsync(v, 0, m * sizeof(TI), s));
   }
   CK(cudaMemcpyAsync(rh, r, m * sizeof(TI), cudaMemcpyDeviceToDevice, s));
+  // Iterations are enqueued without waiting: the convergence tests run on the
+  // device (fused into the reductions), stopped systems skip every kernel, and
+  // the host looks at a single "some system still iterating" flag every
+  // kCheckEvery iterations.
+  constexpr int kCheckEvery = 4;
   for (int it = 1; it <= h->opt.maxit_in; ++it) {
-    bool any = false;
-    for (int q = 0; q < ns; ++q) any |= h->hsc[q].active != 0;
-    if (!any) break;
-    seg_reduce<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, s);
-    sc_beta(ns, sc, it == 1, s);
-    update_p<TI>(S, sc, r, p, v, s);
-    ghat_matvec<TG, TI>(h, p, v, s);
-    seg_reduce<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial, s);
-    sc_alpha(ns, sc, s);
-    update_s<TI>(S, sc, r, v, sv, s);
-    seg_reduce<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial, s);
-    h->launches += 10;
-    download_sc(h, sc, s);
-    bool half_any = false;
-    for (int q = 0; q < ns; ++q) {
-      KScal& k = h->hsc[q];
-      if (!k.active) continue;
-      if (k.nrm <= tol * k.ref) {
-        k.half_done = 1;
-        k.active = 0;
-        iters[q] = it - 0.5;
-        half_any = true;
-      } else if (k.breakdown) {
-        k.active = 0;
-        iters[q] = it;
-      }
-    }
-    upload_sc(h, sc, s);
-    if (half_any) {
-      update_xr<TI>(S, sc, 1, z, p, nullptr, nullptr, nullptr, nullptr, s);
+    if ((it - 1) % kCheckEvery == 0) {
+      any_active(ns, sc, h->any_flag, s);
+      CK(cudaMemcpyAsync(h->any_host, h->any_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      h->stage_next = 0;
       h->launches++;
-      for (int q = 0; q < ns; ++q) h->hsc[q].half_done = 0;
-      upload_sc(h, sc, s);
+      if (!*h->any_host) break;
     }
-    any = false;
-    for (int q = 0; q < ns; ++q) any |= h->hsc[q].active != 0;
-    if (!any) break;
-    ghat_matvec<TG, TI>(h, sv, t, s);
-    seg_reduce<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(), h->partial, s);
-    sc_omega(ns, sc, s);
-    update_xr<TI>(S, sc, 0, z, p, sv, r, sv, t, s);
-    seg_reduce<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial, s);
-    h->launches += 7;
-    download_sc(h, sc, s);
-    for (int q = 0; q < ns; ++q) {
-      KScal& k = h->hsc[q];
-      if (!k.active) continue;
-      iters[q] = it;
-      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown) k.active = 0;
-    }
-    upload_sc(h, sc, s);
+    seg_reduce_post<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, POST_BETA,
+                        sc, tol, it, s);
+    update_p<TI>(S, sc, r, p, v, s);
+    ghat_matvec<TG, TI>(h, p, v, s, sc);
+    seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
+                        POST_ALPHA, sc, tol, it, s);
+    update_s<TI>(S, sc, r, v, sv, s);
+    seg_reduce_post<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
+                        POST_CHECK_HALF, sc, tol, it, s);
+    ghat_matvec<TG, TI>(h, sv, t, s, sc);
+    seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
+                        h->partial, POST_OMEGA, sc, tol, it, s);
+    update_xr_final<TI>(S, sc, z, p, sv, r, t, s);
+    seg_reduce_post<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
+                        POST_CHECK_FULL, sc, tol, it, s);
+    h->launches += 15;
   }
+  download_sc(h, sc, s);
+  for (int q = 0; q < ns; ++q) iters[q] = h->hsc[q].iters;
   convert<double, TI>(m, z, zhat64, s);
   h->launches++;
   double mx = 0;
@@ -590,6 +573,9 @@ double inner_dispatch(ddps_handle* h, const double* ghat64, double* zhat64, cons
   if (gp == DDPS_FP32)
     return ip == DDPS_FP64 ? inner_solve<float, double>(h, ghat64, zhat64, z0, s)
                            : inner_solve<float, float>(h, ghat64, zhat64, z0, s);
+  if (gp == DDPS_FP16)
+    return ip == DDPS_FP64 ? inner_solve<__half, double>(h, ghat64, zhat64, z0, s)
+                           : inner_solve<__half, float>(h, ghat64, zhat64, z0, s);
   return ip == DDPS_FP64 ? inner_solve<__nv_bfloat16, double>(h, ghat64, zhat64, z0, s)
                          : inner_solve<__nv_bfloat16, float>(h, ghat64, zhat64, z0, s);
 }
@@ -851,6 +837,9 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     ncols[b] = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
   }
   h->qblock = dupload(h, qblock);
+  h->block_sys = dupload(h, A.block_sys);
+  h->any_flag = dalloc<int32_t>(h, 1);
+  CK(cudaMallocHost((void**)&h->any_host, sizeof(int32_t)));
   h->gq0 = dupload(h, A.gq0);
   h->gq1 = dupload(h, A.gq1);
   h->gcol_ptr = dupload(h, A.gcol_ptr);
@@ -1019,8 +1008,9 @@ bool valid_options(const ddps_options& o, std::string& why) {
     why = "factor_prec must be FP64 or FP32";
     return false;
   }
-  if (o.ghat_prec < DDPS_FP64 || o.ghat_prec > DDPS_BF16) {
-    why = "ghat_prec must be FP64, FP32 or BF16";
+  if (o.ghat_prec != DDPS_FP64 && o.ghat_prec != DDPS_FP32 && o.ghat_prec != DDPS_BF16 &&
+      o.ghat_prec != DDPS_FP16) {
+    why = "ghat_prec must be FP64, FP32, FP16 or BF16";
     return false;
   }
   if (o.inner_prec != DDPS_FP64 && o.inner_prec != DDPS_FP32) {
@@ -1128,11 +1118,15 @@ ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream) {
         factor_impl<double, double>(h, s);
       else if (gp == DDPS_FP32)
         factor_impl<double, float>(h, s);
+      else if (gp == DDPS_FP16)
+        factor_impl<double, __half>(h, s);
       else
         factor_impl<double, __nv_bfloat16>(h, s);
     } else {
       if (gp == DDPS_FP32)
         factor_impl<float, float>(h, s);
+      else if (gp == DDPS_FP16)
+        factor_impl<float, __half>(h, s);
       else
         factor_impl<float, __nv_bfloat16>(h, s);
     }
@@ -1258,6 +1252,8 @@ ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void
       ghat_matvec<double, double>(h, v, w, s);
     else if (gp == DDPS_FP32)
       ghat_matvec<float, double>(h, v, w, s);
+    else if (gp == DDPS_FP16)
+      ghat_matvec<__half, double>(h, v, w, s);
     else
       ghat_matvec<__nv_bfloat16, double>(h, v, w, s);
     check_launch();
@@ -1360,6 +1356,10 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
           float fv;
           std::memcpy(&fv, e, 4);
           v = fv;
+        } else if (gp == DDPS_FP16) {
+          __half hv;
+          std::memcpy(&hv, e, 2);
+          v = (double)__half2float(hv);
         } else {
           uint16_t hb;
           std::memcpy(&hb, e, 2);
@@ -1384,6 +1384,7 @@ ddps_status ddps_destroy(ddps_handle* h) {
   if (h->hsc_out) cudaFreeHost(h->hsc_out);
   if (h->hsc_in) cudaFreeHost(h->hsc_in);
   if (h->hstage) cudaFreeHost(h->hstage);
+  if (h->any_host) cudaFreeHost(h->any_host);
   delete h;
   return DDPS_OK;
 }

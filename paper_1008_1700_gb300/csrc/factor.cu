@@ -605,5 +605,7 @@ DDPS_INST_TG(double, float)
 DDPS_INST_TG(float, float)
 DDPS_INST_TG(float, __nv_bfloat16)
 DDPS_INST_TG(double, __nv_bfloat16)
+DDPS_INST_TG(float, __half)
+DDPS_INST_TG(double, __half)
 
 }  // namespace ddps

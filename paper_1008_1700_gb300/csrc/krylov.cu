@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void k_seg_final(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
-                            const double* __restrict__ partial) {
+                            const double* __restrict__ partial, int post, KScal* sc, double tol,
+                            int it) {
   const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
   if (sgi >= S.nseg) return;
   RedSpec spec[3] = {r0, r1, r2};
@@ -82,6 +83,71 @@ __global__ void k_seg_final(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec
     if (spec[q].op == 1) v = sqrt(v);
     spec[q].out[(int64_t)sgi * spec[q].stride] = v;
   }
+  if (post == POST_NONE) return;
+  KScal& k = sc[sgi];
+  if (post == POST_CHECK_FULL) k.half_done = 0;
+  if (!k.active) return;
+  switch (post) {
+    case POST_BETA:
+      if (k.rho == 0.0) k.breakdown = 1;
+      k.beta = it == 1 ? 0.0 : (k.rho / k.rho_old) * (k.alpha / k.omega);
+      break;
+    case POST_ALPHA:
+      if (k.sigma == 0.0) {
+        k.breakdown = 1;
+        k.alpha = 0.0;
+      } else {
+        k.alpha = k.rho / k.sigma;
+      }
+      break;
+    case POST_CHECK_HALF:
+      if (k.nrm <= tol * k.ref) {
+        k.half_done = 1;
+        k.active = 0;
+        k.iters = it - 0.5;
+      } else if (k.breakdown) {
+        k.active = 0;
+        k.iters = it;
+      }
+      break;
+    case POST_OMEGA:
+      k.omega = k.tt != 0.0 ? k.ts / k.tt : 0.0;
+      k.rho_old = k.rho;
+      break;
+    case POST_CHECK_FULL:
+      k.iters = it;
+      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown) k.active = 0;
+      break;
+  }
+}
+
+template <typename T>
+__global__ void k_update_xr_final(SegView S, const KScal* __restrict__ sc, T* __restrict__ x,
+                                  const T* __restrict__ p, const T* __restrict__ sv,
+                                  T* __restrict__ r, const T* __restrict__ t) {
+  const int ch = blockIdx.x;
+  const int sg = S.chunk_seg[ch];
+  const bool act = sc[sg].active != 0, half = sc[sg].half_done != 0;
+  if (!act && !half) return;
+  const double alpha = sc[sg].alpha, omega = sc[sg].omega;
+  for (int64_t i = S.chunk_beg[ch] + threadIdx.x; i < S.chunk_end[ch]; i += blockDim.x) {
+    if (act) {
+      x[i] = (T)((double)x[i] + alpha * (double)p[i] + omega * (double)sv[i]);
+      r[i] = (T)((double)sv[i] - omega * (double)t[i]);
+    } else {
+      x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+    }
+  }
+}
+
+__global__ void k_any_active(int nseg, const KScal* __restrict__ sc, int32_t* __restrict__ flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < nseg; g += blockDim.x)
+    if (sc[g].active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any;
 }
 
 // ---- element-wise updates, one CTA per chunk, skipped for inactive segments ----
@@ -200,7 +266,26 @@ void seg_reduce(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2, 
                 cudaStream_t s) {
   if (S.nchunks == 0) return;
   k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial);
-  k_seg_final<<<(S.nseg + 127) / 128, 128, 0, s>>>(S, nred, r0, r1, r2, partial);
+  k_seg_final<<<(S.nseg + 127) / 128, 128, 0, s>>>(S, nred, r0, r1, r2, partial, POST_NONE,
+                                                   nullptr, 0.0, 0);
+}
+
+template <typename T>
+void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
+                     double* partial, int post, KScal* sc, double tol, int it, cudaStream_t s) {
+  if (S.nchunks > 0) k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial);
+  k_seg_final<<<(S.nseg + 127) / 128, 128, 0, s>>>(S, nred, r0, r1, r2, partial, post, sc, tol,
+                                                   it);
+}
+
+template <typename T>
+void update_xr_final(const SegView& S, const KScal* sc, T* x, const T* p, const T* sv, T* r,
+                     const T* t, cudaStream_t s) {
+  if (S.nchunks) k_update_xr_final<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, x, p, sv, r, t);
+}
+
+void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s) {
+  k_any_active<<<1, 256, 0, s>>>(nseg, sc, flag);
 }
 
 template <typename T>
@@ -257,7 +342,11 @@ void sc_omega(int nseg, KScal* sc, cudaStream_t s) {
                            cudaStream_t);                                                        \
   template void masked_axpy<T>(const SegView&, const KScal*, T*, const T*, const T*,             \
                                cudaStream_t);                                                    \
-  template void masked_zero<T>(const SegView&, const KScal*, T*, cudaStream_t);
+  template void masked_zero<T>(const SegView&, const KScal*, T*, cudaStream_t);                  \
+  template void seg_reduce_post<T>(const SegView&, int, RedSpec, RedSpec, RedSpec, double*, int, \
+                                   KScal*, double, int, cudaStream_t);                           \
+  template void update_xr_final<T>(const SegView&, const KScal*, T*, const T*, const T*, T*,     \
+                                   const T*, cudaStream_t);
 DDPS_INST_K(double)
 DDPS_INST_K(float)
 template void convert<float, double>(int64_t, const double*, float*, cudaStream_t);

@@ -34,6 +34,7 @@ struct KScal {
   double ref;         // reference norm of the stopping test
   double nrm;         // last residual norm
   double nrm2;        // second norm slot (true residual)
+  double iters;       // iterations taken (half steps count 0.5), kept on the device
   int32_t active;     // still iterating
   int32_t half_done;  // converged at the half step of the current iteration
   int32_t breakdown;
@@ -63,6 +64,25 @@ void masked_axpy(const SegView& S, const KScal* sc, T* dst, const T* a, const T*
 // dst = 0 on segments whose flag is set
 template <typename T>
 void masked_zero(const SegView& S, const KScal* sc, T* dst, cudaStream_t s);
+// Reduction whose final pass also updates the segment's scalars:
+enum Post {
+  POST_NONE = 0,
+  POST_BETA = 1,        // beta = (rho / rho_old)(alpha / omega), 0 at iteration 1
+  POST_ALPHA = 2,       // alpha = rho / sigma
+  POST_CHECK_HALF = 3,  // ||s|| <= tol ref: stop at the half step (x += alpha p pending)
+  POST_OMEGA = 4,       // omega = (t, s) / (t, t); rho_old = rho
+  POST_CHECK_FULL = 5   // ||r|| <= tol ref, omega = 0 or breakdown: stop; clears half_done
+};
+template <typename T>
+void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
+                     double* partial, int post, KScal* sc, double tol, int it, cudaStream_t s);
+// Full step: active segments x += alpha p + omega s, r = s - omega t; segments
+// stopped at this iteration's half step: x += alpha p.
+template <typename T>
+void update_xr_final(const SegView& S, const KScal* sc, T* x, const T* p, const T* sv, T* r,
+                     const T* t, cudaStream_t s);
+// *flag = 1 if some segment is still active, else 0.
+void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s);
 void sc_beta(int nseg, KScal* sc, int first, cudaStream_t s);
 void sc_alpha(int nseg, KScal* sc, cudaStream_t s);
 void sc_omega(int nseg, KScal* sc, cudaStream_t s);

@@ -4,10 +4,13 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
 namespace ddps {
+
+struct KScal;
 
 // Multifrontal structure of all blocks, resident on the device.
 struct DevFronts {
@@ -129,13 +132,14 @@ void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq
                         const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
                         const int32_t* gcols, int64_t m, const TI* v, TI* w, cudaStream_t s);
 // Tiled G^ product: one CTA per (block, 64 reduced rows); needs max_cols
-// entries of shared memory for the block's gathered vector.
+// entries of shared memory for the block's gathered vector.  With sc
+// non-null, blocks of systems whose inner solve has stopped are skipped.
 template <typename TG, typename TI>
 void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
                               int32_t ntiles, int64_t max_cols, const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
-                              cudaStream_t s);
+                              const KScal* sc, const int32_t* block_sys, cudaStream_t s);
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s);
 void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_t nrt,
                              double* rt_val, cudaStream_t s);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "krylov.h"
 #include "launch.h"
 
 namespace ddps {
@@ -143,6 +144,10 @@ template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half v) {
+  return __half2float(v);
+}
 
 template <typename AT, typename TG>
 __device__ __forceinline__ AT to_acc(TG v) {
@@ -151,6 +156,10 @@ __device__ __forceinline__ AT to_acc(TG v) {
 template <>
 __device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ float to_acc<float, __half>(__half v) {
+  return __half2float(v);
 }
 
 template <typename TG>
@@ -231,6 +240,10 @@ template <>
 struct Vec16<double> {
   static constexpr int n = 2;
 };
+template <>
+struct Vec16<__half> {
+  static constexpr int n = 8;
+};
 
 template <typename TG>
 __device__ __forceinline__ void load16(const TG* p, float* out);
@@ -253,6 +266,19 @@ __device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, fl
   }
 }
 
+template <>
+__device__ __forceinline__ void load16<__half>(const __half* p, float* out) {
+  const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 h2 = *reinterpret_cast<const __half2*>(&w[i]);
+    const float2 f2 = __half22float2(h2);
+    out[2 * i] = f2.x;
+    out[2 * i + 1] = f2.y;
+  }
+}
+
 template <typename TG, typename TI>
 __global__ void __launch_bounds__(256)
     k_ghat_matvec_tiled(const TG* __restrict__ ghat, const int32_t* __restrict__ tile_block,
@@ -260,12 +286,14 @@ __global__ void __launch_bounds__(256)
                         const int64_t* __restrict__ gq1, const int64_t* __restrict__ gcol_ptr,
                         const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
                         const int32_t* __restrict__ gcols,
-                        const TI* __restrict__ v, TI* __restrict__ w) {
+                        const TI* __restrict__ v, TI* __restrict__ w, const KScal* __restrict__ sc,
+                        const int32_t* __restrict__ block_sys) {
   using AT = typename Acc<TG>::type;
   constexpr int VN = Vec16<TG>::n;
   extern __shared__ unsigned char smem_raw[];
   AT* xs = reinterpret_cast<AT*>(smem_raw);
   const int32_t b = tile_block[blockIdx.x];
+  if (sc && !sc[block_sys[b]].active) return;  // this system's inner solve has stopped
   const int64_t r0 = tile_row[blockIdx.x];
   const int64_t c0 = gcol_ptr[b];
   const int64_t nc = gcol_ptr[b + 1] - c0;
@@ -390,7 +418,7 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
                               int32_t ntiles, int64_t max_cols, const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
-                              cudaStream_t s) {
+                              const KScal* sc, const int32_t* block_sys, cudaStream_t s) {
   if (ntiles <= 0) return;
   using AT = typename Acc<TG>::type;
   const size_t sm = (size_t)std::max<int64_t>(max_cols, 1) * sizeof(AT);
@@ -398,7 +426,8 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
     cudaFuncSetAttribute(k_ghat_matvec_tiled<TG, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
   k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, gq0, gq1,
-                                                       gcol_ptr, ghat_off, gld, gcols, v, w);
+                                                       gcol_ptr, ghat_off, gld, gcols, v, w, sc,
+                                                       block_sys);
 }
 
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s) {
@@ -426,12 +455,15 @@ DDPS_INST_S(float)
   template void launch_ghat_matvec_tiled<TG, TI>(const TG*, const int32_t*, const int32_t*, int32_t, \
                                                  int64_t, const int64_t*, const int64_t*,        \
                                                  const int64_t*, const int64_t*, const int64_t*, \
-                                                 const int32_t*, const TI*, TI*, cudaStream_t);
+                                                 const int32_t*, const TI*, TI*, const KScal*,   \
+                                                 const int32_t*, cudaStream_t);
 DDPS_INST_MV(double, double)
 DDPS_INST_MV(float, double)
 DDPS_INST_MV(float, float)
 DDPS_INST_MV(__nv_bfloat16, float)
 DDPS_INST_MV(__nv_bfloat16, double)
+DDPS_INST_MV(__half, float)
+DDPS_INST_MV(__half, double)
 
 #define DDPS_INST_MV0(TG, TI)                                                                    \
   template void launch_ghat_matvec<TG, TI>(const TG*, const int32_t*, const int64_t*,           \
@@ -442,5 +474,7 @@ DDPS_INST_MV0(float, double)
 DDPS_INST_MV0(float, float)
 DDPS_INST_MV0(__nv_bfloat16, float)
 DDPS_INST_MV0(__nv_bfloat16, double)
+DDPS_INST_MV0(__half, float)
+DDPS_INST_MV0(__half, double)
 
 }  // namespace ddps

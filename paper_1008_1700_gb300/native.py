@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libddps.so")
 
-DDPS_FP64, DDPS_FP32, DDPS_BF16, DDPS_BF16X3 = 0, 1, 2, 3
+DDPS_FP64, DDPS_FP32, DDPS_BF16, DDPS_BF16X3, DDPS_FP16 = 0, 1, 2, 3, 4
 DDPS_DROP_NONE, DDPS_DROP_COLUMN, DDPS_DROP_ABS = 0, 1, 2
 STATUS = {0: "DDPS_OK", 1: "DDPS_ERR_INVALID_ARG", 2: "DDPS_ERR_SINGULAR_BLOCK",
           3: "DDPS_ERR_NOT_CONVERGED", 4: "DDPS_ERR_OUT_OF_MEMORY", 5: "DDPS_ERR_CUDA",
