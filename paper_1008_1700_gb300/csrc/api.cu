@@ -53,6 +53,7 @@ struct LevelSplit {
   // fronts [pf_ptr[p], pf_ptr[p+1]) of lu_panel_fronts and tiles
   // [pt_ptr[p], pt_ptr[p+1]) of lu_tile_front / lu_tile_ij
   std::vector<int64_t> pf_ptr, pt_ptr;
+  int32_t inv_first = 0, inv_ntiles = 0;  // multi-CTA inverse tiles of the large fronts
 };
 
 struct ddps_handle {
@@ -107,6 +108,9 @@ struct ddps_handle {
   int32_t* lu_order = nullptr;
   std::vector<LevelSplit> split;
   int32_t *lu_panel_fronts = nullptr, *lu_tile_front = nullptr, *lu_tile_ij = nullptr;
+  int32_t *inv_tile_front = nullptr, *inv_tile_cb = nullptr;
+  int64_t* inv_off = nullptr;  // per front, offset of its 2 k^2 inverse entries in inv
+  void* inv = nullptr;
   // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
   int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
   std::vector<int32_t> tk_ptr, tr_ptr;
@@ -322,8 +326,10 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
                               (int32_t)(ls.pt_ptr[pstep + 1] - ls.pt_ptr[pstep]), j0, arena, s);
         h->launches += 2;
       }
-      launch_tri_inverse<T>(h->F, h->lu_order + ls.first + ls.nsmall, ls.nlarge, h->max_k, arena, s);
-      h->launches++;
+      launch_tri_inverse_mc<T>(h->F, h->inv_tile_front + ls.inv_first, h->inv_tile_cb + ls.inv_first,
+                               ls.inv_ntiles, h->lu_order + ls.first + ls.nsmall, ls.nlarge, h->max_k,
+                               arena, (T*)h->inv, h->inv_off, s);
+      h->launches += 2;
     }
   }
   launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
@@ -881,7 +887,9 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
   {
     const int small = h->opt.factor_prec == DDPS_FP64 ? small_front_max<double>() : small_front_max<float>();
-    std::vector<int32_t> order, pfronts, tfront, tij;
+    std::vector<int32_t> order, pfronts, tfront, tij, ivf, ivc;
+    std::vector<int64_t> ioff(A.f_k.size(), 0);
+    int64_t inv_total = 0;
     h->split.assign(A.nlevels, LevelSplit{});
     for (int L = 0; L < A.nlevels; ++L) {
       LevelSplit& ls = h->split[L];
@@ -903,6 +911,18 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
           kmax = std::max(kmax, A.f_k[f]);
         }
       }
+      // multi-CTA inverse tiles and scratch of the large fronts
+      ls.inv_first = (int32_t)ivf.size();
+      for (int32_t i = ls.first + ls.nsmall; i < (int32_t)order.size(); ++i) {
+        const int32_t f = order[i];
+        ioff[f] = inv_total;
+        inv_total += 2 * (int64_t)A.f_k[f] * A.f_k[f];
+        for (int32_t cb = 0; cb * kInvBlock < A.f_k[f]; ++cb) {
+          ivf.push_back(f);
+          ivc.push_back(cb);
+        }
+      }
+      ls.inv_ntiles = (int32_t)ivf.size() - ls.inv_first;
       // panel steps of the large fronts
       const int npanel = (kmax + kLuPanel - 1) / kLuPanel;
       ls.pf_ptr.assign(1, (int64_t)pfronts.size());
@@ -926,6 +946,10 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       }
     }
     h->lu_order = dupload(h, order);
+    h->inv_tile_front = dupload(h, ivf);
+    h->inv_tile_cb = dupload(h, ivc);
+    h->inv_off = dupload(h, ioff);
+    h->inv = dalloc_bytes(h, std::max<int64_t>(inv_total, 1) * (int64_t)prec_size(h->opt.factor_prec));
     h->lu_panel_fronts = dupload(h, pfronts);
     h->lu_tile_front = dupload(h, tfront);
     h->lu_tile_ij = dupload(h, tij);

@@ -319,6 +319,123 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Triangular inverses of large fronts with many CTAs: CTA (front, column
+// block of 64) computes those columns of L11^-1 (forward substitution over
+// 64-row tiles; the rows already solved enter through a tile GEMM) or of
+// U11^-1 (backward substitution), out of place into `inv` (k x k column-major
+// per front, at inv_off[f]); k_tri_inverse_copy then writes the strictly
+// lower part of L11^-1 and the upper part of U11^-1 back into the front.
+// ---------------------------------------------------------------------------
+constexpr int IB = 64;  // columns per CTA and rows per tile
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_tri_inverse_mc(DevFronts F, const int32_t* __restrict__ tile_front,
+                     const int32_t* __restrict__ tile_cb, const T* __restrict__ arena,
+                     T* __restrict__ inv, const int64_t* __restrict__ inv_off) {
+  const int32_t f = tile_front[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const int j0 = tile_cb[blockIdx.x] * IB;
+  const bool upper = blockIdx.y == 1;
+  const T* __restrict__ A = arena + F.arena[f];
+  T* __restrict__ X = inv + inv_off[f] + (upper ? (int64_t)k * k : 0);
+  const int tid = threadIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
+  T(*Bs)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * IB * (NB + 1));
+  T(*Ts)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * (IB * (NB + 1) + NB * (IB + 1)));
+  const int tr = tid % 16, tc = tid / 16;
+  const int ntile_rows = upper ? (min(j0 + IB, k) + IB - 1) / IB : (k - j0 + IB - 1) / IB;
+  for (int it = 0; it < ntile_rows; ++it) {
+    // lower: row tiles from j0 downwards; upper: from the diagonal tile upwards
+    const int i0 = upper ? ((min(j0 + IB, k) - 1) / IB - it) * IB : j0 + it * IB;
+    // acc = sum over the solved rows l of A(i0.., l) X(l, j0..)
+    const int l_begin = upper ? i0 + IB : j0;
+    const int l_end = upper ? min(j0 + IB, k) : i0;
+    T acc[4][4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = T(0);
+    for (int l0 = l_begin; l0 < l_end; l0 += NB) {
+      for (int t = tid; t < IB * NB; t += blockDim.x) {
+        const int r = t % IB, q = t / IB;
+        const int gi = i0 + r, gl = l0 + q;
+        As[r][q] = (gi < k && gl < l_end) ? A[gi + (int64_t)gl * m] : T(0);
+        const int q2 = t % NB, c2 = t / NB;
+        const int gl2 = l0 + q2, gj = j0 + c2;
+        Bs[q2][c2] = (gl2 < l_end && gj < k) ? X[gl2 + (int64_t)gj * k] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < NB; ++q) {
+        T lv[4], uv[4];
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) lv[a2] = As[tr + 16 * a2][q];
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) uv[b2] = Bs[q][tc + 16 * b2];
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] += lv[a2] * uv[b2];
+      }
+      __syncthreads();
+    }
+    // T = E - acc on the tile, then the triangular solve inside the tile
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) {
+        const int r = tr + 16 * a2, c = tc + 16 * b2;
+        Ts[r][c] = ((i0 + r == j0 + c) ? T(1) : T(0)) - acc[a2][b2];
+      }
+    __syncthreads();
+    const int rows = min(IB, k - i0);
+    if (!upper) {
+      for (int r = 0; r < rows; ++r) {  // unit diagonal: row r is final now
+        for (int t = tid; t < (rows - r - 1) * IB; t += blockDim.x) {
+          const int r2 = r + 1 + t / IB, c = t % IB;
+          Ts[r2][c] -= A[(i0 + r2) + (int64_t)(i0 + r) * m] * Ts[r][c];
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int r = rows - 1; r >= 0; --r) {
+        const T d = A[(i0 + r) + (int64_t)(i0 + r) * m];
+        for (int c = tid; c < IB; c += blockDim.x) Ts[r][c] /= d;
+        __syncthreads();
+        for (int t = tid; t < r * IB; t += blockDim.x) {
+          const int r2 = t / IB, c = t % IB;
+          Ts[r2][c] -= A[(i0 + r2) + (int64_t)(i0 + r) * m] * Ts[r][c];
+        }
+        __syncthreads();
+      }
+    }
+    for (int t = tid; t < IB * IB; t += blockDim.x) {
+      const int r = t % IB, c = t / IB;
+      if (r < rows && j0 + c < k) X[(i0 + r) + (int64_t)(j0 + c) * k] = Ts[r][c];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_tri_inverse_copy(DevFronts F, const int32_t* __restrict__ list,
+                                   T* __restrict__ arena, const T* __restrict__ inv,
+                                   const int64_t* __restrict__ inv_off) {
+  const int32_t f = list[blockIdx.y];
+  const int32_t k = F.k[f], m = F.m[f];
+  T* __restrict__ A = arena + F.arena[f];
+  const T* __restrict__ X = inv + inv_off[f];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)k * k;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    // lower inverse sits in the first k*k entries, upper inverse in the next k*k
+    A[i + (int64_t)j * m] = i > j ? X[t] : X[(int64_t)k * k + t];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Small fronts (m*m entries fit in shared memory): partial LU and the
 // inversion of the diagonal triangles done in shared memory by one CTA, then
 // written back once.  Same arithmetic as k_front_lu followed by
@@ -546,6 +663,20 @@ void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* t
 }
 
 template <typename T>
+void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t* tile_cb,
+                           int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
+                           T* inv, const int64_t* inv_off, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  const size_t sm = sizeof(T) * ((size_t)IB * (NB + 1) + (size_t)NB * (IB + 1) + (size_t)IB * (IB + 1));
+  cudaFuncSetAttribute(k_tri_inverse_mc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_tri_inverse_mc<T><<<dim3(ntiles, 2), kThreads, sm, s>>>(F, tile_front, tile_cb, arena, inv,
+                                                             inv_off);
+  const int64_t per = (int64_t)max_k * max_k;
+  const int gx = (int)std::min<int64_t>(std::max<int64_t>((per + kThreads - 1) / kThreads, 1), 256);
+  k_tri_inverse_copy<T><<<dim3(gx, nf), kThreads, 0, s>>>(F, list, arena, inv, inv_off);
+}
+
+template <typename T>
 void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, T* arena,
                            const double* rownorm_new, double pivot_tol, long long* err,
                            cudaStream_t s) {
@@ -587,6 +718,9 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
                                       cudaStream_t);                                            \
   template void launch_front_lu_small<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,      \
                                          const double*, double, long long*, cudaStream_t);      \
+  template void launch_tri_inverse_mc<T>(DevFronts, const int32_t*, const int32_t*, int32_t,    \
+                                         const int32_t*, int32_t, int32_t, T*, T*,              \
+                                         const int64_t*, cudaStream_t);                         \
   template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,            \
                                    const double*, double, long long*, cudaStream_t);            \
   template void launch_lu_trailing<T>(DevFronts, const int32_t*, const int32_t*, int32_t,      \

@@ -65,6 +65,13 @@ void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t
 // trailing update over tiles of 64 x 64 (tile_ij = (ti << 16) | tj).
 constexpr int kLuPanel = 32;
 constexpr int kLuTile = 64;
+// Multi-CTA triangular inverses of large fronts: tile_front / tile_cb list
+// (front, 64-column block); inv holds 2 k^2 entries per front at inv_off.
+constexpr int kInvBlock = 64;
+template <typename T>
+void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t* tile_cb,
+                           int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
+                           T* inv, const int64_t* inv_off, cudaStream_t s);
 template <typename T>
 void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, T* arena,
                      const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
