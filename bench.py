@@ -47,10 +47,12 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cd3d_64_slabs16",
-                    choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8"])
+                    choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8", "cd2d_batch256",
+                             "randband_1m", "cd3d_48_seq"])
     ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64"], default="mixed")
-    ap.add_argument("--fp64-steps", type=int, default=1,
-                    help="steps of the plain-FP64 comparison run (0 skips it)")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="steps of the plain-FP64 comparison run (0 skips it; default 1, "
+                         "0 for randband_1m whose FP64 factor takes over a minute)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -61,13 +63,30 @@ def parse_args():
 # ----------------------------------------------------------------------------
 
 def make_workload(name):
+    """Returns (problem, sys_block_ptr or None, number of systems, drop rule or None)."""
+    import types
+
+    import numpy as np
+
     import workloads as W
     if name == "cd3d_64_slabs16":
-        return W.cfg2()
+        return W.cfg2(), None, 1, None
     if name == "cd2d_64_p4":
-        return W.cfg1()
-    if name == "cd3d_48_slabs8":
-        return W.cfg5(1)
+        return W.cfg1(), None, 1, None
+    if name in ("cd3d_48_slabs8", "cd3d_48_seq"):
+        return W.cfg5(1), None, 1, None
+    if name == "randband_1m":
+        return W.cfg4(), None, 1, ("abs", 1e-4)
+    if name == "cd2d_batch256":
+        from paper_1008_1700_gb300.solver import stack_systems
+        probs = W.cfg3()
+        rp, ci, v, bp, sbp, srp = stack_systems([(p.rowptr, p.colind, p.values, p.block_ptr)
+                                                 for p in probs])
+        P = types.SimpleNamespace(n=int(srp[-1]), nnz=int(rp[-1]), rowptr=rp, colind=ci, values=v,
+                                  block_ptr=bp, p=len(bp) - 1,
+                                  f=np.concatenate([q.f for q in probs]),
+                                  x_true=np.concatenate([q.x_true for q in probs]), systems=probs)
+        return P, sbp, len(probs), None
     raise ValueError(name)
 
 
@@ -171,7 +190,8 @@ def algorithmic_work(sizes, P, form, steps, prof):
     out["front_lu"] = ("flops", sizes["factor_flops"] * steps)
     out["spike_fwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
     out["spike_bwd"] = ("flops", sizes["spike_flops"] / 2 * steps)
-    out["assemble"] = ("bytes", (nnz * (8 + 8) + sizes["factor_entries"] * sf) * steps)
+    # values and map read, front entries written, pivot thresholds (one pass over A)
+    out["assemble"] = ("bytes", (nnz * (8 + 8 + sf) + nnz * 20 + n * 8) * steps)
     out["ghat_extract"] = ("bytes", sizes["ghat_entries"] * (sf + sg) * steps)
     # per call of the solve phase
     calls = {k: v[1] for k, v in prof.items()}
@@ -219,6 +239,23 @@ def oracle_sample(P, nblocks=4, ncols=1024):
     return est, wall
 
 
+def oracle_batch_sample(systems, count=3):
+    """Whole oracle solves (Fig. 2 and 3, eps_in 1e-4, tol 1e-10) of the first
+    `count` systems of a batch, scaled to the batch by the number of unknowns."""
+    from oracle.ddps_oracle import DDPSOracle
+    t0 = time.perf_counter()
+    nsamp = 0
+    for p in systems[:count]:
+        DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr).solve(p.f, tol=1e-10,
+                                                                          eps_in=1e-4)
+        nsamp += p.n
+    wall = time.perf_counter() - t0
+    ntot = sum(p.n for p in systems)
+    est = wall * ntot / nsamp
+    return est, wall, ("whole oracle solves of %d of the %d systems (%.1f s wall), scaled by "
+                       "unknowns to the batch" % (count, len(systems), wall))
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -236,27 +273,39 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    P = make_workload(args.workload)
+    P, sbp, nsys, drop = make_workload(args.workload)
+    nb, nc = (1, 64) if args.workload == "randband_1m" else (2, 256)
+
+    def sample():
+        if nsys > 1:
+            e, w, _ = oracle_batch_sample(P.systems, count=1)
+            return e, w
+        return oracle_sample(P, nblocks=nb, ncols=nc)
+
     for _ in range(args.warmup):
-        oracle_sample(P, nblocks=2, ncols=256)
+        sample()
     ests, walls = [], []
     for _ in range(args.steps):
-        e, w = oracle_sample(P, nblocks=2, ncols=256)
+        e, w = sample()
         ests.append(e)
         walls.append(w)
     sec = statistics.mean(ests)
-    value = 1.0 / sec
+    value = nsys / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
+        "config": {"workload": args.workload, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz,
+                   "blocks": P.p,
                    "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "oracle Fig. 2 steps 1-5 on 2 of the blocks with 256 spike "
-                                   "columns each, scaled to all blocks and columns; solve phase "
-                                   "not counted (per step wall %.1f s)" % statistics.mean(walls)},
+                         "sample": ("whole oracle solve of 1 of the systems, scaled by unknowns "
+                                    "to the batch" if nsys > 1 else
+                                    "oracle Fig. 2 steps 1-5 on %d of the blocks with %d spike "
+                                    "columns each, scaled to all blocks and columns; solve phase "
+                                    "not counted" % (nb, nc)) +
+                                   " (per step wall %.1f s)" % statistics.mean(walls)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -292,10 +341,12 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    P = make_workload(args.workload)
+    P, sbp, nsys, drop = make_workload(args.workload)
     opts = form_options(args.form)
+    if drop is not None:
+        opts.update(drop_mode=N.DDPS_DROP_ABS, drop_tol=drop[1])
     t0 = time.perf_counter()
-    S = Solver(P.rowptr, P.colind, P.block_ptr, **opts)
+    S = Solver(P.rowptr, P.colind, P.block_ptr, sbp, P.values if drop else None, **opts)
     analyze_ms = (time.perf_counter() - t0) * 1e3
     sizes = S.sizes
     vals = torch.tensor(P.values, device="cuda")
@@ -332,7 +383,7 @@ def run_ours(args):
     launches = S.launch_count() - launches0
     S.set_profiling(0)
     ms_max = max_over_ranks(ms)
-    value = world * args.steps / (ms_max / 1e3)
+    value = world * nsys * args.steps / (ms_max / 1e3)
 
     # accuracy of the last step against the known solution and the residual
     xh = x.cpu().numpy()
@@ -383,7 +434,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "fp64" else ("bf16x3+f16+f32+f64" if args.form == "mixed" else "f32+f64"),
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": P.n, "nnz": P.nnz, "blocks": P.p,
+        "config": {"workload": args.workload, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz,
+                   "blocks": P.p,
                    "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
                    "form": args.form, "parallelism": f"replicas{world}",
                    "l2": "working set (G^ %.1f GB) larger than L2" %
@@ -424,13 +476,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(a0.elapsed_time(a1))
-        line["e2e"] = {"value": world * args.steps / (ems / 1e3), "unit": UNIT,
+        line["e2e"] = {"value": world * nsys * args.steps / (ems / 1e3), "unit": UNIT,
                        "h2d_bytes_per_step": int(P.nnz * 8 + P.n * 8),
                        "d2h_bytes_per_step": int(P.n * 8)}
 
     # plain FP64 DDPS on the same GPU and workload (the comparison the metric names)
     if args.form != "fp64" and args.fp64_steps > 0:
-        S64 = Solver(P.rowptr, P.colind, P.block_ptr, **form_options("fp64"))
+        o64 = form_options("fp64")
+        if drop is not None:
+            o64.update(drop_mode=N.DDPS_DROP_ABS, drop_tol=drop[1])
+        S64 = Solver(P.rowptr, P.colind, P.block_ptr, sbp, P.values if drop else None, **o64)
         x64 = torch.empty_like(f)
         S64.factor(vals)
         S64.solve(f, x64)
@@ -445,7 +500,7 @@ def run_ours(args):
         b1.record(stream)
         torch.cuda.synchronize()
         fms = max_over_ranks(b0.elapsed_time(b1))
-        v64 = world * args.fp64_steps / (fms / 1e3)
+        v64 = world * nsys * args.fp64_steps / (fms / 1e3)
         line["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": fms / args.fp64_steps,
                               "relres_inf": i64["relres_inf"],
                               "outer_iterations": i64["outer_iterations"]}
@@ -454,12 +509,16 @@ def run_ours(args):
 
     # CPU oracle, bounded sample, rank 0 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, wall = oracle_sample(P, nblocks=4, ncols=1024)
-        line["cpu_baseline"] = {
-            "value": 1.0 / est, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-            "sample": "oracle Fig. 2 steps 1-5 on 4 of the %d blocks with 1024 spike columns "
+        if nsys > 1:
+            est, wall, sample = oracle_batch_sample(P.systems)
+        else:
+            nb, nc = (1, 128) if args.workload == "randband_1m" else (4, 1024)
+            est, wall = oracle_sample(P, nblocks=nb, ncols=nc)
+            sample = ("oracle Fig. 2 steps 1-5 on %d of the %d blocks with %d spike columns "
                       "each, scaled to all blocks and columns (%.1f s wall); the solve phase is "
-                      "not counted, so this overstates the oracle's solves/s" % (P.p, wall)}
+                      "not counted, so this overstates the oracle's solves/s" % (nb, P.p, nc, wall))
+        line["cpu_baseline"] = {"value": nsys / est, "unit": UNIT, "cores": cpu_threads(),
+                                "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     S.close()
@@ -467,10 +526,88 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sequence_bench(args):
+    """Time sequence of 48^3 systems, b(t) = 20 + 10 sin(2 pi t / 200), fixed
+    source: zero-guess solves of steps 1-100 train the step-change network
+    (not timed); the timed region is `steps` evaluation steps from t = 101,
+    each factor + predicted guess + solve; the same steps with a zero guess
+    are timed for comparison."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1008_1700_gb300 import Solver
+    from paper_1008_1700_gb300.learned import StepGuess
+
+    opts = form_options(args.form)
+    P0 = W.cfg5(1)
+    S = Solver(P0.rowptr, P0.colind, P0.block_ptr, **opts)
+    f = torch.tensor(P0.f, device="cuda")
+    x = torch.empty_like(f)
+    t0 = time.perf_counter()
+    zs, bs = [], []
+    for t in range(1, 101):
+        S.factor(torch.tensor(W.cfg5(t).values, device="cuda"))
+        S.set_reduced_guess(None)
+        S.solve(f, x)
+        zs.append(S.reduced_solution()[0].clone())
+        bs.append(W.cfg5_coeff(t))
+    model = StepGuess(torch.stack(zs), bs)
+    train_s = time.perf_counter() - t0
+    ts = list(range(101, 101 + args.steps))
+    vals = [torch.tensor(W.cfg5(t).values, device="cuda") for t in ts]
+    stream = torch.cuda.current_stream()
+
+    def run(learned):
+        z_prev, b_prev = zs[-1], bs[-1]
+        infos = []
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t, v in zip(ts, vals):
+            S.factor(v)
+            bt = W.cfg5_coeff(t)
+            S.set_reduced_guess(model.predict(z_prev, bt, b_prev) if learned else None)
+            _, info = S.solve(f, x)
+            infos.append(info)
+            z_prev = S.reduced_solution()[0].clone()
+            b_prev = bt
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), infos
+
+    run(True)  # warm-up of the prediction path
+    ms_l, inf_l = run(True)
+    ms_0, inf_0 = run(False)
+    line = {
+        "metric": METRIC, "value": args.steps / (ms_l / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": ms_l / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f16+f32+f64", "data": "synthetic",
+        "config": {"workload": "cd3d_48_seq", "n": P0.n, "blocks": P0.p,
+                   "train_steps": "1-100", "timed_steps": f"{ts[0]}-{ts[-1]}", "form": args.form},
+        "train_s": round(train_s, 2),
+        "learned": {"first_inner_mean": float(np.mean([i["first_inner_iters"] for i in inf_l])),
+                    "inner_mean": float(np.mean([i["inner_iterations"] for i in inf_l])),
+                    "relres_max": float(max(i["relres_inf"] for i in inf_l))},
+        "zero_guess": {"value": args.steps / (ms_0 / 1e3), "ms_per_step": ms_0 / args.steps,
+                       "first_inner_mean": float(np.mean([i["first_inner_iters"] for i in inf_0])),
+                       "inner_mean": float(np.mean([i["inner_iterations"] for i in inf_0])),
+                       "relres_max": float(max(i["relres_inf"] for i in inf_0))},
+    }
+    print(json.dumps(line), flush=True)
+    S.close()
+
+
 def main():
     args = parse_args()
+    if args.fp64_steps is None:
+        args.fp64_steps = 0 if args.workload == "randband_1m" else 1
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cd3d_48_seq":
+        run_sequence_bench(args)
     else:
         run_ours(args)
 

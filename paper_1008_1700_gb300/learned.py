@@ -99,6 +99,30 @@ def _beta(b, b_mean, b_scale):
     return (b - b_mean) / b_scale
 
 
+class StepGuess:
+    """The ``mlp_warm`` strategy as a reusable predictor: trained on the
+    reduced solutions z^(t) of consecutive steps, it predicts z^(t) from
+    z^(t-1) and the normalised coefficients of steps t and t-1."""
+
+    def __init__(self, Z, b, hidden=256, layers=3, seed=1, fit_iters=2000, lr=1e-3):
+        b = np.asarray(b, dtype=np.float64)
+        self.b_mean = float(b.mean())
+        self.b_scale = float(max(b.std(), 1e-12))
+        D = Z[1:] - Z[:-1]
+        self.scale = float(D.abs().max().item()) or 1.0
+        bb = _beta(b, self.b_mean, self.b_scale)
+        X = torch.tensor(np.stack([bb[1:], (bb[1:] - bb[:-1]) * 10.0], axis=1),
+                         dtype=torch.float32, device=Z.device)
+        self.net = GuessNet(2, Z.shape[1], hidden, layers, seed)
+        self.losses = self.net.fit(X, (D / self.scale).to(torch.float32), iters=fit_iters, lr=lr)
+
+    def predict(self, z_prev, b_t, b_prev):
+        bb = _beta(b_t, self.b_mean, self.b_scale)
+        bp = _beta(b_prev, self.b_mean, self.b_scale)
+        xin = torch.tensor([[bb, (bb - bp) * 10.0]], dtype=torch.float32, device=z_prev.device)
+        return (z_prev + self.scale * self.net.forward(xin)[0].to(torch.float64)).contiguous()
+
+
 def run_sequence(make_problem, coeff, t_train, t_eval, solver_opts, modes=("zero", "mlp"),
                  hidden=256, layers=3, fit_iters=2000, lr=1e-3, seed=0, log=None):
     """Solves the sequence: zero-guess solves on ``t_train`` collect (g^, z^);
