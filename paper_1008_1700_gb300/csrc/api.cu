@@ -3,7 +3,9 @@
 // kernels of factor.cu, solve.cu and krylov.cu; this file only sequences them.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -117,6 +119,17 @@ struct ddps_handle {
   // tensor-core spikes: A operands packed as bf16 blocks, byte offsets per op and tile
   unsigned char* atc = nullptr;
   int64_t* tc_aoff[4] = {nullptr, nullptr, nullptr, nullptr};
+  // Sparse forward sweep of the spikes.  Each block's coupling columns are
+  // ordered by the (postorder) front of their first entry; chunk c of NR
+  // panel columns then only touches the fronts on the paths from its
+  // columns' fronts to the roots: fw_active[c * nfronts + f] flags them, and
+  // the forward launches of chunk c and depth L use lists of those fronts
+  // and their tiles (index (c * nlevels + L) into the *_ptr vectors).
+  int32_t* gperm = nullptr;  // panel column -> coupling column, per block
+  uint8_t* fw_active = nullptr;
+  int32_t *fw_g = nullptr, *fw_kf = nullptr, *fw_km = nullptr, *fw_rf = nullptr, *fw_rm = nullptr;
+  int64_t *fw_ka = nullptr, *fw_ra = nullptr;  // packed-A offsets (tensor-core path)
+  std::vector<int64_t> fw_g_ptr, fw_k_ptr, fw_r_ptr;
   int32_t tc_max_kt[4] = {0, 0, 0, 0};
   int tc_passes = 0;
   // segments
@@ -267,14 +280,12 @@ void check_launch() {
 // One spike GEMM op over a tile list: tensor cores for FP32 factors with
 // bf16 spike products, SIMT otherwise.
 template <typename T>
-void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, int32_t first,
+void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, const int64_t* ta,
               int32_t nt, const T* arena, int64_t j0, T* X, T* Tb, cudaStream_t s) {
-  tf += first;
-  tm += first;
   if constexpr (std::is_same<T, float>::value) {
     if (h->tc_passes) {
-      launch_spike_gemm_tc(op, h->tc_passes, h->F, tf, tm, h->tc_aoff[op] + first, h->atc, nt,
-                           h->block_ncols, j0, h->NR, X, Tb, h->derr, h->opt.debug_wait_timeout, s);
+      launch_spike_gemm_tc(op, h->tc_passes, h->F, tf, tm, ta, h->atc, nt, h->block_ncols, j0,
+                           h->NR, X, Tb, h->derr, h->opt.debug_wait_timeout, s);
       return;
     }
   }
@@ -352,31 +363,39 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
     T* X = (T*)h->X;
     T* Tb = (T*)h->U;
     const int32_t NR = h->NR;
-    for (int64_t j0 = 0; j0 < A.max_rhs; j0 += NR) {
+    const int64_t nf = (int64_t)A.f_k.size();
+    for (int64_t j0 = 0, c = 0; j0 < A.max_rhs; j0 += NR, ++c) {
       CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
       launch_spike_rhs<T>(h->rt_rownew, h->rt_rhscol, h->rt_src, h->nrt, h->vals, j0, NR, X, s);
       h->launches++;
       for (int L = A.nlevels - 1; L >= 0; --L) {
         Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
-        launch_spike_gather<T>(h->F, h->level_fronts + A.level_ptr[L],
-                               A.level_ptr[L + 1] - A.level_ptr[L], h->block_ncols, j0, NR, X, Tb, s);
-        spike_op<T>(h, OP_FWD_LINV, h->tk_front, h->tk_m0, h->tk_ptr[L],
-                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
-        spike_op<T>(h, OP_FWD_L21, h->tr_front, h->tr_m0, h->tr_ptr[L],
-                    h->tr_ptr[L + 1] - h->tr_ptr[L], arena, j0, X, Tb, s);
+        const int64_t q = c * A.nlevels + L;
+        launch_spike_gather<T>(h->F, h->fw_g + h->fw_g_ptr[q],
+                               (int32_t)(h->fw_g_ptr[q + 1] - h->fw_g_ptr[q]), h->block_ncols, j0,
+                               NR, X, Tb, h->fw_active + c * nf, s);
+        spike_op<T>(h, OP_FWD_LINV, h->fw_kf + h->fw_k_ptr[q], h->fw_km + h->fw_k_ptr[q],
+                    h->fw_ka ? h->fw_ka + h->fw_k_ptr[q] : nullptr, (int32_t)(h->fw_k_ptr[q + 1] - h->fw_k_ptr[q]),
+                    arena, j0, X, Tb, s);
+        spike_op<T>(h, OP_FWD_L21, h->fw_rf + h->fw_r_ptr[q], h->fw_rm + h->fw_r_ptr[q],
+                    h->fw_ra ? h->fw_ra + h->fw_r_ptr[q] : nullptr, (int32_t)(h->fw_r_ptr[q + 1] - h->fw_r_ptr[q]),
+                    arena, j0, X, Tb, s);
         h->launches += 3;
       }
       for (int L = 0; L < A.nlevels; ++L) {
         Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
-        spike_op<T>(h, OP_BWD_U12, h->tk_front, h->tk_m0, h->tk_ptr[L],
-                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
-        spike_op<T>(h, OP_BWD_UINV, h->tk_front, h->tk_m0, h->tk_ptr[L],
-                    h->tk_ptr[L + 1] - h->tk_ptr[L], arena, j0, X, Tb, s);
+        const int32_t first = h->tk_ptr[L], nt = h->tk_ptr[L + 1] - h->tk_ptr[L];
+        spike_op<T>(h, OP_BWD_U12, h->tk_front + first, h->tk_m0 + first,
+                    h->tc_aoff[OP_BWD_U12] ? h->tc_aoff[OP_BWD_U12] + first : nullptr, nt, arena,
+                    j0, X, Tb, s);
+        spike_op<T>(h, OP_BWD_UINV, h->tk_front + first, h->tk_m0 + first,
+                    h->tc_aoff[OP_BWD_UINV] ? h->tc_aoff[OP_BWD_UINV] + first : nullptr, nt, arena,
+                    j0, X, Tb, s);
         h->launches += 2;
       }
       Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
       launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, h->gld,
-                                 m, j0, NR, X, (TG*)h->ghat, s);
+                                 h->gperm, m, j0, NR, X, (TG*)h->ghat, s);
       h->launches++;
     }
   }
@@ -783,6 +802,102 @@ ddps_status fail(ddps_handle* h, const Fail& e) {
   return e.st;
 }
 
+// Column order, active fronts and forward launch lists of the sparse
+// forward sweep (see the handle's fields).  kf/km and rf/rm are the tile
+// lists over the pivot rows and over the update rows of every front,
+// tc_off the packed-A offsets per op (empty without tensor cores).
+void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
+                          const std::vector<int32_t>& km, const std::vector<int32_t>& rf,
+                          const std::vector<int32_t>& rm,
+                          const std::vector<std::vector<int64_t>>& tc_off) {
+  const Analysis& A = h->A;
+  const int64_t nf = (int64_t)A.f_k.size();
+  const int64_t n = A.n;
+  std::vector<int32_t> owner(n, -1);
+  for (int64_t f = 0; f < nf; ++f)
+    for (int32_t i = 0; i < A.f_k[f]; ++i) owner[A.f_row0[f] + i] = (int32_t)f;
+  // entries of each coupling column (global column slot gcol_ptr[b] + j): their fronts
+  const int64_t ncol_all = A.gcol_ptr[A.p];
+  std::vector<int32_t> key(ncol_all, INT32_MAX);
+  std::vector<std::vector<int32_t>> col_fronts(ncol_all);
+  std::vector<int32_t> row_block(n);
+  for (int32_t b = 0; b < A.p; ++b)
+    for (int64_t i = A.block_ptr[b]; i < A.block_ptr[b + 1]; ++i) row_block[i] = b;
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t e = A.rt_rowptr[i]; e < A.rt_rowptr[i + 1]; ++e) {
+      const int64_t slot = A.gcol_ptr[row_block[i]] + A.rt_rhscol[e];
+      const int32_t f = owner[A.rt_rownew[e]];
+      col_fronts[slot].push_back(f);
+      key[slot] = std::min(key[slot], f);
+    }
+  // order each block's columns by the first front they touch
+  std::vector<int32_t> gperm(ncol_all), inv(ncol_all);
+  for (int32_t b = 0; b < A.p; ++b) {
+    const int64_t c0 = A.gcol_ptr[b], nc = A.gcol_ptr[b + 1] - c0;
+    std::vector<int32_t> ord(nc);
+    for (int64_t j = 0; j < nc; ++j) ord[j] = (int32_t)j;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t bb) { return key[c0 + a] < key[c0 + bb]; });
+    for (int64_t pcol = 0; pcol < nc; ++pcol) {
+      gperm[c0 + pcol] = ord[pcol];
+      inv[c0 + ord[pcol]] = (int32_t)pcol;
+    }
+  }
+  h->gperm = dupload(h, gperm);
+  std::vector<int32_t> rhscol(A.rt_rhscol.size());
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t e = A.rt_rowptr[i]; e < A.rt_rowptr[i + 1]; ++e)
+      rhscol[e] = inv[A.gcol_ptr[row_block[i]] + A.rt_rhscol[e]];
+  CK(cudaMemcpy(h->rt_rhscol, rhscol.data(), rhscol.size() * sizeof(int32_t),
+                cudaMemcpyHostToDevice));
+  // per chunk: active fronts, then per depth the gather list and the forward tiles
+  const int64_t NR = std::max<int32_t>(h->NR, 1);
+  const int64_t nchunks = A.max_rhs > 0 ? (A.max_rhs + NR - 1) / NR : 0;
+  std::vector<uint8_t> active((size_t)std::max<int64_t>(nchunks, 1) * nf, 0);
+  std::vector<int32_t> g, kfo, kmo, rfo, rmo;
+  std::vector<int64_t> kao, rao;
+  h->fw_g_ptr.assign(1, 0);
+  h->fw_k_ptr.assign(1, 0);
+  h->fw_r_ptr.assign(1, 0);
+  const bool tc = !tc_off.empty();
+  for (int64_t c = 0; c < nchunks; ++c) {
+    uint8_t* act = active.data() + c * nf;
+    for (int32_t b = 0; b < A.p; ++b) {
+      const int64_t c0 = A.gcol_ptr[b], nc = A.gcol_ptr[b + 1] - c0;
+      for (int64_t pcol = c * NR; pcol < std::min<int64_t>((c + 1) * NR, nc); ++pcol)
+        for (int32_t f : col_fronts[c0 + gperm[c0 + pcol]])
+          for (int32_t a = f; a >= 0 && !act[a]; a = A.f_parent[a]) act[a] = 1;
+    }
+    for (int L = 0; L < A.nlevels; ++L) {
+      for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q)
+        if (act[A.level_fronts[q]]) g.push_back(A.level_fronts[q]);
+      for (int32_t t = h->tk_ptr[L]; t < h->tk_ptr[L + 1]; ++t)
+        if (act[kf[t]]) {
+          kfo.push_back(kf[t]);
+          kmo.push_back(km[t]);
+          if (tc) kao.push_back(tc_off[OP_FWD_LINV][t]);
+        }
+      for (int32_t t = h->tr_ptr[L]; t < h->tr_ptr[L + 1]; ++t)
+        if (act[rf[t]]) {
+          rfo.push_back(rf[t]);
+          rmo.push_back(rm[t]);
+          if (tc) rao.push_back(tc_off[OP_FWD_L21][t]);
+        }
+      h->fw_g_ptr.push_back((int64_t)g.size());
+      h->fw_k_ptr.push_back((int64_t)kfo.size());
+      h->fw_r_ptr.push_back((int64_t)rfo.size());
+    }
+  }
+  h->fw_active = dupload(h, active);
+  h->fw_g = dupload(h, g);
+  h->fw_kf = dupload(h, kfo);
+  h->fw_km = dupload(h, kmo);
+  h->fw_rf = dupload(h, rfo);
+  h->fw_rm = dupload(h, rmo);
+  h->fw_ka = tc ? dupload(h, kao) : nullptr;
+  h->fw_ra = tc ? dupload(h, rao) : nullptr;
+}
+
 void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) {
   Analysis& A = h->A;
   const int64_t n = A.n, m = (int64_t)A.c.size();
@@ -980,6 +1095,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->tr_front = dupload(h, rf);
     h->tr_m0 = dupload(h, rm);
     const int sp = h->opt.spike_prec;
+    std::vector<std::vector<int64_t>> tc_off_host, tc_off_local(4);
     if ((sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0) {
       h->tc_passes = sp == DDPS_BF16X3 ? 3 : 1;
       const int BK = tc_tile_bk();
@@ -997,9 +1113,12 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
           h->tc_max_kt[op] = std::max(h->tc_max_kt[op], nk);
         }
         h->tc_aoff[op] = dupload(h, off);
+        tc_off_local[op] = off;
       }
       h->atc = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(run, 16));
+      tc_off_host.swap(tc_off_local);
     }
+    build_sparse_forward(h, kf, km, rf, rm, tc_off_host);
   }
   // segments
   h->nseg = A.nsys;

@@ -566,7 +566,7 @@ template <typename T, typename TG>
 __global__ void k_ghat_extract(const int32_t* __restrict__ qblock, const int32_t* __restrict__ c_rownew,
                                const int64_t* __restrict__ gq0, const int64_t* __restrict__ gcol_ptr,
                                const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
-                               int64_t m, int64_t j0, int32_t NR,
+                               const int32_t* __restrict__ gperm, int64_t m, int64_t j0, int32_t NR,
                                const T* __restrict__ X, TG* __restrict__ ghat) {
   const int64_t total = m * NR;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -578,7 +578,7 @@ __global__ void k_ghat_extract(const int32_t* __restrict__ qblock, const int32_t
     const int64_t j = j0 + jj;
     if (j >= ncol) continue;
     const T v = X[(int64_t)c_rownew[q] * NR + jj];
-    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + j] = (TG)(float)v;
+    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + gperm[gcol_ptr[b] + j]] = (TG)(float)v;
   }
 }
 
@@ -588,7 +588,8 @@ __global__ void k_ghat_extract<double, double>(const int32_t* __restrict__ qbloc
                                                const int64_t* __restrict__ gq0,
                                                const int64_t* __restrict__ gcol_ptr,
                                                const int64_t* __restrict__ ghat_off,
-                                               const int64_t* __restrict__ gld, int64_t m,
+                                               const int64_t* __restrict__ gld,
+                                               const int32_t* __restrict__ gperm, int64_t m,
                                                int64_t j0, int32_t NR, const double* __restrict__ X,
                                                double* __restrict__ ghat) {
   const int64_t total = m * NR;
@@ -600,7 +601,8 @@ __global__ void k_ghat_extract<double, double>(const int32_t* __restrict__ qbloc
     const int64_t ncol = gcol_ptr[b + 1] - gcol_ptr[b];
     const int64_t j = j0 + jj;
     if (j >= ncol) continue;
-    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + j] = X[(int64_t)c_rownew[q] * NR + jj];
+    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + gperm[gcol_ptr[b] + j]] =
+        X[(int64_t)c_rownew[q] * NR + jj];
   }
 }
 
@@ -700,10 +702,11 @@ void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t ma
 template <typename T, typename TG>
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
-                         int64_t m, int64_t j0, int32_t NR, const T* X, TG* ghat, cudaStream_t s) {
+                         const int32_t* gperm, int64_t m, int64_t j0, int32_t NR, const T* X,
+                         TG* ghat, cudaStream_t s) {
   if (m <= 0) return;
   k_ghat_extract<T, TG><<<grid_for(m * NR, kThreads), kThreads, 0, s>>>(
-      qblock, c_rownew, gq0, gcol_ptr, ghat_off, gld, m, j0, NR, X, ghat);
+      qblock, c_rownew, gq0, gcol_ptr, ghat_off, gld, gperm, m, j0, NR, X, ghat);
 }
 
 #define DDPS_INST_T(T)                                                                          \
@@ -732,7 +735,8 @@ DDPS_INST_T(float)
 #define DDPS_INST_TG(T, TG)                                                                     \
   template void launch_ghat_extract<T, TG>(const int32_t*, const int32_t*, const int64_t*,     \
                                            const int64_t*, const int64_t*, const int64_t*,      \
-                                           int64_t, int64_t, int32_t, const T*, TG*, cudaStream_t);
+                                           const int32_t*, int64_t, int64_t, int32_t, const T*, \
+                                           TG*, cudaStream_t);
 
 DDPS_INST_TG(double, double)
 DDPS_INST_TG(double, float)

@@ -90,8 +90,10 @@ enum SpikeOp { OP_FWD_LINV = 0, OP_FWD_L21 = 1, OP_BWD_U12 = 2, OP_BWD_UINV = 3 
 template <typename T>
 int spike_tile_m();
 template <typename T>
+// active (per front, may be null): children with active[c] == 0 are skipped.
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
-                         int64_t j0, int32_t NR, const T* X, T* Tb, cudaStream_t s);
+                         int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
+                         cudaStream_t s);
 // spike_tc.cu: the same ops on the tensor cores (fp32 factors, bf16 operands,
 // fp32 accumulation); passes = 1 (hi*hi) or 3 (hi*hi + hi*lo + lo*hi).  A wait
 // that runs out writes error code 2 into err[0].
@@ -113,9 +115,11 @@ void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int
                        int32_t ntiles, const T* arena, const int64_t* block_ncols, int64_t j0,
                        int32_t NR, T* X, T* Tb, cudaStream_t s);
 template <typename T, typename TG>
+// Panel column j of block b holds coupling column gperm[gcol_ptr[b] + j].
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
-                         int64_t m, int64_t j0, int32_t NR, const T* X, TG* ghat, cudaStream_t s);
+                         const int32_t* gperm, int64_t m, int64_t j0, int32_t NR, const T* X,
+                         TG* ghat, cudaStream_t s);
 
 // ---- solve.cu ---------------------------------------------------------------
 template <typename T>

@@ -53,7 +53,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_spike_gather(DevFronts F, const int32_t* __restrict__ list,
                    const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
-                   const T* __restrict__ X, T* __restrict__ Tb) {
+                   const T* __restrict__ X, T* __restrict__ Tb,
+                   const uint8_t* __restrict__ active) {
   using V = typename GatherVec<T>::V;
   constexpr int VN = GatherVec<T>::n;
   const int32_t f = list[blockIdx.x];
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
     const int32_t c = F.children[ci];
+    if (active && !active[c]) continue;  // a child untouched by this chunk contributes zero
     const int32_t kc = F.k[c], rc = F.m[c] - kc;
     const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
     const T* __restrict__ Tc = Tb + (F.idx_off[c] + kc) * NR;
@@ -213,11 +215,12 @@ int spike_tile_m() {
 
 template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
-                         int64_t j0, int32_t NR, const T* X, T* Tb, cudaStream_t s) {
+                         int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
+                         cudaStream_t s) {
   if (nf <= 0) return;
   const int per = 32 * GatherVec<T>::n;
   dim3 grid(nf, (NR + per - 1) / per);
-  k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb);
+  k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb, active);
 }
 
 template <typename T>
@@ -248,7 +251,8 @@ void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int
 #define DDPS_INST_SP(T)                                                                         \
   template int spike_tile_m<T>();                                                               \
   template void launch_spike_gather<T>(DevFronts, const int32_t*, int32_t, const int64_t*,     \
-                                       int64_t, int32_t, const T*, T*, cudaStream_t);          \
+                                       int64_t, int32_t, const T*, T*, const uint8_t*,         \
+                                       cudaStream_t);                                          \
   template void launch_spike_gemm<T>(int, DevFronts, const int32_t*, const int32_t*, int32_t,  \
                                      const T*, const int64_t*, int64_t, int32_t, T*, T*,       \
                                      cudaStream_t);
