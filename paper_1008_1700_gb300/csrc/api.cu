@@ -125,7 +125,7 @@ struct ddps_handle {
   // columns' fronts to the roots: fw_active[c * nfronts + f] flags them, and
   // the forward launches of chunk c and depth L use lists of those fronts
   // and their tiles (index (c * nlevels + L) into the *_ptr vectors).
-  int32_t* gperm = nullptr;  // panel column -> coupling column, per block
+  std::vector<int32_t> gperm;  // panel column -> coupling column (G^ column order), per block
   uint8_t* fw_active = nullptr;
   int32_t *fw_g = nullptr, *fw_kf = nullptr, *fw_km = nullptr, *fw_rf = nullptr, *fw_rm = nullptr;
   int64_t *fw_ka = nullptr, *fw_ra = nullptr;  // packed-A offsets (tensor-core path)
@@ -395,7 +395,7 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       }
       Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
       launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, h->gld,
-                                 h->gperm, m, j0, NR, X, (TG*)h->ghat, s);
+                                 m, j0, NR, X, (TG*)h->ghat, s);
       h->launches++;
     }
   }
@@ -843,7 +843,15 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
       inv[c0 + ord[pcol]] = (int32_t)pcol;
     }
   }
-  h->gperm = dupload(h, gperm);
+  h->gperm = gperm;
+  // G^ keeps its columns in panel order: the matvec gathers v through the permuted column list
+  std::vector<int32_t> gcols_panel(ncol_all);
+  for (int64_t t = 0; t < ncol_all; ++t) gcols_panel[t] = A.gcols[t];
+  for (int32_t b = 0; b < A.p; ++b)
+    for (int64_t pcol = A.gcol_ptr[b]; pcol < A.gcol_ptr[b + 1]; ++pcol)
+      gcols_panel[pcol] = A.gcols[A.gcol_ptr[b] + gperm[pcol]];
+  CK(cudaMemcpy(h->gcols, gcols_panel.data(), gcols_panel.size() * sizeof(int32_t),
+                cudaMemcpyHostToDevice));
   std::vector<int32_t> rhscol(A.rt_rhscol.size());
   for (int64_t i = 0; i < n; ++i)
     for (int32_t e = A.rt_rowptr[i]; e < A.rt_rowptr[i + 1]; ++e)
@@ -1511,7 +1519,7 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
           std::memcpy(&fv, &bits, 4);
           v = fv;
         }
-        dst[i * nc + j] = v;
+        dst[i * nc + h->gperm[A.gcol_ptr[b] + j]] = v;
       }
   } catch (const Fail& e) {
     return fail(h, e);

@@ -562,47 +562,72 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // G^ rows of every block from the solved panel, converted to the storage type.
+// Four consecutive panel values of one row (16-byte aligned: NR and the
+// column offset are multiples of 4).
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T v[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 c = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = c.x, v[3] = c.y;
+  }
+}
+
+template <typename TG, typename T>
+__device__ __forceinline__ TG to_storage(T v) {
+  if constexpr (sizeof(TG) == 8)
+    return (TG)v;
+  else
+    return (TG)(float)v;
+}
+
+// Four consecutive G^ entries of one row (aligned to 4 elements: G^ rows
+// start at multiples of 8 elements and the column offset is a multiple of 4).
+template <typename TG>
+__device__ __forceinline__ void store4(TG* p, const TG v[4]) {
+  if constexpr (sizeof(TG) == 2) {
+    uint16_t u[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) u[t] = *reinterpret_cast<const uint16_t*>(&v[t]);
+    *reinterpret_cast<uint2*>(p) = make_uint2(u[0] | ((uint32_t)u[1] << 16), u[2] | ((uint32_t)u[3] << 16));
+  } else if constexpr (sizeof(TG) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+// G(c, c) of Fig. 2 step 5: row q of G^ (interface row c[q] of block b)
+// takes panel columns j0 .. j0 + NR of the spike rows of c[q].  G^ keeps its
+// columns in panel order; one warp per row, four columns per lane.
 template <typename T, typename TG>
 __global__ void k_ghat_extract(const int32_t* __restrict__ qblock, const int32_t* __restrict__ c_rownew,
                                const int64_t* __restrict__ gq0, const int64_t* __restrict__ gcol_ptr,
                                const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
-                               const int32_t* __restrict__ gperm, int64_t m, int64_t j0, int32_t NR,
-                               const T* __restrict__ X, TG* __restrict__ ghat) {
-  const int64_t total = m * NR;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = t / NR;
-    const int32_t jj = (int32_t)(t % NR);
-    const int32_t b = qblock[q];
-    const int64_t ncol = gcol_ptr[b + 1] - gcol_ptr[b];
-    const int64_t j = j0 + jj;
-    if (j >= ncol) continue;
-    const T v = X[(int64_t)c_rownew[q] * NR + jj];
-    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + gperm[gcol_ptr[b] + j]] = (TG)(float)v;
-  }
-}
-
-template <>
-__global__ void k_ghat_extract<double, double>(const int32_t* __restrict__ qblock,
-                                               const int32_t* __restrict__ c_rownew,
-                                               const int64_t* __restrict__ gq0,
-                                               const int64_t* __restrict__ gcol_ptr,
-                                               const int64_t* __restrict__ ghat_off,
-                                               const int64_t* __restrict__ gld,
-                                               const int32_t* __restrict__ gperm, int64_t m,
-                                               int64_t j0, int32_t NR, const double* __restrict__ X,
-                                               double* __restrict__ ghat) {
-  const int64_t total = m * NR;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = t / NR;
-    const int32_t jj = (int32_t)(t % NR);
-    const int32_t b = qblock[q];
-    const int64_t ncol = gcol_ptr[b + 1] - gcol_ptr[b];
-    const int64_t j = j0 + jj;
-    if (j >= ncol) continue;
-    ghat[ghat_off[b] + (q - gq0[b]) * gld[b] + gperm[gcol_ptr[b] + j]] =
-        X[(int64_t)c_rownew[q] * NR + jj];
+                               int64_t m, int64_t j0, int32_t NR, const T* __restrict__ X,
+                               TG* __restrict__ ghat) {
+  const int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  if (q >= m) return;
+  const int lane = threadIdx.x & 31;
+  const int32_t b = qblock[q];
+  const int64_t ncols = min((int64_t)NR, gcol_ptr[b + 1] - gcol_ptr[b] - j0);
+  const T* __restrict__ src = X + (int64_t)c_rownew[q] * NR;
+  TG* __restrict__ dst = ghat + ghat_off[b] + (q - gq0[b]) * gld[b] + j0;
+  for (int64_t jj = lane * 4; jj < ncols; jj += 128) {
+    T v[4];
+    load4(src + jj, v);
+    TG g[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) g[t] = to_storage<TG>(v[t]);
+    if (jj + 4 <= ncols) {
+      store4(dst + jj, g);
+    } else {
+      for (int t = 0; jj + t < ncols; ++t) dst[jj + t] = g[t];
+    }
   }
 }
 
@@ -702,11 +727,11 @@ void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t ma
 template <typename T, typename TG>
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
-                         const int32_t* gperm, int64_t m, int64_t j0, int32_t NR, const T* X,
-                         TG* ghat, cudaStream_t s) {
+                         int64_t m, int64_t j0, int32_t NR, const T* X, TG* ghat, cudaStream_t s) {
   if (m <= 0) return;
-  k_ghat_extract<T, TG><<<grid_for(m * NR, kThreads), kThreads, 0, s>>>(
-      qblock, c_rownew, gq0, gcol_ptr, ghat_off, gld, gperm, m, j0, NR, X, ghat);
+  const int rows = kThreads / 32;
+  k_ghat_extract<T, TG><<<(unsigned)((m + rows - 1) / rows), kThreads, 0, s>>>(
+      qblock, c_rownew, gq0, gcol_ptr, ghat_off, gld, m, j0, NR, X, ghat);
 }
 
 #define DDPS_INST_T(T)                                                                          \
@@ -735,8 +760,8 @@ DDPS_INST_T(float)
 #define DDPS_INST_TG(T, TG)                                                                     \
   template void launch_ghat_extract<T, TG>(const int32_t*, const int32_t*, const int64_t*,     \
                                            const int64_t*, const int64_t*, const int64_t*,      \
-                                           const int32_t*, int64_t, int64_t, int32_t, const T*, \
-                                           TG*, cudaStream_t);
+                                           int64_t, int64_t, int32_t, const T*, TG*,           \
+                                           cudaStream_t);
 
 DDPS_INST_TG(double, double)
 DDPS_INST_TG(double, float)

@@ -114,12 +114,13 @@ template <typename T>
 void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                        int32_t ntiles, const T* arena, const int64_t* block_ncols, int64_t j0,
                        int32_t NR, T* X, T* Tb, cudaStream_t s);
+// G^ stores its columns in panel order (the matvec's column list is permuted
+// to match), so row q of G^ is a straight copy of the panel row of c[q].
 template <typename T, typename TG>
-// Panel column j of block b holds coupling column gperm[gcol_ptr[b] + j].
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
-                         const int32_t* gperm, int64_t m, int64_t j0, int32_t NR, const T* X,
-                         TG* ghat, cudaStream_t s);
+                         int64_t m, int64_t j0, int32_t NR, const T* X, TG* ghat,
+                         cudaStream_t s);
 
 // ---- solve.cu ---------------------------------------------------------------
 template <typename T>
