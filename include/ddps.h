@@ -89,6 +89,11 @@ typedef struct {
                                  4096 polls) on an mbarrier that nothing arrives at, so that the
                                  wait runs out and ddps_factor returns DDPS_ERR_TIMEOUT; tests the
                                  failure path.  0 in normal use. */
+  int32_t fused_rows;     /* tensor-core spikes: a front with at most this many output rows of a
+                             sweep (backward: its k pivots, forward: its order m) runs both
+                             products of the sweep as one GEMM with a precomputed block
+                             (0 = the largest supported, 512; -1 = never, every front takes the
+                             two tile products) */
 } ddps_options;
 
 typedef struct {

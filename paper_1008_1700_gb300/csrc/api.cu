@@ -113,9 +113,22 @@ struct ddps_handle {
   int32_t *inv_tile_front = nullptr, *inv_tile_cb = nullptr;
   int64_t* inv_off = nullptr;  // per front, offset of its 2 k^2 inverse entries in inv
   void* inv = nullptr;
-  // spike GEMM tile lists per depth: tiles over the k pivot rows and over the r update rows
+  // spike GEMM tile lists per depth: backward tiles over the k pivot rows (tk),
+  // forward tiles over the pivot rows (fk) and over the r update rows (tr).
+  // With tensor-core spikes they hold only the fronts too large for the fused
+  // front products; without, every front.
   int32_t *tk_front = nullptr, *tk_m0 = nullptr, *tr_front = nullptr, *tr_m0 = nullptr;
-  std::vector<int32_t> tk_ptr, tr_ptr;
+  int32_t *fk_front = nullptr, *fk_m0 = nullptr;
+  std::vector<int32_t> tk_ptr, tr_ptr, fk_ptr;
+  // fused front products (tensor-core spikes): packed W per front and direction
+  // (byte offsets, -1 where the front takes the tile ops), the fronts to pack,
+  // and the backward launch lists per (depth, class): [bz_ptr[4L + cls], bz_ptr[4L + cls + 1])
+  unsigned char* wpk = nullptr;
+  int64_t *woff_b = nullptr, *woff_f = nullptr;
+  int32_t *wpk_b = nullptr, *wpk_f = nullptr;
+  int32_t wpk_nb = 0, wpk_nf = 0, wpk_b_kb = 0, wpk_b_k = 0, wpk_f_kb = 0, wpk_f_k = 0;
+  int32_t* bz = nullptr;
+  std::vector<int64_t> bz_ptr;
   // tensor-core spikes: A operands packed as bf16 blocks, byte offsets per op and tile
   unsigned char* atc = nullptr;
   int64_t* tc_aoff[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -130,6 +143,9 @@ struct ddps_handle {
   int32_t *fw_g = nullptr, *fw_kf = nullptr, *fw_km = nullptr, *fw_rf = nullptr, *fw_rm = nullptr;
   int64_t *fw_ka = nullptr, *fw_ra = nullptr;  // packed-A offsets (tensor-core path)
   std::vector<int64_t> fw_g_ptr, fw_k_ptr, fw_r_ptr;
+  // fused forward fronts per (chunk, depth, class): [fz_ptr[4q + cls], fz_ptr[4q + cls + 1])
+  int32_t* fz = nullptr;
+  std::vector<int64_t> fz_ptr;
   int32_t tc_max_kt[4] = {0, 0, 0, 0};
   int tc_passes = 0;
   // segments
@@ -282,6 +298,8 @@ void check_launch() {
 template <typename T>
 void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, const int64_t* ta,
               int32_t nt, const T* arena, int64_t j0, T* X, T* Tb, cudaStream_t s) {
+  if (nt <= 0) return;
+  h->launches++;
   if constexpr (std::is_same<T, float>::value) {
     if (h->tc_passes) {
       launch_spike_gemm_tc(op, h->tc_passes, h->F, tf, tm, ta, h->atc, nt, h->block_ncols, j0,
@@ -290,6 +308,24 @@ void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, cons
     }
   }
   launch_spike_gemm<T>(op, h->F, tf, tm, nt, arena, h->block_ncols, j0, h->NR, X, Tb, s);
+}
+
+// The fused front products of one depth (tensor-core spikes): one launch per
+// tensor-memory class, lists [ptr[cls], ptr[cls + 1]) of `list`.
+template <typename T>
+void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* ptr, int64_t j0,
+                  T* X, T* Tb, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (!h->tc_passes) return;
+    for (int cls = 0; cls < 4; ++cls) {
+      const int32_t n = (int32_t)(ptr[cls + 1] - ptr[cls]);
+      if (n <= 0) continue;
+      launch_front_gemm_tc(bwd ? 1 : 0, cls, h->tc_passes, h->F, list + ptr[cls], n,
+                           bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X, Tb,
+                           h->derr, h->opt.debug_wait_timeout, s);
+      h->launches++;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -347,14 +383,26 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
   h->launches++;
   const int64_t m = (int64_t)A.c.size();
   if constexpr (std::is_same<T, float>::value) {
-    if (h->tc_passes && m > 0) {  // pack the four A operands of every front for the tensor cores
+    if (h->tc_passes && m > 0) {  // pack the A operands of the tile ops and W of the fused fronts
       Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
       for (int op = 0; op < 4; ++op) {
-        const bool r_tiles = op == OP_FWD_L21;
-        launch_tc_pack_a(op, h->tc_passes, h->F, r_tiles ? h->tr_front : h->tk_front,
-                         r_tiles ? h->tr_m0 : h->tk_m0, h->tc_aoff[op],
-                         r_tiles ? h->tr_ptr.back() : h->tk_ptr.back(), h->tc_max_kt[op], arena,
-                         h->atc, s);
+        const int32_t* tf = op == OP_FWD_L21 ? h->tr_front : op == OP_FWD_LINV ? h->fk_front : h->tk_front;
+        const int32_t* tm = op == OP_FWD_L21 ? h->tr_m0 : op == OP_FWD_LINV ? h->fk_m0 : h->tk_m0;
+        const int32_t nt = op == OP_FWD_L21 ? h->tr_ptr.back() : op == OP_FWD_LINV ? h->fk_ptr.back() : h->tk_ptr.back();
+        if (nt > 0) {
+          launch_tc_pack_a(op, h->tc_passes, h->F, tf, tm, h->tc_aoff[op], nt, h->tc_max_kt[op],
+                           arena, h->atc, s);
+          h->launches++;
+        }
+      }
+      if (h->wpk_nb > 0) {
+        launch_tc_w_pack(1, h->tc_passes, h->F, h->wpk_b, h->wpk_nb, h->wpk_b_kb, h->wpk_b_k,
+                         h->woff_b, arena, h->wpk, s);
+        h->launches++;
+      }
+      if (h->wpk_nf > 0) {
+        launch_tc_w_pack(0, h->tc_passes, h->F, h->wpk_f, h->wpk_nf, h->wpk_f_kb, h->wpk_f_k,
+                         h->woff_f, arena, h->wpk, s);
         h->launches++;
       }
     }
@@ -371,19 +419,21 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       for (int L = A.nlevels - 1; L >= 0; --L) {
         Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
         const int64_t q = c * A.nlevels + L;
-        launch_spike_gather<T>(h->F, h->fw_g + h->fw_g_ptr[q],
-                               (int32_t)(h->fw_g_ptr[q + 1] - h->fw_g_ptr[q]), h->block_ncols, j0,
-                               NR, X, Tb, h->fw_active + c * nf, s);
+        const int32_t ng = (int32_t)(h->fw_g_ptr[q + 1] - h->fw_g_ptr[q]);
+        launch_spike_gather<T>(h->F, h->fw_g + h->fw_g_ptr[q], ng, h->block_ncols, j0, NR, X, Tb,
+                               h->fw_active + c * nf, s);
+        h->launches += ng > 0;
+        fused_fronts<T>(h, false, h->fz, h->fz_ptr.data() + 4 * q, j0, X, Tb, s);
         spike_op<T>(h, OP_FWD_LINV, h->fw_kf + h->fw_k_ptr[q], h->fw_km + h->fw_k_ptr[q],
                     h->fw_ka ? h->fw_ka + h->fw_k_ptr[q] : nullptr, (int32_t)(h->fw_k_ptr[q + 1] - h->fw_k_ptr[q]),
                     arena, j0, X, Tb, s);
         spike_op<T>(h, OP_FWD_L21, h->fw_rf + h->fw_r_ptr[q], h->fw_rm + h->fw_r_ptr[q],
                     h->fw_ra ? h->fw_ra + h->fw_r_ptr[q] : nullptr, (int32_t)(h->fw_r_ptr[q + 1] - h->fw_r_ptr[q]),
                     arena, j0, X, Tb, s);
-        h->launches += 3;
       }
       for (int L = 0; L < A.nlevels; ++L) {
         Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
+        fused_fronts<T>(h, true, h->bz, h->bz_ptr.data() + 4 * L, j0, X, Tb, s);
         const int32_t first = h->tk_ptr[L], nt = h->tk_ptr[L + 1] - h->tk_ptr[L];
         spike_op<T>(h, OP_BWD_U12, h->tk_front + first, h->tk_m0 + first,
                     h->tc_aoff[OP_BWD_U12] ? h->tc_aoff[OP_BWD_U12] + first : nullptr, nt, arena,
@@ -391,7 +441,6 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
         spike_op<T>(h, OP_BWD_UINV, h->tk_front + first, h->tk_m0 + first,
                     h->tc_aoff[OP_BWD_UINV] ? h->tc_aoff[OP_BWD_UINV] + first : nullptr, nt, arena,
                     j0, X, Tb, s);
-        h->launches += 2;
       }
       Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
       launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, h->gld,
@@ -809,7 +858,8 @@ ddps_status fail(ddps_handle* h, const Fail& e) {
 void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
                           const std::vector<int32_t>& km, const std::vector<int32_t>& rf,
                           const std::vector<int32_t>& rm,
-                          const std::vector<std::vector<int64_t>>& tc_off) {
+                          const std::vector<std::vector<int64_t>>& tc_off,
+                          const std::vector<uint8_t>& fused) {
   const Analysis& A = h->A;
   const int64_t nf = (int64_t)A.f_k.size();
   const int64_t n = A.n;
@@ -867,6 +917,8 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
   h->fw_g_ptr.assign(1, 0);
   h->fw_k_ptr.assign(1, 0);
   h->fw_r_ptr.assign(1, 0);
+  h->fz_ptr.assign(1, 0);
+  std::vector<int32_t> fz;
   const bool tc = !tc_off.empty();
   for (int64_t c = 0; c < nchunks; ++c) {
     uint8_t* act = active.data() + c * nf;
@@ -879,7 +931,7 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
     for (int L = 0; L < A.nlevels; ++L) {
       for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q)
         if (act[A.level_fronts[q]]) g.push_back(A.level_fronts[q]);
-      for (int32_t t = h->tk_ptr[L]; t < h->tk_ptr[L + 1]; ++t)
+      for (int32_t t = h->fk_ptr[L]; t < h->fk_ptr[L + 1]; ++t)
         if (act[kf[t]]) {
           kfo.push_back(kf[t]);
           kmo.push_back(km[t]);
@@ -894,6 +946,13 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
       h->fw_g_ptr.push_back((int64_t)g.size());
       h->fw_k_ptr.push_back((int64_t)kfo.size());
       h->fw_r_ptr.push_back((int64_t)rfo.size());
+      for (int cls = 0; cls < 4; ++cls) {
+        for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+          const int32_t f = A.level_fronts[q];
+          if (act[f] && fused[f] && tc_fused_class(A.f_m[f]) == cls) fz.push_back(f);
+        }
+        h->fz_ptr.push_back((int64_t)fz.size());
+      }
     }
   }
   h->fw_active = dupload(h, active);
@@ -904,6 +963,7 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
   h->fw_rm = dupload(h, rmo);
   h->fw_ka = tc ? dupload(h, kao) : nullptr;
   h->fw_ra = tc ? dupload(h, rao) : nullptr;
+  h->fz = dupload(h, fz);
 }
 
 void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) {
@@ -1079,38 +1139,71 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   }
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();
-    std::vector<int32_t> kf, km, rf, rm;
+    const int sp = h->opt.spike_prec;
+    const bool tcp = (sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0;
+    const int passes = sp == DDPS_BF16X3 ? 3 : 1;
+    const int64_t nfr = (int64_t)A.f_k.size();
+    // fronts whose output rows fit one CTA take the fused products
+    std::vector<uint8_t> fzb(nfr, 0), fzf(nfr, 0);
+    const int fmax = h->opt.fused_rows < 0    ? 0
+                     : h->opt.fused_rows == 0 ? tc_fused_max_rows()
+                                              : std::min(h->opt.fused_rows, tc_fused_max_rows());
+    if (tcp)
+      for (int64_t f = 0; f < nfr; ++f) {
+        fzb[f] = A.f_k[f] > 0 && A.f_k[f] <= fmax;
+        fzf[f] = A.f_k[f] > 0 && A.f_m[f] <= fmax;
+      }
+    std::vector<int32_t> bkf, bkm, fkf, fkm, rf, rm, bz;
     h->tk_ptr.assign(1, 0);
+    h->fk_ptr.assign(1, 0);
     h->tr_ptr.assign(1, 0);
+    h->bz_ptr.assign(1, 0);
     for (int L = 0; L < A.nlevels; ++L) {
       for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
         const int32_t f = A.level_fronts[q];
         const int32_t kk = A.f_k[f], rr = A.f_m[f] - A.f_k[f];
         for (int32_t m0 = 0; m0 < kk; m0 += BM) {
-          kf.push_back(f);
-          km.push_back(m0);
+          if (!fzb[f]) {
+            bkf.push_back(f);
+            bkm.push_back(m0);
+          }
+          if (!fzf[f]) {
+            fkf.push_back(f);
+            fkm.push_back(m0);
+          }
         }
-        for (int32_t m0 = 0; m0 < rr; m0 += BM) {
-          rf.push_back(f);
-          rm.push_back(m0);
-        }
+        if (!fzf[f])
+          for (int32_t m0 = 0; m0 < rr; m0 += BM) {
+            rf.push_back(f);
+            rm.push_back(m0);
+          }
       }
-      h->tk_ptr.push_back((int32_t)kf.size());
+      h->tk_ptr.push_back((int32_t)bkf.size());
+      h->fk_ptr.push_back((int32_t)fkf.size());
       h->tr_ptr.push_back((int32_t)rf.size());
+      for (int cls = 0; cls < 4; ++cls) {
+        for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+          const int32_t f = A.level_fronts[q];
+          if (fzb[f] && tc_fused_class(A.f_k[f]) == cls) bz.push_back(f);
+        }
+        h->bz_ptr.push_back((int64_t)bz.size());
+      }
     }
-    h->tk_front = dupload(h, kf);
-    h->tk_m0 = dupload(h, km);
+    h->tk_front = dupload(h, bkf);
+    h->tk_m0 = dupload(h, bkm);
+    h->fk_front = dupload(h, fkf);
+    h->fk_m0 = dupload(h, fkm);
     h->tr_front = dupload(h, rf);
     h->tr_m0 = dupload(h, rm);
-    const int sp = h->opt.spike_prec;
-    std::vector<std::vector<int64_t>> tc_off_host, tc_off_local(4);
-    if ((sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0) {
-      h->tc_passes = sp == DDPS_BF16X3 ? 3 : 1;
+    h->bz = dupload(h, bz);
+    std::vector<std::vector<int64_t>> tc_off_host(tcp ? 4 : 0);
+    if (tcp) {
+      h->tc_passes = passes;
       const int BK = tc_tile_bk();
       const int64_t bb = tc_a_block_bytes(h->tc_passes);
       int64_t run = 0;
       for (int op = 0; op < 4; ++op) {
-        const std::vector<int32_t>& tf = op == OP_FWD_L21 ? rf : kf;
+        const std::vector<int32_t>& tf = op == OP_FWD_L21 ? rf : op == OP_FWD_LINV ? fkf : bkf;
         std::vector<int64_t> off(tf.size());
         for (size_t t = 0; t < tf.size(); ++t) {
           const int32_t kk = A.f_k[tf[t]], rr = A.f_m[tf[t]] - kk;
@@ -1121,12 +1214,39 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
           h->tc_max_kt[op] = std::max(h->tc_max_kt[op], nk);
         }
         h->tc_aoff[op] = dupload(h, off);
-        tc_off_local[op] = off;
+        tc_off_host[op] = off;
       }
       h->atc = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(run, 16));
-      tc_off_host.swap(tc_off_local);
+      // packed W of the fused fronts
+      std::vector<int64_t> wob(nfr, -1), wof(nfr, -1);
+      std::vector<int32_t> pb, pf;
+      int64_t wrun = 0;
+      for (int64_t f = 0; f < nfr; ++f) {
+        const int32_t kk = A.f_k[f], mm = A.f_m[f];
+        if (fzb[f]) {
+          wob[f] = wrun;
+          wrun += tc_fused_w_bytes(passes, kk, mm);
+          pb.push_back((int32_t)f);
+          h->wpk_b_kb = std::max(h->wpk_b_kb, (mm + BK - 1) / BK);
+          h->wpk_b_k = std::max(h->wpk_b_k, kk);
+        }
+        if (fzf[f]) {
+          wof[f] = wrun;
+          wrun += tc_fused_w_bytes(passes, mm, kk);
+          pf.push_back((int32_t)f);
+          h->wpk_f_kb = std::max(h->wpk_f_kb, (kk + BK - 1) / BK);
+          h->wpk_f_k = std::max(h->wpk_f_k, kk);
+        }
+      }
+      h->wpk = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(wrun, 16));
+      h->woff_b = dupload(h, wob);
+      h->woff_f = dupload(h, wof);
+      h->wpk_b = dupload(h, pb);
+      h->wpk_f = dupload(h, pf);
+      h->wpk_nb = (int32_t)pb.size();
+      h->wpk_nf = (int32_t)pf.size();
     }
-    build_sparse_forward(h, kf, km, rf, rm, tc_off_host);
+    build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf);
   }
   // segments
   h->nseg = A.nsys;
@@ -1187,6 +1307,10 @@ bool valid_options(const ddps_options& o, std::string& why) {
   }
   if (!(o.tol_out > 0) || !(o.tol_in > 0) || o.maxit_out < 1 || o.maxit_in < 1 || o.pivot_tol < 0) {
     why = "tolerances must be positive and iteration caps at least 1";
+    return false;
+  }
+  if (o.fused_rows < -1) {
+    why = "fused_rows must be -1, 0 or positive";
     return false;
   }
   return true;

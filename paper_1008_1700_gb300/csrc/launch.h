@@ -105,6 +105,21 @@ int64_t tc_a_block_bytes(int passes);
 void launch_tc_pack_a(int op, int passes, DevFronts F, const int32_t* tile_front,
                       const int32_t* tile_m0, const int64_t* tile_aoff, int32_t ntiles,
                       int32_t max_kt, const float* arena, unsigned char* atc, cudaStream_t s);
+// Fused front products (spike_tc.cu): fronts with at most tc_fused_max_rows()
+// output rows (backward: k, forward: m) run both products of a sweep as one
+// GEMM with a precomputed W (launch_tc_w_pack, once per factorisation; woff[f]
+// = byte offset of front f's W, tc_fused_w_bytes bytes, 1024-byte aligned).
+// cls = tc_fused_class(rows) selects the tensor-memory width (64 << cls).
+int tc_fused_max_rows();
+int tc_fused_class(int rows);
+int64_t tc_fused_w_bytes(int passes, int rows, int K);
+void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, int32_t nfr,
+                      int32_t max_kb, int32_t max_k, const int64_t* woff, const float* arena,
+                      unsigned char* wpk, cudaStream_t s);
+void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
+                          int32_t nfr, const int64_t* woff, const unsigned char* wpk,
+                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X, float* Tb,
+                          long long* err, int inject_wait, cudaStream_t s);
 void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_front,
                           const int32_t* tile_m0, const int64_t* tile_aoff,
                           const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,

@@ -20,6 +20,7 @@
 // out records error code 2 in the kernel's error record.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "launch.h"
@@ -121,6 +122,27 @@ __device__ __forceinline__ void store_split(unsigned char* hi_dst, unsigned char
     *reinterpret_cast<uint4*>(lo_dst) =
         make_uint4(lo[0] | ((uint32_t)lo[1] << 16), lo[2] | ((uint32_t)lo[3] << 16),
                    lo[4] | ((uint32_t)lo[5] << 16), lo[6] | ((uint32_t)lo[7] << 16));
+}
+
+// Eight consecutive values -> bf16 high parts (16 bytes) and remainders,
+// two values per conversion instruction; bitwise equal to store_split.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo_elem, float hi_elem) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+  return r;
+}
+__device__ __forceinline__ void store_split_x2(unsigned char* hi_dst, unsigned char* lo_dst,
+                                               const float* v, bool with_lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    h[t] = cvt_bf16x2(v[2 * t], v[2 * t + 1]);
+    const float r0 = v[2 * t] - __uint_as_float(h[t] << 16);
+    const float r1 = v[2 * t + 1] - __uint_as_float(h[t] & 0xffff0000u);
+    l[t] = cvt_bf16x2(r0, r1);
+  }
+  *reinterpret_cast<uint4*>(hi_dst) = make_uint4(h[0], h[1], h[2], h[3]);
+  if (with_lo) *reinterpret_cast<uint4*>(lo_dst) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Dimensions of one op for front f: M rows of C, K, and the origin of A in the front.
@@ -364,6 +386,566 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                  "r"((uint32_t)TC_BN));
 }
 
+// ---------------------------------------------------------------------------
+// Fused front products.  For a front whose output rows fit one CTA, the two
+// products of each sweep are folded into one GEMM over the front's rows:
+//   forward:  [X_piv; dT_upd] = W_f T_piv,        W_f = [L11^-1; -L21 L11^-1]   (m x k)
+//   backward: X_piv = W_b [X_piv; X_upd],         W_b = [U11^-1, -U11^-1 U12]    (k x m)
+// (X_upd: the solution on the front's update rows, gathered through its row
+// list; dT_upd is added to the front's update rows for the parent's gather).
+// The MMA is transposed with respect to the tile ops above: its M = 128 are
+// panel columns and its N = the front's output rows rounded up to 16, so a
+// small front costs N, not 128, rows of work; the accumulator lives in
+// tensor memory as 128 lanes (columns) x N (rows).  W is packed once per
+// factorisation in the same K-major bf16 layout with N rows per 32-column
+// K-block (high part, then the remainder).
+// ---------------------------------------------------------------------------
+enum { DIR_FWD = 0, DIR_BWD = 1 };
+
+__device__ __forceinline__ uint32_t idesc_m128(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_n(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// Output rows and K of a fused front product.
+template <int DIR>
+__device__ __forceinline__ void fused_dims(int32_t k, int32_t m, int& nout, int& K) {
+  nout = DIR == DIR_BWD ? k : m;
+  K = DIR == DIR_BWD ? m : k;
+}
+
+// W of one front, K-block kb (32 columns): entries that are blocks of the
+// factored front are copied, the product blocks are formed here in fp32:
+//   backward, column j >= k:  -sum_{l >= i} U11^-1(i, l) U12(l, j)
+//   forward,  row i >= k:     -sum_{l >= j} L21(i, l) L11^-1(l, j)
+// The right factor's 32 columns are staged in shared memory ([k][33]).
+template <int DIR, int PASSES>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_w_pack(DevFronts F, const int32_t* __restrict__ fronts, const int64_t* __restrict__ woff,
+             const float* __restrict__ arena, unsigned char* __restrict__ wpk) {
+  extern __shared__ float Rs[];
+  const int32_t f = fronts[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  int nout, K;
+  fused_dims<DIR>(k, m, nout, K);
+  const int kb = blockIdx.y;
+  if (kb * TC_BK >= K) return;
+  const int nf = (nout + 15) & ~15;
+  const float* __restrict__ A = arena + F.arena[f];
+  const int j0 = kb * TC_BK;
+  // right factor: backward U12(l, j) (rows l < k of column j >= k), forward L11^-1(l, j)
+  for (int e = threadIdx.x; e < k * TC_BK; e += TC_THREADS) {
+    const int l = e % k, jj = e / k, j = j0 + jj;
+    float v = 0.f;
+    if (j < K) {
+      if (DIR == DIR_BWD)
+        v = j >= k ? A[l + (int64_t)j * m] : 0.f;
+      else
+        v = l > j ? A[l + (int64_t)j * m] : (l == j ? 1.f : 0.f);
+    }
+    Rs[l * (TC_BK + 1) + jj] = v;
+  }
+  __syncthreads();
+  const uint32_t part = (uint32_t)nf * TC_BK * 2;
+  unsigned char* dst = wpk + woff[f] + (int64_t)kb * (PASSES == 3 ? 2 : 1) * part;
+  const int jj = threadIdx.x & 31;
+  const int j = j0 + jj;
+  for (int i = threadIdx.x >> 5; i < nf; i += TC_THREADS / 32) {
+    float w = 0.f;
+    if (i < nout && j < K) {
+      if (DIR == DIR_BWD) {
+        if (j < k) {
+          w = i <= j ? A[i + (int64_t)j * m] : 0.f;
+        } else {
+          float acc = 0.f;
+          for (int l = i; l < k; ++l) acc = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], acc);
+          w = -acc;
+        }
+      } else {
+        if (i < k) {
+          w = i > j ? A[i + (int64_t)j * m] : (i == j ? 1.f : 0.f);
+        } else {
+          float acc = 0.f;
+          for (int l = j0; l < k; ++l) acc = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], acc);
+          w = -acc;
+        }
+      }
+    }
+    uint16_t hi, lo;
+    split_bf16(w, hi, lo);
+    const uint32_t off = chunk_off(i, jj >> 3) + (jj & 7) * 2;
+    *reinterpret_cast<uint16_t*>(dst + off) = hi;
+    if (PASSES == 3) *reinterpret_cast<uint16_t*>(dst + part + off) = lo;
+  }
+}
+
+// Bounded wait that does not give up when another CTA has recorded a
+// timeout: used only to let a CTA's own copies land before it exits.
+__device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// One work item = (front, 128-column panel tile) of a fused front product.
+// The front's fields are kept between items: consecutive items of a CTA are
+// mostly the tiles of one front, so an item usually costs one cached load.
+struct FItem {
+  int32_t f = -1;
+  int32_t k, nout, K, nf, nkt, cv;
+  int64_t ncols, n0, row0, tb0;
+  const int32_t* idx;
+  const unsigned char* w;
+  uint32_t wpart, wblk;
+};
+
+template <int DIR, int PASSES>
+__device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_t nct,
+                                      const int64_t* woff, const unsigned char* wpk,
+                                      const int64_t* block_ncols, int64_t j0, int32_t NR, int it,
+                                      FItem& w) {
+  const int32_t f = fronts[it / nct];
+  if (f != w.f) {
+    w.f = f;
+    w.ncols = min((int64_t)NR, block_ncols[F.block[f]] - j0);
+    w.k = F.k[f];
+    fused_dims<DIR>(w.k, F.m[f], w.nout, w.K);
+    w.nf = (w.nout + 15) & ~15;
+    w.nkt = (w.K + TC_BK - 1) / TC_BK;
+    w.row0 = F.row0[f];
+    w.tb0 = F.idx_off[f];
+    w.idx = F.idx + F.idx_off[f];
+    w.w = wpk + woff[f];
+    w.wpart = (uint32_t)w.nf * TC_BK * 2;
+    w.wblk = (PASSES == 3 ? 2u : 1u) * w.wpart;
+  }
+  w.n0 = (int64_t)(it % nct) * TC_BN;
+  if (w.n0 >= w.ncols) return false;
+  w.cv = (int)min((int64_t)TC_BN, w.ncols - w.n0);
+  return true;
+}
+
+// Persistent, warp-specialised fused front product.  Each CTA (one per SM)
+// takes a contiguous range of work items (front, 128-column tile); a tile is
+// nkt K-stages of 32 panel rows.  A stage lives in one slot of a ring of SR
+// 16 KB slots from the moment its rows are copied in until its MMAs complete:
+//   warps 12-15 (row producers, stage g by warp 12 + g % NPROD): one 1-D bulk
+//     copy per panel row (fp32, up to 512 bytes, gathered through the front's
+//     row list) into the stage's slot.  One warp streams copies at a bounded
+//     rate, so several issue side by side; every slot belongs to one warp;
+//   warp 17 lane 0 (W producer): the stage's W block into a ring of SW slots;
+//   warps 0-3 (converters): read the slot's fp32 rows, then (after a barrier
+//     of the four warps) overwrite the slot with the bf16 (high, remainder)
+//     K-major operand;
+//   warp 16 lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256 output rows)
+//     into one of NACC tensor-memory accumulators; its commits hand the slot
+//     and the W slot back to the producers and, after the tile's last stage,
+//     the accumulator to the epilogue;
+//   warps 4-11 (epilogue, two groups of four): tcgen05.ld of lane quarter
+//     (warp % 4); group q stores the 16-row groups q, q + 2, ...; one 128-byte
+//     row segment per store (forward: the update rows are read one group
+//     ahead and accumulated).
+// Every wait is bounded: a wait that runs out records error code 2 at once
+// (so that the other waits of every CTA give up quickly), the role stops,
+// and before exiting each producer lets its own copies land.
+constexpr int FG_CONV = 128;   // converter threads (warps 0-3)
+constexpr int FG_EPI0 = 4;     // epilogue warps 4-11 (tensor-memory lane quarter = warp % 4)
+constexpr int FG_NEPI = 8;
+constexpr int FG_PROD0 = 12;   // producer warps 12-15
+constexpr int FG_NPROD = 4;
+constexpr int FG_MMA = 16;     // MMA issuer warp
+constexpr int FG_WPROD = 17;   // W producer warp
+constexpr int FG_THREADS = 18 * 32;
+
+template <int DIR, int NT, int PASSES, int SR, int SW, int NACC, int NPROD>
+__global__ void __launch_bounds__(FG_THREADS, 1)
+    k_front_gemm_tc(DevFronts F, const int32_t* __restrict__ fronts, int32_t nitems, int32_t nct,
+                    const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
+                    const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
+                    float* __restrict__ X, float* __restrict__ Tb, long long* __restrict__ err,
+                    int inject_wait) {
+  // every ring slot is always filled by the same producer warp, so that no
+  // producer waits on a slot barrier more than one phase ahead of it
+  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD, "ring ownership");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t raw_full[SR], op_full[SR], slot_empty[SR];
+  __shared__ __align__(8) uint64_t w_full[SW], w_empty[SW], acc_full[NACC], acc_empty[NACC];
+  __shared__ __align__(8) uint64_t never;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int skip_all;
+  constexpr uint32_t kSlot = TC_BK * TC_BN * 4;                       // 32 fp32 rows x 128
+  constexpr uint32_t kWs = (PASSES == 3 ? 2u : 1u) * NT * TC_BK * 2;  // W block
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t w0 = sbase + SR * kSlot;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int it0 = (int)blockIdx.x * per, it1 = min(nitems, it0 + per);
+  const float* __restrict__ src = DIR == DIR_BWD ? X : Tb;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"((uint32_t)(NT * NACC)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < SR; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&op_full[i])),
+                   "r"(FG_CONV));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_empty[i])));
+    }
+    for (int i = 0; i < SW; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_empty[i])));
+    }
+    for (int i = 0; i < NACC; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
+                   "r"(FG_NEPI * 32));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&never)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    skip_all = 0;
+    if (inject_wait) {  // failure-path test: a short bounded wait that must run out
+      if (!mbar_wait(smem_u32(&never), 0, err, 4096u)) {
+        atomicCAS((unsigned long long*)&err[0], 0ull, 2ull);
+        skip_all = 1;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  bool bail = skip_all != 0;
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if (bail) return;
+    if (!mbar_wait(smem_u32(bar), parity, err)) {
+      bail = true;
+      atomicCAS((unsigned long long*)&err[0], 0ull, 2ull);
+    }
+  };
+  uint32_t issued = 0;  // producer: stages issued
+
+  if (warp >= FG_PROD0 && warp < FG_PROD0 + NPROD) {
+    // ---------------- producers ----------------
+    const int p = warp - FG_PROD0;
+    struct Pos {
+      int it, kt;
+      FItem w;
+    };
+    Pos pos{it0, 0, {}};
+    auto next_valid = [&](int from) {
+      int it = from;
+      while (it < it1 && !fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, pos.w)) ++it;
+      pos.it = it;
+      pos.kt = 0;
+    };
+    auto advance = [&]() {
+      if (pos.it >= it1) return;
+      if (++pos.kt >= pos.w.nkt) next_valid(pos.it + 1);
+    };
+    auto row_of = [&](const FItem& w, int kk) -> int64_t {
+      const int gk = kk * TC_BK + lane;
+      if (gk >= w.K) return 0;
+      return DIR == DIR_BWD ? (gk < w.k ? w.row0 + gk : (int64_t)w.idx[gk]) : w.tb0 + gk;
+    };
+    next_valid(it0);
+    uint32_t g = 0;
+    for (int i = 0; i < p; ++i, ++g) advance();
+    int64_t row_next = pos.it < it1 ? row_of(pos.w, pos.kt) : 0;
+    while (pos.it < it1 && !bail) {
+      const int64_t row = row_next;
+      const Pos cur = pos;
+      const uint32_t gc = g;
+      for (int i = 0; i < NPROD; ++i, ++g) advance();  // this warp's next stage
+      if (pos.it < it1) row_next = row_of(pos.w, pos.kt);
+      // panel rows of stage gc into its slot (free once the MMAs of stage gc - SR completed)
+      const uint32_t sl = gc % SR;
+      if (gc >= SR) wait(&slot_empty[sl], ((gc / SR) - 1) & 1);
+      bail = __any_sync(0xffffffffu, bail);  // keep the warp together for __syncwarp
+      if (bail) break;
+      const int nr = min(TC_BK, cur.w.K - cur.kt * TC_BK);
+      const uint32_t rb = (uint32_t)((cur.w.cv + 3) & ~3) * 4;
+      if (lane == 0) mbar_expect_tx(smem_u32(&raw_full[sl]), (uint32_t)nr * rb);
+      __syncwarp();
+      if (lane < nr)
+        bulk_g2s(sbase + sl * kSlot + (uint32_t)lane * (TC_BN * 4), src + row * NR + cur.w.n0, rb,
+                 smem_u32(&raw_full[sl]));
+      issued = gc + 1;
+    }
+  } else if (warp == FG_WPROD) {
+    // ---------------- W producer ----------------
+    // W blocks come from their own warp, so that they do not queue behind the
+    // row copies; a W slot is refilled once the MMAs of its stage completed.
+    if (lane == 0) {
+      uint32_t g = 0;
+      FItem w;
+      for (int it = it0; it < it1 && !bail; ++it) {
+        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+        for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+          const uint32_t ws = g % SW;
+          if (g >= SW) wait(&w_empty[ws], ((g / SW) - 1) & 1);
+          if (bail) break;
+          mbar_expect_tx(smem_u32(&w_full[ws]), w.wblk);
+          bulk_g2s(w0 + ws * kWs, w.w + (int64_t)kt * w.wblk, w.wblk, smem_u32(&w_full[ws]));
+          issued = g + 1;
+        }
+      }
+    }
+  } else if (warp < FG_CONV / 32) {
+    // ---------------- converters ----------------
+    const int ct = tid;
+    uint32_t g = 0;
+    FItem w;
+    for (int it = it0; it < it1 && !bail; ++it) {
+      if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+        const uint32_t sl = g % SR;
+        wait(&raw_full[sl], (g / SR) & 1);
+        unsigned char* slot = smem + sl * kSlot;
+        const float* raw = reinterpret_cast<const float*>(slot);
+        const int nr = min(TC_BK, w.K - kt * TC_BK);
+        constexpr int kQ = (TC_BN * TC_BK / 8) / FG_CONV;
+        float v[kQ][8];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const int e = ct + q * FG_CONV;
+          const int col = e % TC_BN, kc = e / TC_BN;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int r = kc * 8 + u;
+            v[q][u] = (!bail && r < nr && col < w.cv) ? raw[r * TC_BN + col] : 0.f;
+          }
+        }
+        // the four warps have read the slot before any overwrites it; the
+        // barrier also makes a timeout in any of them a decision of all
+        uint32_t any_bail;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+            "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(any_bail)
+            : "r"((uint32_t)bail), "r"(FG_CONV)
+            : "memory");
+        bail = any_bail != 0;
+        if (bail) break;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const int e = ct + q * FG_CONV;
+          const uint32_t off = chunk_off(e % TC_BN, e / TC_BN);
+          store_split_x2(slot + off, slot + TC_TILE_BYTES + off, v[q], PASSES == 3);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&op_full[sl]));
+      }
+    }
+  } else if (warp == FG_MMA) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      // descriptors differ only in their start-address field (address / 16,
+      // 14 bits; every address here is below 256 KB): build the two bases
+      // once and add offsets, so that issuing a stage costs few instructions
+      const uint64_t dS = make_desc(sbase, 128, kSBO), dW = make_desc(w0, 128, kSBO);
+      uint32_t g = 0, tc = 0;
+      FItem w;
+      for (int it = it0; it < it1 && !bail; ++it) {
+        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+        const uint32_t a = tc % NACC;
+        if (tc >= NACC) wait(&acc_empty[a], ((tc / NACC) - 1) & 1);
+        const uint32_t acc = tmem + a * NT;
+        const uint32_t id0 = idesc_m128(min(256, w.nf));
+        const uint32_t id1 = w.nf > 256 ? idesc_m128(w.nf - 256) : 0u;
+        const uint64_t lo_w = w.wpart >> 4;
+        for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+          const uint32_t sl = g % SR, ws = g % SW;
+          wait(&op_full[sl], (g / SR) & 1);
+          wait(&w_full[ws], (g / SW) & 1);
+          if (bail) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t aHi = dS + ((sl * kSlot) >> 4), aLo = aHi + (TC_TILE_BYTES >> 4);
+          const uint64_t bHi = dW + ((ws * kWs) >> 4), bLo = bHi + lo_w;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint64_t ko = kk * (256 >> 4);
+            const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+            mma_bf16_n(acc, aHi + ko, bHi + ko, id0, acc0);
+            if (PASSES == 3) {
+              mma_bf16_n(acc, aHi + ko, bLo + ko, id0, 1u);
+              mma_bf16_n(acc, aLo + ko, bHi + ko, id0, 1u);
+            }
+            if (NT > 256 && id1) {  // output rows 256.. : B rows 256.. and accumulator columns 256..
+              const uint64_t wo = (256 / 8) * kSBO >> 4;
+              mma_bf16_n(acc + 256, aHi + ko, bHi + wo + ko, id1, acc0);
+              if (PASSES == 3) {
+                mma_bf16_n(acc + 256, aHi + ko, bLo + wo + ko, id1, 1u);
+                mma_bf16_n(acc + 256, aLo + ko, bHi + wo + ko, id1, 1u);
+              }
+            }
+          }
+          mma_commit(smem_u32(&slot_empty[sl]));
+          mma_commit(smem_u32(&w_empty[ws]));
+          if (kt == w.nkt - 1) mma_commit(smem_u32(&acc_full[a]));
+        }
+        ++tc;
+      }
+    }
+  } else if (warp >= FG_EPI0 && warp < FG_EPI0 + FG_NEPI) {
+    // ---------------- epilogue ----------------
+    const int quarter = warp & 3, grp = (warp - FG_EPI0) >> 2;
+    uint32_t tc = 0;
+    FItem w;
+    for (int it = it0; it < it1 && !bail; ++it) {
+      if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      const uint32_t a = tc % NACC;
+      const int64_t gj = w.n0 + quarter * 32 + lane;
+      const bool col_ok = quarter * 32 + lane < w.cv;
+      // forward: old values of the update rows of this warp's first row group, read early
+      float old[16];
+      auto load_old = [&](int c16) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int i = c16 + u;
+          old[u] = (DIR == DIR_FWD && col_ok && i >= w.k && i < w.nout)
+                       ? Tb[(w.tb0 + i) * NR + gj]
+                       : 0.f;
+        }
+      };
+      if (DIR == DIR_FWD) load_old(grp * 16);
+      wait(&acc_full[a], (tc / NACC) & 1);
+      bail = __any_sync(0xffffffffu, bail);  // tcgen05.ld is warp-collective
+      if (bail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + a * NT + ((uint32_t)(quarter * 32) << 16);
+      for (int c16 = grp * 16; c16 < w.nout; c16 += 32) {
+        uint32_t rv[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(rv[0]), "=r"(rv[1]), "=r"(rv[2]), "=r"(rv[3]), "=r"(rv[4]), "=r"(rv[5]),
+              "=r"(rv[6]), "=r"(rv[7]), "=r"(rv[8]), "=r"(rv[9]), "=r"(rv[10]), "=r"(rv[11]),
+              "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
+            : "r"(acc + (uint32_t)c16));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (DIR == DIR_FWD) {
+          float cur[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) cur[u] = old[u];
+          if (c16 + 32 < w.nout) load_old(c16 + 32);  // next group's old values
+          if (col_ok) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int i = c16 + u;
+              const float val = __uint_as_float(rv[u]);
+              if (i < w.k)
+                X[(w.row0 + i) * NR + gj] = val;
+              else if (i < w.nout)
+                Tb[(w.tb0 + i) * NR + gj] = cur[u] + val;
+            }
+          }
+        } else if (col_ok) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int i = c16 + u;
+            if (i < w.nout) X[(w.row0 + i) * NR + gj] = __uint_as_float(rv[u]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&acc_empty[a]));
+      ++tc;
+    }
+  }
+  if (warp >= FG_PROD0 && warp < FG_PROD0 + NPROD && lane == 0 && bail) {
+    // let this warp's own copies land before the CTA exits
+    for (uint32_t g = issued > SR ? issued - SR : 0; g < issued; ++g)
+      if ((int)(g % NPROD) == warp - FG_PROD0) mbar_drain(smem_u32(&raw_full[g % SR]), (g / SR) & 1);
+  }
+  if (warp == FG_WPROD && lane == 0 && bail)
+    for (uint32_t g = issued > SW ? issued - SW : 0; g < issued; ++g)
+      mbar_drain(smem_u32(&w_full[g % SW]), (g / SW) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)(NT * NACC)));
+}
+
+// Ring depths per tensor-memory width (shared memory: SR x 16 KB stage slots,
+// SW x W blocks; one CTA per SM).
+template <int NT>
+struct FrontCfg {
+  static constexpr int SR = NT <= 128 ? 8 : 4;
+  static constexpr int SW = NT <= 128 ? 6 : NT <= 256 ? 4 : 2;
+  static constexpr int NACC = NT <= 256 ? 2 : 1;
+  static constexpr int NPROD = 4;  // row producer warps (divides SR)
+};
+
+template <int DIR, int NT, int PASSES>
+void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
+                  const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
+                  float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
+  using C = FrontCfg<NT>;
+  auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NPROD>;
+  constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
+                        (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2;
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  }
+  const int32_t nct = (NR + TC_BN - 1) / TC_BN;
+  const int32_t nitems = nfr * nct;
+  const int32_t grid = std::min(nitems, nsm);
+  kern<<<grid, FG_THREADS, sm, s>>>(F, fronts, nitems, nct, woff, wpk, block_ncols, j0, NR, X, Tb,
+                                    err, inject);
+}
+
+template <int DIR, int PASSES>
+void dispatch_front(int cls, DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
+                    const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
+                    float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
+  switch (cls) {
+    case 0:
+      launch_front<DIR, 64, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                    inject, s);
+      break;
+    case 1:
+      launch_front<DIR, 128, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                     inject, s);
+      break;
+    case 2:
+      launch_front<DIR, 256, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                     inject, s);
+      break;
+    default:
+      launch_front<DIR, 512, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                     inject, s);
+  }
+}
+
 template <int OP, int PASSES>
 void launch_one(DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                 const int64_t* tile_aoff, const unsigned char* atc, int32_t ntiles,
@@ -422,6 +1004,64 @@ void dispatch_pack(int op, DevFronts F, const int32_t* tf, const int32_t* tm, co
 }
 
 }  // namespace
+
+int tc_fused_max_rows() { return 512; }
+int tc_fused_class(int rows) {
+  const int n = (rows + 15) & ~15;
+  return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : 3;
+}
+int64_t tc_fused_w_bytes(int passes, int rows, int K) {
+  const int64_t nf = (rows + 15) & ~15;
+  const int64_t nkb = (K + TC_BK - 1) / TC_BK;
+  return (passes == 3 ? 2 : 1) * nf * TC_BK * 2 * nkb;
+}
+
+void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, int32_t nfr,
+                      int32_t max_kb, int32_t max_k, const int64_t* woff, const float* arena,
+                      unsigned char* wpk, cudaStream_t s) {
+  if (nfr <= 0 || max_kb <= 0) return;
+  const size_t sm = (size_t)std::max(max_k, 1) * (TC_BK + 1) * sizeof(float);
+  dim3 grid(nfr, max_kb);
+#define DDPS_WPACK(D, P)                                                                        \
+  cudaFuncSetAttribute(k_w_pack<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+  k_w_pack<D, P><<<grid, TC_THREADS, sm, s>>>(F, fronts, woff, arena, wpk);
+  if (bwd) {
+    if (passes == 3) {
+      DDPS_WPACK(DIR_BWD, 3)
+    } else {
+      DDPS_WPACK(DIR_BWD, 1)
+    }
+  } else {
+    if (passes == 3) {
+      DDPS_WPACK(DIR_FWD, 3)
+    } else {
+      DDPS_WPACK(DIR_FWD, 1)
+    }
+  }
+#undef DDPS_WPACK
+}
+
+void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
+                          int32_t nfr, const int64_t* woff, const unsigned char* wpk,
+                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X, float* Tb,
+                          long long* err, int inject_wait, cudaStream_t s) {
+  if (nfr <= 0) return;
+  if (bwd) {
+    if (passes == 3)
+      dispatch_front<DIR_BWD, 3>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                 inject_wait, s);
+    else
+      dispatch_front<DIR_BWD, 1>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                 inject_wait, s);
+  } else {
+    if (passes == 3)
+      dispatch_front<DIR_FWD, 3>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                 inject_wait, s);
+    else
+      dispatch_front<DIR_FWD, 1>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
+                                 inject_wait, s);
+  }
+}
 
 int tc_tile_bk() { return TC_BK; }
 int64_t tc_a_block_bytes(int passes) { return (passes == 3 ? 2 : 1) * (int64_t)TC_TILE_BYTES; }

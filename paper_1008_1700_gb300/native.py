@@ -31,7 +31,7 @@ class ddps_options(C.Structure):
                 ("tol_in", C.c_double), ("maxit_in", C.c_int32),
                 ("pivot_tol", C.c_double), ("leaf_size", C.c_int32),
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
-                ("debug_wait_timeout", C.c_int32)]
+                ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):

@@ -26,6 +26,11 @@ TC3 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_F
            inner_prec=N.DDPS_FP32)
 TC1 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16, ghat_prec=N.DDPS_BF16,
            inner_prec=N.DDPS_FP32)
+# the same products without the fused front GEMMs (every front takes the two
+# tile products of each sweep), and with both kinds of fronts in one depth
+TC3_TILES = dict(TC3, fused_rows=-1)
+TC3_MIXED = dict(TC3, fused_rows=24)
+FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mixed": TC3_MIXED}
 
 
 def test_worked_example_on_gpu():
@@ -100,12 +105,14 @@ def test_precond_apply_direct_mode(case):
     assert relerr(z, zo) <= 1e-9
 
 
-@pytest.mark.parametrize("form,bound", [("mixed", 2e-6), ("tc3", 1e-4), ("tc1", 3e-2)])
+@pytest.mark.parametrize("form,bound", [("mixed", 2e-6), ("tc3", 1e-4), ("tc1", 3e-2),
+                                        ("tc3_tiles", 1e-4), ("tc3_mixed", 1e-4)])
 def test_ghat_precision_forms(case, form, bound):
     """G^ formed with FP32 factors: SIMT FP32 products, bf16x3 and bf16 tensor-core
-    products; each within its arithmetic's accuracy of the FP64 oracle."""
+    products (fused front GEMMs, tile products, or both); each within its
+    arithmetic's accuracy of the FP64 oracle."""
     name, P, drop, o = case
-    S = make_solver(P, drop, **{"mixed": MIXED, "tc3": TC3, "tc1": TC1}[form])
+    S = make_solver(P, drop, **FORMS[form])
     for b, ob in enumerate(o.blk):
         q0, q1, cols = S.ghat_layout(b)
         if (q1 - q0) * len(cols) == 0:
@@ -231,14 +238,17 @@ def test_batch_every_system_meets_tolerance():
         assert relerr(x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]], xo) <= 1e-7
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
-    """Failure path of the tensor-core spike kernel: with debug_wait_timeout the
-    kernel waits on an mbarrier that nothing arrives at; the bounded wait runs
-    out, the kernel frees its tensor memory and returns, ddps_factor reports
-    DDPS_ERR_TIMEOUT, and the context stays usable for a normal solve."""
+@pytest.mark.parametrize("fused_rows", [0, -1])
+def test_bounded_wait_reports_timeout_and_context_survives(fused_rows):
+    """Failure path of the tensor-core spike kernels (fused front GEMM, tile
+    products): with debug_wait_timeout the kernel waits on an mbarrier that
+    nothing arrives at; the bounded wait runs out, the kernel frees its tensor
+    memory and returns, ddps_factor reports DDPS_ERR_TIMEOUT, and the context
+    stays usable for a normal solve."""
     P = W.small_convdiff_2d(24, 3)
     from paper_1008_1700_gb300 import Solver
-    S = Solver(P.rowptr, P.colind, P.block_ptr, debug_wait_timeout=1, **TC3)
+    S = Solver(P.rowptr, P.colind, P.block_ptr, debug_wait_timeout=1, fused_rows=fused_rows,
+               **TC3)
     with pytest.raises(N.DDPSError, match="TIMEOUT"):
         S.factor(dev(P.values))
     S.close()
