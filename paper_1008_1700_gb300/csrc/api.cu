@@ -263,7 +263,9 @@ T* dupload(ddps_handle* h, const std::vector<T>& v) {
 
 // Chunk table of a segmented vector.
 SegView make_segview(ddps_handle* h, const std::vector<int64_t>& seg_ptr) {
-  const int64_t CH = 8192;
+  // chunk length: about eight chunks per SM over the whole vector, between 256 and 8192
+  const int64_t total = seg_ptr.empty() ? 0 : seg_ptr.back() - seg_ptr.front();
+  const int64_t CH = std::min<int64_t>(8192, std::max<int64_t>(256, (total / (8 * 152) + 255) / 256 * 256));
   std::vector<int64_t> cb, ce;
   std::vector<int32_t> cs, scp;
   const int nseg = (int)seg_ptr.size() - 1;
@@ -274,6 +276,11 @@ SegView make_segview(ddps_handle* h, const std::vector<int64_t>& seg_ptr) {
       ce.push_back(std::min(b + CH, seg_ptr[s + 1]));
       cs.push_back(s);
     }
+    if (seg_ptr[s + 1] == seg_ptr[s]) {  // an empty segment still gets its (empty) chunk
+      cb.push_back(seg_ptr[s]);
+      ce.push_back(seg_ptr[s]);
+      cs.push_back(s);
+    }
     scp.push_back((int32_t)cb.size());
   }
   SegView S{};
@@ -281,6 +288,7 @@ SegView make_segview(ddps_handle* h, const std::vector<int64_t>& seg_ptr) {
   S.chunk_end = dupload(h, ce);
   S.chunk_seg = dupload(h, cs);
   S.seg_chunk_ptr = dupload(h, scp);
+  S.done = dupload(h, std::vector<int32_t>(std::max(nseg, 1), 0));
   S.nchunks = (int32_t)cb.size();
   S.nseg = nseg;
   return S;

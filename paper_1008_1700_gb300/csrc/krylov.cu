@@ -2,8 +2,8 @@
 // Fig. 3 step 6.3 inner loop; Sec. 4 names BiCGStab for both).  Vectors are
 // segmented by system: every system of a batch keeps its own scalars
 // (rho, alpha, omega, ...) and its own convergence flag.  Reductions are
-// deterministic: fixed chunks, fixed tree inside a chunk, chunks summed in
-// order by one thread per segment.
+// deterministic: fixed chunks, fixed tree inside a chunk, and the chunks of a
+// segment summed in a fixed pattern by the CTA that finishes last.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -27,63 +27,23 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// One CTA per chunk: up to three reductions in one pass.
-//   op 0: sum x*y   op 1: sum x*x   op 2: max |x|
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_seg_reduce(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2, double* __restrict__ partial) {
-  const int ch = blockIdx.x;
-  const int64_t b = S.chunk_beg[ch], e = S.chunk_end[ch];
-  RedSpec spec[3] = {r0, r1, r2};
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q >= nred) break;
-      const T* x = (const T*)spec[q].x;
-      const T* y = (const T*)spec[q].y;
-      const double xv = (double)x[i];
-      if (spec[q].op == 0)
-        acc[q] += xv * (double)y[i];
-      else if (spec[q].op == 1)
-        acc[q] += xv * xv;
-      else
-        acc[q] = fmax(acc[q], fabs(xv));
-    }
-  }
-  __shared__ double red[3][kThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q >= nred) break;
-    double v = spec[q].op == 2 ? warp_max(acc[q]) : warp_sum(acc[q]);
-    if (lane == 0) red[q][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 3 && (int)threadIdx.x < nred) {
-    const int q = threadIdx.x;
-    double v = red[q][0];
-    for (int w = 1; w < kThreads / 32; ++w) v = spec[q].op == 2 ? fmax(v, red[q][w]) : v + red[q][w];
-    partial[(int64_t)q * S.nchunks + ch] = v;
-  }
-}
-
-__global__ void k_seg_final(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
-                            const double* __restrict__ partial, int post, KScal* sc, double tol,
-                            int it) {
-  const int sgi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sgi >= S.nseg) return;
-  RedSpec spec[3] = {r0, r1, r2};
+// Result of the reductions of segment sgi from its chunks' partial values
+// (lane l adds the chunks l, l + 32, ...; then a fixed shuffle tree), and
+// the BiCGStab scalar step `post` of that segment; run by one warp.
+__device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, const RedSpec* spec,
+                             const double* partial, int post, KScal* sc, double tol, int it) {
+  const int c0 = S.seg_chunk_ptr[sgi], c1 = S.seg_chunk_ptr[sgi + 1];
   for (int q = 0; q < nred; ++q) {
     double v = 0.0;
-    for (int c = S.seg_chunk_ptr[sgi]; c < S.seg_chunk_ptr[sgi + 1]; ++c) {
-      const double pv = partial[(int64_t)q * S.nchunks + c];
+    for (int c = c0 + lane; c < c1; c += 32) {
+      const double pv = __ldcg(partial + (int64_t)q * S.nchunks + c);
       v = spec[q].op == 2 ? fmax(v, pv) : v + pv;
     }
+    v = spec[q].op == 2 ? warp_max(v) : warp_sum(v);
     if (spec[q].op == 1) v = sqrt(v);
-    spec[q].out[(int64_t)sgi * spec[q].stride] = v;
+    if (lane == 0) spec[q].out[(int64_t)sgi * spec[q].stride] = v;
   }
-  if (post == POST_NONE) return;
+  if (post == POST_NONE || lane != 0) return;
   KScal& k = sc[sgi];
   if (post == POST_CHECK_FULL) k.half_done = 0;
   if (!k.active) return;
@@ -118,6 +78,65 @@ __global__ void k_seg_final(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec
       k.iters = it;
       if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown) k.active = 0;
       break;
+  }
+}
+
+// One CTA per chunk: up to three reductions in one pass.
+//   op 0: sum x*y   op 1: sum x*x   op 2: max |x|
+// The last CTA of a segment to finish (counted in S.done) forms the
+// segment's results and its scalar step, then re-arms the counter.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_seg_reduce(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
+                 double* __restrict__ partial, int post, KScal* sc, double tol, int it) {
+  const int ch = blockIdx.x;
+  const int64_t b = S.chunk_beg[ch], e = S.chunk_end[ch];
+  RedSpec spec[3] = {r0, r1, r2};
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q >= nred) break;
+      const T* x = (const T*)spec[q].x;
+      const T* y = (const T*)spec[q].y;
+      const double xv = (double)x[i];
+      if (spec[q].op == 0)
+        acc[q] += xv * (double)y[i];
+      else if (spec[q].op == 1)
+        acc[q] += xv * xv;
+      else
+        acc[q] = fmax(acc[q], fabs(xv));
+    }
+  }
+  __shared__ double red[3][kThreads / 32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q >= nred) break;
+    double v = spec[q].op == 2 ? warp_max(acc[q]) : warp_sum(acc[q]);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  const int sgi = S.chunk_seg[ch];
+  if (threadIdx.x < 3 && (int)threadIdx.x < nred) {
+    const int q = threadIdx.x;
+    double v = red[q][0];
+    for (int w = 1; w < kThreads / 32; ++w) v = spec[q].op == 2 ? fmax(v, red[q][w]) : v + red[q][w];
+    partial[(int64_t)q * S.nchunks + ch] = v;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nch = S.seg_chunk_ptr[sgi + 1] - S.seg_chunk_ptr[sgi];
+    last = atomicAdd(&S.done[sgi], 1) == nch - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (warp == 0) {
+    seg_finalize(S, sgi, lane, nred, spec, partial, post, sc, tol, it);
+    if (lane == 0) S.done[sgi] = 0;
   }
 }
 
@@ -265,17 +284,15 @@ template <typename T>
 void seg_reduce(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2, double* partial,
                 cudaStream_t s) {
   if (S.nchunks == 0) return;
-  k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial);
-  k_seg_final<<<(S.nseg + 127) / 128, 128, 0, s>>>(S, nred, r0, r1, r2, partial, POST_NONE,
-                                                   nullptr, 0.0, 0);
+  k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial, POST_NONE, nullptr,
+                                                 0.0, 0);
 }
 
 template <typename T>
 void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
                      double* partial, int post, KScal* sc, double tol, int it, cudaStream_t s) {
-  if (S.nchunks > 0) k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial);
-  k_seg_final<<<(S.nseg + 127) / 128, 128, 0, s>>>(S, nred, r0, r1, r2, partial, post, sc, tol,
-                                                   it);
+  if (S.nchunks > 0)
+    k_seg_reduce<T><<<S.nchunks, kThreads, 0, s>>>(S, nred, r0, r1, r2, partial, post, sc, tol, it);
 }
 
 template <typename T>

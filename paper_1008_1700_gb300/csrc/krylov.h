@@ -13,7 +13,8 @@ struct SegView {
   const int64_t* chunk_beg;
   const int64_t* chunk_end;
   const int32_t* chunk_seg;
-  const int32_t* seg_chunk_ptr;  // nseg+1
+  const int32_t* seg_chunk_ptr;  // nseg+1 (every segment has at least one chunk)
+  int32_t* done;                 // nseg counters of finished chunks (zero between reductions)
   int32_t nchunks;
   int32_t nseg;
 };
