@@ -303,57 +303,51 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TG* __restrict__ base = ghat + ghat_off[b];
   const int64_t nvec = nc / VN;
-  for (int rr = warp * 2; rr < 64; rr += 16) {
-    const int64_t ra = r0 + rr, rb = r0 + rr + 1;
-    const bool va = ra < nrows, vb = rb < nrows;
-    const TG* __restrict__ pa = base + ra * gld[b];
-    const TG* __restrict__ pb = base + rb * gld[b];
-    AT sa = 0, sb = 0;
+  const int64_t ld = gld[b];
+  const int64_t q0 = gq0[b];
+  // each warp streams four rows at once (the last group of a block repeats
+  // its last valid row), two 16-byte loads per row and lane in flight
+  for (int rr = warp * 4; rr < 64; rr += 32) {
+    const int64_t ra = r0 + rr;
+    if (ra >= nrows) break;
+    const int nv = (int)min((int64_t)4, nrows - ra);
+    const TG* __restrict__ p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[u] = base + (ra + min(u, nv - 1)) * ld;
+    AT s4[4] = {0, 0, 0, 0};
+#pragma unroll 2
     for (int64_t q = lane; q < nvec; q += 32) {
-      AT ga[VN], gb[VN];
-      if (va) {
+      AT g[4][VN];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
         if constexpr (sizeof(TG) == 8) {
-          const double2 t = __ldcs(reinterpret_cast<const double2*>(pa + q * VN));
-          ga[0] = t.x;
-          ga[1] = t.y;
+          const double2 t = __ldcs(reinterpret_cast<const double2*>(p[u] + q * VN));
+          g[u][0] = t.x;
+          g[u][1] = t.y;
         } else {
           float tmp[VN];
-          load16<TG>(pa + q * VN, tmp);
+          load16<TG>(p[u] + q * VN, tmp);
 #pragma unroll
-          for (int e = 0; e < VN; ++e) ga[e] = tmp[e];
+          for (int e = 0; e < VN; ++e) g[u][e] = tmp[e];
         }
-#pragma unroll
-        for (int e = 0; e < VN; ++e) sa += ga[e] * xs[q * VN + e];
       }
-      if (vb) {
-        if constexpr (sizeof(TG) == 8) {
-          const double2 t = __ldcs(reinterpret_cast<const double2*>(pb + q * VN));
-          gb[0] = t.x;
-          gb[1] = t.y;
-        } else {
-          float tmp[VN];
-          load16<TG>(pb + q * VN, tmp);
 #pragma unroll
-          for (int e = 0; e < VN; ++e) gb[e] = tmp[e];
-        }
+      for (int e = 0; e < VN; ++e) {
+        const AT xv = xs[q * VN + e];
 #pragma unroll
-        for (int e = 0; e < VN; ++e) sb += gb[e] * xs[q * VN + e];
+        for (int u = 0; u < 4; ++u) s4[u] += g[u][e] * xv;
       }
     }
     for (int64_t j = nvec * VN + lane; j < nc; j += 32) {  // ragged tail
-      if (va) sa += to_acc<AT>(pa[j]) * xs[j];
-      if (vb) sb += to_acc<AT>(pb[j]) * xs[j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s4[u] += to_acc<AT>(p[u][j]) * xs[j];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sa += __shfl_xor_sync(0xffffffffu, sa, o);
-      sb += __shfl_xor_sync(0xffffffffu, sb, o);
-    }
-    if (lane == 0) {
-      const int64_t q0 = gq0[b];
-      if (va) w[q0 + ra] = (TI)((AT)v[q0 + ra] + sa);
-      if (vb) w[q0 + rb] = (TI)((AT)v[q0 + rb] + sb);
-    }
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s4[u] += __shfl_xor_sync(0xffffffffu, s4[u], o);
+    if (lane == 0)
+      for (int u = 0; u < nv; ++u) w[q0 + ra + u] = (TI)((AT)v[q0 + ra + u] + s4[u]);
   }
 }
 
