@@ -179,6 +179,15 @@ class ClockSampler:
 # algorithmic work per kernel class (bytes for memory-bound, flops for ALU-bound)
 # ----------------------------------------------------------------------------
 
+# DRAM bytes per algorithmic byte of a launch, from one ncu capture of the
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic
+# bytes of that launch; profiles/ncu_ghat_matvec_tiled_cd3d_48.md): a launch's
+# traffic is this ratio times its algorithmic bytes.  Classes without a
+# capture of their current kernel report null.
+TRAFFIC_RATIO = {"ghat_matvec": (1.012, "ncu --set full, k_ghat_matvec_tiled<__half,float>, "
+                                        "cd3d_48_slabs8 (279.6 MB per 276.3 MB), scaled by bytes")}
+
+
 def algorithmic_work(sizes, P, form, steps, prof):
     """Per class: (kind, total algorithmic amount over the timed region)."""
     sf = 8 if form == "fp64" else 4
@@ -387,7 +396,8 @@ def run_ours(args):
 
     # accuracy of the last step against the known solution and the residual
     xh = x.cpu().numpy()
-    err_xtrue = float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))
+    err_xtrue = (float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))
+                 if P.x_true is not None else None)
     relres = max(i["relres_inf"] for i in infos)
     converged = all(i["status"] == "DDPS_OK" for i in infos)
 
@@ -424,9 +434,14 @@ def run_ours(args):
         bound = "alu"
         peak_note = ("FP64: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz if args.form == "fp64"
                      else "FP32 SIMT: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz)
+    traffic, traffic_note = None, None
+    if dk["unit"] == "GB/s" and dom in TRAFFIC_RATIO and args.form == "mixed":
+        ratio, traffic_note = TRAFFIC_RATIO[dom]
+        per_launch = work[dom][1] / max(prof[dom][1], 1)
+        traffic = int(ratio * per_launch)
     roof = {"kernel": dom, "bound": bound, "achieved": dk["achieved"], "peak": round(peak, 2),
-            "unit": dk["unit"], "frac": round(dk["achieved"] / peak, 4), "traffic": None,
-            "peak_source": peak_note}
+            "unit": dk["unit"], "frac": round(dk["achieved"] / peak, 4), "traffic": traffic,
+            "traffic_source": traffic_note, "peak_source": peak_note}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
