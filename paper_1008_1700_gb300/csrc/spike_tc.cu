@@ -548,33 +548,35 @@ __device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_
 // takes a contiguous range of work items (front, 128-column tile); a tile is
 // nkt K-stages of 32 panel rows.  A stage lives in one slot of a ring of SR
 // 16 KB slots from the moment its rows are copied in until its MMAs complete:
-//   warps 12-15 (row producers, stage g by warp 12 + g % NPROD): one 1-D bulk
+//   warps 16-19 (row producers, stage g by warp 16 + g % NPROD): one 1-D bulk
 //     copy per panel row (fp32, up to 512 bytes, gathered through the front's
 //     row list) into the stage's slot.  One warp streams copies at a bounded
 //     rate, so several issue side by side; every slot belongs to one warp;
-//   warp 17 lane 0 (W producer): the stage's W block into a ring of SW slots;
-//   warps 0-3 (converters): read the slot's fp32 rows, then (after a barrier
-//     of the four warps) overwrite the slot with the bf16 (high, remainder)
+//   warp 20 lane 0 (W producer): the stage's W block into a ring of SW slots;
+//   warps 0-7 (converters): read the slot's fp32 rows, then (after a barrier
+//     of the eight warps) overwrite the slot with the bf16 (high, remainder)
 //     K-major operand;
-//   warp 16 lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256 output rows)
-//     into one of NACC tensor-memory accumulators; its commits hand the slot
-//     and the W slot back to the producers and, after the tile's last stage,
-//     the accumulator to the epilogue;
-//   warps 4-11 (epilogue, two groups of four): tcgen05.ld of lane quarter
+//   warps 21 .. 20 + NACC, lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256
+//     output rows) into one of NACC tensor-memory accumulators, tile t by the
+//     thread of accumulator t % NACC; the commits hand the slot and the W slot
+//     back to the producers and, after the tile's last stage, the accumulator
+//     to the epilogue;
+//   warps 8-15 (epilogue, two groups of four): tcgen05.ld of lane quarter
 //     (warp % 4); group q stores the 16-row groups q, q + 2, ...; one 128-byte
 //     row segment per store (forward: the update rows are read one group
 //     ahead and accumulated).
 // Every wait is bounded: a wait that runs out records error code 2 at once
 // (so that the other waits of every CTA give up quickly), the role stops,
 // and before exiting each producer lets its own copies land.
-constexpr int FG_CONV = 128;   // converter threads (warps 0-3)
-constexpr int FG_EPI0 = 4;     // epilogue warps 4-11 (tensor-memory lane quarter = warp % 4)
+constexpr int FG_CONV = 256;   // converter threads (warps 0-7)
+constexpr int FG_EPI0 = 8;     // epilogue warps 8-15 (tensor-memory lane quarter = warp % 4)
 constexpr int FG_NEPI = 8;
-constexpr int FG_PROD0 = 12;   // producer warps 12-15
+constexpr int FG_PROD0 = 16;   // producer warps 16-19
 constexpr int FG_NPROD = 4;
-constexpr int FG_MMA = 16;     // MMA issuer warp
-constexpr int FG_WPROD = 17;   // W producer warp
-constexpr int FG_THREADS = 18 * 32;
+constexpr int FG_WPROD = 20;   // W producer warp
+constexpr int FG_MMA0 = 21;    // MMA issuer warps 21 .. 21 + NACC - 1 (one per accumulator)
+constexpr int FG_MAXACC = 2;
+constexpr int FG_THREADS = (FG_MMA0 + FG_MAXACC) * 32;
 
 template <int DIR, int NT, int PASSES, int SR, int SW, int NACC, int NPROD>
 __global__ void __launch_bounds__(FG_THREADS, 1)
@@ -585,10 +587,12 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
                     int inject_wait) {
   // every ring slot is always filled by the same producer warp, so that no
   // producer waits on a slot barrier more than one phase ahead of it
-  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD, "ring ownership");
+  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD && NACC <= FG_MAXACC, "ring ownership");
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t raw_full[SR], op_full[SR], slot_empty[SR];
-  __shared__ __align__(8) uint64_t w_full[SW], w_empty[SW], acc_full[NACC], acc_empty[NACC];
+  // op_full and w_full are split by MMA thread (the owner of the stage's
+  // tile, t % NACC): each has one consumer, which sees its phases in order
+  __shared__ __align__(8) uint64_t raw_full[SR], op_full[NACC][SR], slot_empty[SR];
+  __shared__ __align__(8) uint64_t w_full[NACC][SW], w_empty[SW], acc_full[NACC], acc_empty[NACC];
   __shared__ __align__(8) uint64_t never;
   __shared__ uint32_t tmem_slot;
   __shared__ int skip_all;
@@ -611,12 +615,14 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   if (tid == 0) {
     for (int i = 0; i < SR; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&op_full[i])),
-                   "r"(FG_CONV));
+      for (int a = 0; a < NACC; ++a)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&op_full[a][i])),
+                     "r"(FG_CONV));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_empty[i])));
     }
     for (int i = 0; i < SW; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_full[i])));
+      for (int a = 0; a < NACC; ++a)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_full[a][i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_empty[i])));
     }
     for (int i = 0; i < NACC; ++i) {
@@ -647,6 +653,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     }
   };
   uint32_t issued = 0;  // producer: stages issued
+  uint32_t wpar[NACC] = {}, last_own = 0u, last_par = 0u;  // W producer: phases per (owner, slot)
 
   if (warp >= FG_PROD0 && warp < FG_PROD0 + NPROD) {
     // ---------------- producers ----------------
@@ -700,27 +707,37 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     // W blocks come from their own warp, so that they do not queue behind the
     // row copies; a W slot is refilled once the MMAs of its stage completed.
     if (lane == 0) {
-      uint32_t g = 0;
+      uint32_t g = 0, tc = 0;
       FItem w;
-      for (int it = it0; it < it1 && !bail; ++it) {
-        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      for (int it = it0; it < it1 && !bail; ++it, ++tc) {
+        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) {
+          --tc;
+          continue;
+        }
+        const uint32_t own = tc % NACC;
         for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t ws = g % SW;
           if (g >= SW) wait(&w_empty[ws], ((g / SW) - 1) & 1);
           if (bail) break;
-          mbar_expect_tx(smem_u32(&w_full[ws]), w.wblk);
-          bulk_g2s(w0 + ws * kWs, w.w + (int64_t)kt * w.wblk, w.wblk, smem_u32(&w_full[ws]));
+          mbar_expect_tx(smem_u32(&w_full[own][ws]), w.wblk);
+          bulk_g2s(w0 + ws * kWs, w.w + (int64_t)kt * w.wblk, w.wblk, smem_u32(&w_full[own][ws]));
           issued = g + 1;
+          // for the drain after a timeout: owner and phase parity of slot ws's last fill
+          const uint32_t par = (wpar[own] >> ws) & 1u;
+          wpar[own] ^= 1u << ws;
+          last_own = (last_own & ~(3u << (2 * ws))) | (own << (2 * ws));
+          last_par = (last_par & ~(1u << ws)) | (par << ws);
         }
       }
     }
   } else if (warp < FG_CONV / 32) {
     // ---------------- converters ----------------
     const int ct = tid;
-    uint32_t g = 0;
+    uint32_t g = 0, tc = 0;
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
       if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      const uint32_t own = tc++ % NACC;
       for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
         const uint32_t sl = g % SR;
         wait(&raw_full[sl], (g / SR) & 1);
@@ -739,7 +756,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
             v[q][u] = (!bail && r < nr && col < w.cv) ? raw[r * TC_BN + col] : 0.f;
           }
         }
-        // the four warps have read the slot before any overwrites it; the
+        // the converter warps have read the slot before any overwrites it; the
         // barrier also makes a timeout in any of them a decision of all
         uint32_t any_bail;
         asm volatile(
@@ -757,21 +774,30 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
           store_split_x2(slot + off, slot + TC_TILE_BYTES + off, v[q], PASSES == 3);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(smem_u32(&op_full[sl]));
+        mbar_arrive(smem_u32(&op_full[own][sl]));
       }
     }
-  } else if (warp == FG_MMA) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp >= FG_MMA0 && warp < FG_MMA0 + NACC) {
+    // ---------------- MMA issuers ----------------
+    // tile t is issued by the thread of accumulator t % NACC, so that the
+    // per-stage issue work of NACC tiles overlaps
+    const uint32_t mine = (uint32_t)(warp - FG_MMA0);
     if (lane == 0) {
       // descriptors differ only in their start-address field (address / 16,
       // 14 bits; every address here is below 256 KB): build the two bases
       // once and add offsets, so that issuing a stage costs few instructions
       const uint64_t dS = make_desc(sbase, 128, kSBO), dW = make_desc(w0, 128, kSBO);
       uint32_t g = 0, tc = 0;
+      uint32_t opar = 0u, wpar_m = 0u;  // phase parity of this thread's barriers, bit per slot
       FItem w;
       for (int it = it0; it < it1 && !bail; ++it) {
         if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
         const uint32_t a = tc % NACC;
+        if (a != mine) {  // another thread's tile: skip its stages
+          g += w.nkt;
+          ++tc;
+          continue;
+        }
         if (tc >= NACC) wait(&acc_empty[a], ((tc / NACC) - 1) & 1);
         const uint32_t acc = tmem + a * NT;
         const uint32_t id0 = idesc_m128(min(256, w.nf));
@@ -779,9 +805,11 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
         const uint64_t lo_w = w.wpart >> 4;
         for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t sl = g % SR, ws = g % SW;
-          wait(&op_full[sl], (g / SR) & 1);
-          wait(&w_full[ws], (g / SW) & 1);
+          wait(&op_full[a][sl], (opar >> sl) & 1u);
+          wait(&w_full[a][ws], (wpar_m >> ws) & 1u);
           if (bail) break;
+          opar ^= 1u << sl;
+          wpar_m ^= 1u << ws;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t aHi = dS + ((sl * kSlot) >> 4), aLo = aHi + (TC_TILE_BYTES >> 4);
           const uint64_t bHi = dW + ((ws * kWs) >> 4), bLo = bHi + lo_w;
@@ -882,8 +910,8 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       if ((int)(g % NPROD) == warp - FG_PROD0) mbar_drain(smem_u32(&raw_full[g % SR]), (g / SR) & 1);
   }
   if (warp == FG_WPROD && lane == 0 && bail)
-    for (uint32_t g = issued > SW ? issued - SW : 0; g < issued; ++g)
-      mbar_drain(smem_u32(&w_full[g % SW]), (g / SW) & 1);
+    for (uint32_t ws = 0; ws < (uint32_t)SW && ws < issued; ++ws)
+      mbar_drain(smem_u32(&w_full[(last_own >> (2 * ws)) & 3u][ws]), (last_par >> ws) & 1u);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -897,7 +925,7 @@ template <int NT>
 struct FrontCfg {
   static constexpr int SR = NT <= 128 ? 8 : 4;
   static constexpr int SW = NT <= 128 ? 6 : NT <= 256 ? 4 : 2;
-  static constexpr int NACC = NT <= 256 ? 2 : 1;
+  static constexpr int NACC = NT <= 256 ? 2 : 1;  // accumulators = MMA threads
   static constexpr int NPROD = 4;  // row producer warps (divides SR)
 };
 
