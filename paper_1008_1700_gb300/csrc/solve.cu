@@ -42,6 +42,27 @@ __global__ void k_permute_out(const T* __restrict__ w, const int32_t* __restrict
 // memory) starts with the pivot entries of w and zeros and receives the
 // children's update vectors; then y = L11^-1 t(piv) goes back to w and the
 // update entries t(upd) - L21 y go to u for the parent.
+// sum_{j0 <= j < j1} A[i + j m] x[j] (A column-major with leading dimension
+// m, x in shared memory): eight loads in flight and four partial sums, so
+// that a long row costs a few memory latencies rather than one per term.
+template <typename T>
+__device__ __forceinline__ T dot_row(const T* __restrict__ A, int64_t m, int i, int j0, int j1,
+                                     const T* x) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int j = j0;
+  for (; j + 8 <= j1; j += 8) {
+    T a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = A[i + (int64_t)(j + u) * m];
+    s0 += a[0] * x[j] + a[4] * x[j + 4];
+    s1 += a[1] * x[j + 1] + a[5] * x[j + 5];
+    s2 += a[2] * x[j + 2] + a[6] * x[j + 6];
+    s3 += a[3] * x[j + 3] + a[7] * x[j + 7];
+  }
+  for (; j < j1; ++j) s0 += A[i + (int64_t)j * m] * x[j];
+  return (s0 + s1) + (s2 + s3);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_fwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
@@ -64,17 +85,9 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = tid; i < rc; i += blockDim.x) t[rel[i]] += uc[i];
     __syncthreads();
   }
-  for (int i = tid; i < k; i += blockDim.x) {
-    T s = t[i];
-    for (int j = 0; j < i; ++j) s += A[i + (int64_t)j * m] * t[j];
-    y[i] = s;
-  }
+  for (int i = tid; i < k; i += blockDim.x) y[i] = t[i] + dot_row(A, m, i, 0, i, t);
   __syncthreads();
-  for (int i = k + tid; i < m; i += blockDim.x) {
-    T s = t[i];
-    for (int j = 0; j < k; ++j) s -= A[i + (int64_t)j * m] * y[j];
-    u[F.upd[f] + (i - k)] = s;
-  }
+  for (int i = k + tid; i < m; i += blockDim.x) u[F.upd[f] + (i - k)] = t[i] - dot_row(A, m, i, 0, k, y);
   for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = y[i];
 }
 
@@ -95,17 +108,9 @@ __global__ void __launch_bounds__(kThreads)
   T* xu = t + k;
   for (int j = tid; j < r; j += blockDim.x) xu[j] = w[idx[k + j]];
   __syncthreads();
-  for (int i = tid; i < k; i += blockDim.x) {
-    T acc = w[row0 + i];
-    for (int j = 0; j < r; ++j) acc -= A[i + (int64_t)(k + j) * m] * xu[j];
-    t[i] = acc;
-  }
+  for (int i = tid; i < k; i += blockDim.x) t[i] = w[row0 + i] - dot_row(A + (int64_t)k * m, m, i, 0, r, xu);
   __syncthreads();
-  for (int i = tid; i < k; i += blockDim.x) {
-    T s = T(0);
-    for (int j = i; j < k; ++j) s += A[i + (int64_t)j * m] * t[j];
-    w[row0 + i] = s;
-  }
+  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = dot_row(A, m, i, i, k, t);
 }
 
 // y = A x, CSR, four lanes per row.
