@@ -70,11 +70,12 @@ __global__ void k_extend_add_p(DevFronts F, const int32_t* __restrict__ parent,
   const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
   const T* __restrict__ C = arena + F.arena[c];
   T* __restrict__ P = arena + F.arena[p];
-  const int64_t rr = (int64_t)r * r;
-  for (int64_t t = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; t < rr;
-       t += (int64_t)gridDim.y * blockDim.x) {
-    const int32_t i = (int32_t)(t % r), j = (int32_t)(t / r);
-    P[rel[i] + (int64_t)rel[j] * mp] += C[(kc + i) + (int64_t)(kc + j) * mc];
+  // one warp per update column, lanes over its rows (no index division)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int32_t j = blockIdx.y * nw + warp; j < r; j += gridDim.y * nw) {
+    T* __restrict__ Pc = P + (int64_t)rel[j] * mp;
+    const T* __restrict__ Cc = C + kc + (int64_t)(kc + j) * mc;
+    for (int32_t i = lane; i < r; i += 32) Pc[rel[i]] += Cc[i];
   }
 }
 
@@ -119,12 +120,10 @@ __global__ void __launch_bounds__(kThreads)
       const T inv = T(1) / piv;
       for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
       __syncthreads();
-      const int nr = m - (j + 1);
-      const int nc = j0 + jb - (j + 1);
-      for (int t = tid; t < nr * nc; t += blockDim.x) {
-        const int i = j + 1 + t % nr;
-        const int c = j + 1 + t / nr;
-        A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * A[j + (int64_t)c * m];
+      for (int c = j + 1 + (tid >> 5); c < j0 + jb; c += blockDim.x >> 5) {
+        const T u = A[j + (int64_t)c * m];
+        for (int i = j + 1 + (tid & 31); i < m; i += 32)
+          A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * u;
       }
       __syncthreads();
     }
@@ -233,12 +232,10 @@ __global__ void __launch_bounds__(kThreads)
     const T inv = T(1) / piv;
     for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
     __syncthreads();
-    const int nr = m - (j + 1);
-    const int nc = j0 + jb - (j + 1);
-    for (int t = tid; t < nr * nc; t += blockDim.x) {
-      const int i = j + 1 + t % nr;
-      const int c = j + 1 + t / nr;
-      A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * A[j + (int64_t)c * m];
+    for (int c = j + 1 + (tid >> 5); c < j0 + jb; c += blockDim.x >> 5) {
+      const T u = A[j + (int64_t)c * m];
+      for (int i = j + 1 + (tid & 31); i < m; i += 32)
+        A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * u;
     }
     __syncthreads();
   }
@@ -472,11 +469,10 @@ __global__ void __launch_bounds__(kThreads)
     const T inv = T(1) / piv;
     for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + j * m] *= inv;
     __syncthreads();
-    const int nr = m - (j + 1);
-    for (int t = tid; t < nr * nr; t += blockDim.x) {
-      const int i = j + 1 + t % nr;
-      const int c = j + 1 + t / nr;
-      A[i + c * m] -= A[i + j * m] * A[j + c * m];
+    // rank-1 update: one warp per column, lanes over rows (no index division)
+    for (int c = j + 1 + (tid >> 5); c < m; c += blockDim.x >> 5) {
+      const T u = A[j + c * m];
+      for (int i = j + 1 + (tid & 31); i < m; i += 32) A[i + c * m] -= A[i + j * m] * u;
     }
     __syncthreads();
   }
