@@ -456,27 +456,58 @@ __global__ void __launch_bounds__(TC_THREADS)
   __syncthreads();
   const uint32_t part = (uint32_t)nf * TC_BK * 2;
   unsigned char* dst = wpk + woff[f] + (int64_t)kb * (PASSES == 3 ? 2 : 1) * part;
+  if constexpr (DIR == DIR_FWD) {
+  // forward (m output rows): one thread per row, the 32 entries of the row in
+  // this K-block as outer products (a coalesced column read of L21 per term,
+  // the row of L11^-1 from shared memory), then 16-byte stores
+  for (int i = threadIdx.x; i < nf; i += TC_THREADS) {
+    float acc[TC_BK];
+#pragma unroll
+    for (int jj = 0; jj < TC_BK; ++jj) acc[jj] = 0.f;
+    if (i < nout && i >= k) {
+      for (int l = j0; l < k; ++l) {  // -sum_l L21(i, l) L11^-1(l, j); L11^-1(l, j) = 0 for l < j
+        const float a = A[i + (int64_t)l * m];
+        const float* __restrict__ r = Rs + l * (TC_BK + 1);
+#pragma unroll
+        for (int jj = 0; jj < TC_BK; ++jj) acc[jj] = fmaf(a, r[jj], acc[jj]);
+      }
+    }
+#pragma unroll
+    for (int kc = 0; kc < TC_BK / 8; ++kc) {
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int jj = kc * 8 + t, j = j0 + jj;
+        float w = 0.f;
+        if (i < nout && j < K)
+          w = i < k ? (i > j ? A[i + (int64_t)j * m] : (i == j ? 1.f : 0.f)) : -acc[jj];
+        v[t] = w;
+      }
+      const uint32_t off = chunk_off(i, kc);
+      store_split(dst + off, dst + part + off, v, PASSES == 3);
+    }
+  }
+  } else {
+  // backward (k output rows, often few): one warp per row, lanes over the
+  // 32 columns; -sum_{l >= i} U11^-1(i, l) U12(l, j) for the columns j >= k
   const int jj = threadIdx.x & 31;
   const int j = j0 + jj;
   for (int i = threadIdx.x >> 5; i < nf; i += TC_THREADS / 32) {
     float w = 0.f;
     if (i < nout && j < K) {
-      if (DIR == DIR_BWD) {
-        if (j < k) {
-          w = i <= j ? A[i + (int64_t)j * m] : 0.f;
-        } else {
-          float acc = 0.f;
-          for (int l = i; l < k; ++l) acc = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], acc);
-          w = -acc;
-        }
+      if (j < k) {
+        w = i <= j ? A[i + (int64_t)j * m] : 0.f;
       } else {
-        if (i < k) {
-          w = i > j ? A[i + (int64_t)j * m] : (i == j ? 1.f : 0.f);
-        } else {
-          float acc = 0.f;
-          for (int l = j0; l < k; ++l) acc = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], acc);
-          w = -acc;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int l = i;
+        for (; l + 4 <= k; l += 4) {
+          a0 = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], a0);
+          a1 = fmaf(A[i + (int64_t)(l + 1) * m], Rs[(l + 1) * (TC_BK + 1) + jj], a1);
+          a2 = fmaf(A[i + (int64_t)(l + 2) * m], Rs[(l + 2) * (TC_BK + 1) + jj], a2);
+          a3 = fmaf(A[i + (int64_t)(l + 3) * m], Rs[(l + 3) * (TC_BK + 1) + jj], a3);
         }
+        for (; l < k; ++l) a0 = fmaf(A[i + (int64_t)l * m], Rs[l * (TC_BK + 1) + jj], a0);
+        w = -((a0 + a1) + (a2 + a3));
       }
     }
     uint16_t hi, lo;
@@ -484,6 +515,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     const uint32_t off = chunk_off(i, jj >> 3) + (jj & 7) * 2;
     *reinterpret_cast<uint16_t*>(dst + off) = hi;
     if (PASSES == 3) *reinterpret_cast<uint16_t*>(dst + part + off) = lo;
+  }
   }
 }
 
