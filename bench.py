@@ -55,6 +55,9 @@ def parse_args():
                          "0 for randband_1m whose FP64 factor takes over a minute)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--drop-sweep", action="store_true",
+                    help="instead of the bench line: the Sec. 3 column rule on the random-band "
+                         "workload for several delta (outer/inner iterations, |c|, solves/s)")
     return ap.parse_args()
 
 
@@ -615,8 +618,70 @@ def run_sequence_bench(args):
     S.close()
 
 
+def run_drop_sweep(args):
+    """Sec. 3 column rule (drop column k of R_i when its inf-norm is at most
+    delta times the largest of the block) on the 1M random-band workload, one
+    row per delta: kept coupling columns, G^ entries, outer and inner
+    iterations, factor and solve times and solves/s (mixed form), the way the
+    paper varies its dropping threshold.  Times are CUDA events over `steps`
+    factor + solve steps after one warm-up step."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1008_1700_gb300 import Solver
+    from paper_1008_1700_gb300 import native as N
+
+    P = W.cfg4()
+    vals = torch.tensor(P.values, device="cuda")
+    f = torch.tensor(P.f, device="cuda")
+    x = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for delta in (0.99, 0.9, 0.6, 0.3, 0.1, 1e-5):
+        opts = form_options(args.form)
+        opts.update(drop_mode=N.DDPS_DROP_COLUMN, drop_tol=delta)
+        t0 = time.perf_counter()
+        S = Solver(P.rowptr, P.colind, P.block_ptr, values_host=P.values, **opts)
+        analyze_ms = (time.perf_counter() - t0) * 1e3
+        sizes = S.sizes
+        S.factor(vals)
+        S.solve(f, x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        fac_ms = sol_ms = 0.0
+        info = None
+        for _ in range(args.steps):
+            e0.record(stream)
+            S.factor(vals)
+            e1.record(stream)
+            _, info = S.solve(f, x)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            fac_ms += e0.elapsed_time(e1)
+            sol_ms += e1.elapsed_time(e2)
+        err = float(np.linalg.norm(x.cpu().numpy() - P.x_true) / np.linalg.norm(P.x_true))
+        rows.append({"delta": delta, "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
+                     "outer_iterations": info["outer_iterations"],
+                     "inner_iterations": info["inner_iterations"],
+                     "factor_ms": round(fac_ms / args.steps, 2), "solve_ms": round(sol_ms / args.steps, 2),
+                     "solves_per_s": round(args.steps / ((fac_ms + sol_ms) / 1e3), 4),
+                     "relres_inf": info["relres_inf"], "rel_err_vs_xtrue": err,
+                     "status": info["status"], "analyze_ms": round(analyze_ms, 1)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        S.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"experiment": "drop_sweep", "rule": "column (Sec. 3)", "workload": "randband_1m",
+                      "form": args.form, "steps": args.steps, "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.drop_sweep:
+        run_drop_sweep(args)
+        return
     if args.fp64_steps is None:
         args.fp64_steps = 0 if args.workload == "randband_1m" else 1
     if args.impl == "reference":
