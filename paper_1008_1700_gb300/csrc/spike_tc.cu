@@ -588,11 +588,11 @@ __device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_
 //   warps 0-7 (converters): read the slot's fp32 rows, then (after a barrier
 //     of the eight warps) overwrite the slot with the bf16 (high, remainder)
 //     K-major operand;
-//   warps 21 .. 20 + NACC, lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256
-//     output rows) into one of NACC tensor-memory accumulators, tile t by the
-//     thread of accumulator t % NACC; the commits hand the slot and the W slot
-//     back to the producers and, after the tile's last stage, the accumulator
-//     to the epilogue;
+//   warps 21 .. 20 + NMMA, lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256
+//     output rows) into one of NACC tensor-memory accumulators, tile t by
+//     thread t % NMMA into accumulator t % NACC; the commits hand the slot and
+//     the W slot back to the producers and, after the tile's last stage, the
+//     accumulator to the epilogue;
 //   warps 8-15 (epilogue, two groups of four): tcgen05.ld of lane quarter
 //     (warp % 4); group q stores the 16-row groups q, q + 2, ...; one 128-byte
 //     row segment per store (forward: the update rows are read one group
@@ -606,11 +606,11 @@ constexpr int FG_NEPI = 8;
 constexpr int FG_PROD0 = 16;   // producer warps 16-19
 constexpr int FG_NPROD = 4;
 constexpr int FG_WPROD = 20;   // W producer warp
-constexpr int FG_MMA0 = 21;    // MMA issuer warps 21 .. 21 + NACC - 1 (one per accumulator)
-constexpr int FG_MAXACC = 2;
-constexpr int FG_THREADS = (FG_MMA0 + FG_MAXACC) * 32;
+constexpr int FG_MMA0 = 21;    // MMA issuer warps 21 .. 21 + NMMA - 1
+constexpr int FG_MAXMMA = 2;
+constexpr int FG_THREADS = (FG_MMA0 + FG_MAXMMA) * 32;
 
-template <int DIR, int NT, int PASSES, int SR, int SW, int NACC, int NPROD>
+template <int DIR, int NT, int PASSES, int SR, int SW, int NACC, int NMMA, int NPROD>
 __global__ void __launch_bounds__(FG_THREADS, 1)
     k_front_gemm_tc(DevFronts F, const int32_t* __restrict__ fronts, int32_t nitems, int32_t nct,
                     const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
@@ -619,12 +619,13 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
                     int inject_wait) {
   // every ring slot is always filled by the same producer warp, so that no
   // producer waits on a slot barrier more than one phase ahead of it
-  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD && NACC <= FG_MAXACC, "ring ownership");
+  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD && NMMA <= FG_MAXMMA && NACC % NMMA == 0,
+                "ring ownership");
   extern __shared__ __align__(1024) unsigned char smem[];
   // op_full and w_full are split by MMA thread (the owner of the stage's
-  // tile, t % NACC): each has one consumer, which sees its phases in order
-  __shared__ __align__(8) uint64_t raw_full[SR], op_full[NACC][SR], slot_empty[SR];
-  __shared__ __align__(8) uint64_t w_full[NACC][SW], w_empty[SW], acc_full[NACC], acc_empty[NACC];
+  // tile, t % NMMA): each has one consumer, which sees its phases in order
+  __shared__ __align__(8) uint64_t raw_full[SR], op_full[NMMA][SR], slot_empty[SR];
+  __shared__ __align__(8) uint64_t w_full[NMMA][SW], w_empty[SW], acc_full[NACC], acc_empty[NACC];
   __shared__ __align__(8) uint64_t never;
   __shared__ uint32_t tmem_slot;
   __shared__ int skip_all;
@@ -647,13 +648,13 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   if (tid == 0) {
     for (int i = 0; i < SR; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[i])));
-      for (int a = 0; a < NACC; ++a)
+      for (int a = 0; a < NMMA; ++a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&op_full[a][i])),
                      "r"(FG_CONV));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_empty[i])));
     }
     for (int i = 0; i < SW; ++i) {
-      for (int a = 0; a < NACC; ++a)
+      for (int a = 0; a < NMMA; ++a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_full[a][i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&w_empty[i])));
     }
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     }
   };
   uint32_t issued = 0;  // producer: stages issued
-  uint32_t wpar[NACC] = {}, last_own = 0u, last_par = 0u;  // W producer: phases per (owner, slot)
+  uint32_t wpar[NMMA] = {}, last_own = 0u, last_par = 0u;  // W producer: phases per (owner, slot)
 
   if (warp >= FG_PROD0 && warp < FG_PROD0 + NPROD) {
     // ---------------- producers ----------------
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
           --tc;
           continue;
         }
-        const uint32_t own = tc % NACC;
+        const uint32_t own = tc % NMMA;
         for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t ws = g % SW;
           if (g >= SW) wait(&w_empty[ws], ((g / SW) - 1) & 1);
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
       if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
-      const uint32_t own = tc++ % NACC;
+      const uint32_t own = tc++ % NMMA;
       for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
         const uint32_t sl = g % SR;
         wait(&raw_full[sl], (g / SR) & 1);
@@ -809,10 +810,11 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
         mbar_arrive(smem_u32(&op_full[own][sl]));
       }
     }
-  } else if (warp >= FG_MMA0 && warp < FG_MMA0 + NACC) {
+  } else if (warp >= FG_MMA0 && warp < FG_MMA0 + NMMA) {
     // ---------------- MMA issuers ----------------
-    // tile t is issued by the thread of accumulator t % NACC, so that the
-    // per-stage issue work of NACC tiles overlaps
+    // tile t is issued by thread t % NMMA into accumulator t % NACC, so that
+    // the per-stage issue work of NMMA tiles overlaps and a tile's epilogue
+    // has NACC / NMMA tiles of one thread to finish in
     const uint32_t mine = (uint32_t)(warp - FG_MMA0);
     if (lane == 0) {
       // descriptors differ only in their start-address field (address / 16,
@@ -825,7 +827,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       for (int it = it0; it < it1 && !bail; ++it) {
         if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
         const uint32_t a = tc % NACC;
-        if (a != mine) {  // another thread's tile: skip its stages
+        if (tc % NMMA != mine) {  // another thread's tile: skip its stages
           g += w.nkt;
           ++tc;
           continue;
@@ -837,8 +839,8 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
         const uint64_t lo_w = w.wpart >> 4;
         for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t sl = g % SR, ws = g % SW;
-          wait(&op_full[a][sl], (opar >> sl) & 1u);
-          wait(&w_full[a][ws], (wpar_m >> ws) & 1u);
+          wait(&op_full[mine][sl], (opar >> sl) & 1u);
+          wait(&w_full[mine][ws], (wpar_m >> ws) & 1u);
           if (bail) break;
           opar ^= 1u << sl;
           wpar_m ^= 1u << ws;
@@ -957,7 +959,8 @@ template <int NT>
 struct FrontCfg {
   static constexpr int SR = NT <= 128 ? 8 : 4;
   static constexpr int SW = NT <= 128 ? 6 : NT <= 256 ? 4 : 2;
-  static constexpr int NACC = NT <= 256 ? 2 : 1;  // accumulators = MMA threads
+  static constexpr int NACC = NT <= 128 ? 4 : NT <= 256 ? 2 : 1;  // accumulators
+  static constexpr int NMMA = NACC >= 2 ? 2 : 1;                   // MMA-issuing threads
   static constexpr int NPROD = 4;  // row producer warps (divides SR)
 };
 
@@ -966,7 +969,7 @@ void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t
                   const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
                   float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
   using C = FrontCfg<NT>;
-  auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NPROD>;
+  auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NMMA, C::NPROD>;
   constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
                         (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2;
   static int nsm = 0;
