@@ -55,6 +55,7 @@ struct LevelSplit {
   // fronts [pf_ptr[p], pf_ptr[p+1]) of lu_panel_fronts and tiles
   // [pt_ptr[p], pt_ptr[p+1]) of lu_tile_front / lu_tile_ij
   std::vector<int64_t> pf_ptr, pt_ptr;
+  std::vector<int32_t> pf_rows;  // per panel step: the largest m - j0 of its fronts
   int32_t inv_first = 0, inv_ntiles = 0;  // multi-CTA inverse tiles of the large fronts
 };
 
@@ -374,7 +375,8 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       for (size_t pstep = 0; pstep + 1 < ls.pf_ptr.size(); ++pstep) {
         const int32_t j0 = (int32_t)pstep * kLuPanel;
         launch_lu_panel<T>(h->F, h->lu_panel_fronts + ls.pf_ptr[pstep],
-                           (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]), j0, arena,
+                           (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]), j0,
+                           ls.pf_rows[pstep], arena,
                            h->rownorm, h->opt.pivot_tol, h->derr, s);
         launch_lu_trailing<T>(h->F, h->lu_tile_front + ls.pt_ptr[pstep],
                               h->lu_tile_ij + ls.pt_ptr[pstep],
@@ -1120,10 +1122,12 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       ls.pt_ptr.assign(1, (int64_t)tfront.size());
       for (int pstep = 0; pstep < npanel; ++pstep) {
         const int32_t j0 = pstep * kLuPanel;
+        int32_t rows = 0;
         for (int32_t i = ls.first + ls.nsmall; i < (int32_t)order.size(); ++i) {
           const int32_t f = order[i];
           if (A.f_k[f] <= j0) continue;
           pfronts.push_back(f);
+          rows = std::max(rows, A.f_m[f] - j0);
           const int32_t t0 = std::min(j0 + kLuPanel, A.f_k[f]);
           const int32_t nt = (A.f_m[f] - t0 + kLuTile - 1) / kLuTile;
           for (int32_t ti = 0; ti < nt; ++ti)
@@ -1134,6 +1138,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
         }
         ls.pf_ptr.push_back((int64_t)pfronts.size());
         ls.pt_ptr.push_back((int64_t)tfront.size());
+        ls.pf_rows.push_back(rows);
       }
     }
     h->lu_order = dupload(h, order);

@@ -263,6 +263,81 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The same panel step with the panel (rows j0 .. m-1 of its <= 32 columns,
+// column-major with leading dimension ldp) factored in shared memory: one
+// load and one store of the panel instead of global traffic and latency on
+// every column step.  ldp >= m - j0 for every front of the launch; the
+// launch passes (NB ldp + NB (NB + 1)) elements of dynamic shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_lu_panel_smem(DevFronts F, const int32_t* __restrict__ list, int32_t j0, int32_t ldp,
+                    T* __restrict__ arena, const double* __restrict__ rownorm, double pivot_tol,
+                    long long* __restrict__ err) {
+  // all shared memory is dynamic (panel, then the L11 block), so that the
+  // launch's size is the whole request
+  extern __shared__ unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);
+  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(P + (size_t)NB * ldp);
+  const int32_t f = list[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  if (j0 >= k) return;
+  T* __restrict__ A = arena + F.arena[f];
+  const int64_t row0 = F.row0[f];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int jb = min(NB, k - j0);
+  const int nrows = m - j0;
+  for (int c = warp; c < jb; c += nw)
+    for (int r = lane; r < nrows; r += 32) P[c * ldp + r] = A[(j0 + r) + (int64_t)(j0 + c) * m];
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    T piv = P[j * ldp + j];
+    const double thr = pivot_tol * rownorm[row0 + j0 + j];
+    const bool small = !(fabs((double)piv) > thr);
+    if (small) {
+      const double rep = thr > 0.0 ? thr : 1e-300;
+      piv = (T)((double)piv < 0.0 ? -rep : rep);
+    }
+    __syncthreads();  // every thread has read the pivot before it is replaced
+    if (small && tid == 0) {
+      if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+        err[1] = f;
+        err[2] = row0 + j0 + j;
+      }
+      P[j * ldp + j] = piv;
+    }
+    const T inv = T(1) / piv;
+    for (int r = j + 1 + tid; r < nrows; r += blockDim.x) P[j * ldp + r] *= inv;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < jb; c += nw) {
+      const T u = P[c * ldp + j];
+      for (int r = j + 1 + lane; r < nrows; r += 32) P[c * ldp + r] -= P[j * ldp + r] * u;
+    }
+    __syncthreads();
+  }
+  for (int c = warp; c < jb; c += nw)
+    for (int r = lane; r < nrows; r += 32) A[(j0 + r) + (int64_t)(j0 + c) * m] = P[c * ldp + r];
+  const int t0 = j0 + jb;
+  if (t0 >= m) return;
+  for (int q = warp; q < jb; q += nw)
+    for (int r = lane; r < jb; r += 32) Ls[r][q] = P[q * ldp + r];
+  __syncthreads();
+  for (int c = t0 + tid; c < m; c += blockDim.x) {
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
+#pragma unroll
+    for (int r = 1; r < NB; ++r) {
+      T sacc = x[r];
+#pragma unroll
+      for (int q = 0; q < r; ++q) sacc -= Ls[r][q] * x[q];
+      x[r] = sacc;
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+      if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
+  }
+}
+
 // tile word: front in tile_front, (ti << 16) | tj in tile_ij, rows/cols from t0 = j0 + 32
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -672,10 +747,19 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 }
 
 template <typename T>
-void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, int32_t max_rows,
+                     T* arena, const double* rownorm_new, double pivot_tol, long long* err,
+                     cudaStream_t s) {
   if (nf <= 0) return;
-  k_lu_panel<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
+  const size_t sm = ((size_t)std::max(max_rows, 1) * NB + NB * (NB + 1)) * sizeof(T);
+  if (sm <= 200 * 1024) {  // the panel fits in shared memory
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_lu_panel_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_lu_panel_smem<T><<<nf, kThreads, sm, s>>>(F, list, j0, std::max(max_rows, 1), arena,
+                                                rownorm_new, pivot_tol, err);
+  } else {
+    k_lu_panel<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
+  }
 }
 
 template <typename T>
@@ -745,7 +829,7 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
   template void launch_tri_inverse_mc<T>(DevFronts, const int32_t*, const int32_t*, int32_t,    \
                                          const int32_t*, int32_t, int32_t, T*, T*,              \
                                          const int64_t*, cudaStream_t);                         \
-  template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,            \
+  template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, int32_t, int32_t, T*,   \
                                    const double*, double, long long*, cudaStream_t);            \
   template void launch_lu_trailing<T>(DevFronts, const int32_t*, const int32_t*, int32_t,      \
                                       int32_t, T*, cudaStream_t);

@@ -73,8 +73,9 @@ void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t
                            int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                            T* inv, const int64_t* inv_off, cudaStream_t s);
 template <typename T>
-void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, int32_t max_rows,
+                     T* arena, const double* rownorm_new, double pivot_tol, long long* err,
+                     cudaStream_t s);
 template <typename T>
 void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
                         int32_t ntiles, int32_t j0, T* arena, cudaStream_t s);
