@@ -416,6 +416,9 @@ __global__ void __launch_bounds__(kThreads)
   T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
   T(*Bs)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * IB * (NB + 1));
   T(*Ts)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * (IB * (NB + 1) + NB * (IB + 1)));
+  // the diagonal tile of A, staged once per row tile for the in-tile solve
+  T(*Ds)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(
+      smem_raw + sizeof(T) * (IB * (NB + 1) + NB * (IB + 1) + IB * (IB + 1)));
   const int tr = tid % 16, tc = tid / 16;
   const int ntile_rows = upper ? (min(j0 + IB, k) + IB - 1) / IB : (k - j0 + IB - 1) / IB;
   for (int it = 0; it < ntile_rows; ++it) {
@@ -461,24 +464,28 @@ __global__ void __launch_bounds__(kThreads)
         const int r = tr + 16 * a2, c = tc + 16 * b2;
         Ts[r][c] = ((i0 + r == j0 + c) ? T(1) : T(0)) - acc[a2][b2];
       }
-    __syncthreads();
     const int rows = min(IB, k - i0);
+    for (int t = tid; t < IB * IB; t += blockDim.x) {
+      const int r = t % IB, c = t / IB;
+      Ds[r][c] = (r < rows && c < rows) ? A[(i0 + r) + (int64_t)(i0 + c) * m] : T(0);
+    }
+    __syncthreads();
     if (!upper) {
       for (int r = 0; r < rows; ++r) {  // unit diagonal: row r is final now
         for (int t = tid; t < (rows - r - 1) * IB; t += blockDim.x) {
           const int r2 = r + 1 + t / IB, c = t % IB;
-          Ts[r2][c] -= A[(i0 + r2) + (int64_t)(i0 + r) * m] * Ts[r][c];
+          Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
         }
         __syncthreads();
       }
     } else {
       for (int r = rows - 1; r >= 0; --r) {
-        const T d = A[(i0 + r) + (int64_t)(i0 + r) * m];
+        const T d = Ds[r][r];
         for (int c = tid; c < IB; c += blockDim.x) Ts[r][c] /= d;
         __syncthreads();
         for (int t = tid; t < r * IB; t += blockDim.x) {
           const int r2 = t / IB, c = t % IB;
-          Ts[r2][c] -= A[(i0 + r2) + (int64_t)(i0 + r) * m] * Ts[r][c];
+          Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
         }
         __syncthreads();
       }
@@ -774,7 +781,7 @@ void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t
                            int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                            T* inv, const int64_t* inv_off, cudaStream_t s) {
   if (ntiles <= 0) return;
-  const size_t sm = sizeof(T) * ((size_t)IB * (NB + 1) + (size_t)NB * (IB + 1) + (size_t)IB * (IB + 1));
+  const size_t sm = sizeof(T) * ((size_t)IB * (NB + 1) + (size_t)NB * (IB + 1) + 2 * (size_t)IB * (IB + 1));
   cudaFuncSetAttribute(k_tri_inverse_mc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_tri_inverse_mc<T><<<dim3(ntiles, 2), kThreads, sm, s>>>(F, tile_front, tile_cb, arena, inv,
                                                              inv_off);
