@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kThreads)
   const int32_t f = list[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   T* __restrict__ G = arena + F.arena[f];
-  T* v = A + (int64_t)m * m;  // k scratch entries for the inversion
+  T* v = A + (int64_t)m * m;  // 2 m scratch entries for the inversions
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
   for (int t = tid; t < m * m; t += blockDim.x) A[t] = G[t];
@@ -558,30 +558,40 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
   }
-  // L11^-1 (strictly lower part, unit diagonal), columns descending
-  for (int j = k - 2; j >= 0; --j) {
-    for (int i = j + 1 + tid; i < k; i += blockDim.x) v[i] = A[i + j * m];
-    __syncthreads();
-    for (int i = j + 1 + tid; i < k; i += blockDim.x) {
-      T s2 = v[i];
-      for (int l = j + 1; l < i; ++l) s2 += A[i + l * m] * v[l];
-      A[i + j * m] = -s2;
+  // The two inverses touch disjoint triangles: the first half of the CTA
+  // forms L11^-1, the second U11^-1, each with its own scratch vector and
+  // named barrier.
+  const int half = blockDim.x >> 1;
+  const int gt = tid % half;
+  if (tid < half) {
+    // L11^-1 (strictly lower part, unit diagonal), columns descending
+    for (int j = k - 2; j >= 0; --j) {
+      for (int i = j + 1 + gt; i < k; i += half) v[i] = A[i + j * m];
+      asm volatile("bar.sync 1, %0;" ::"r"(half) : "memory");
+      for (int i = j + 1 + gt; i < k; i += half) {
+        T s2 = v[i];
+        for (int l = j + 1; l < i; ++l) s2 += A[i + l * m] * v[l];
+        A[i + j * m] = -s2;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(half) : "memory");
     }
-    __syncthreads();
-  }
-  // U11^-1 (upper part with the diagonal), columns ascending
-  for (int j = 0; j < k; ++j) {
-    for (int i = tid; i <= j; i += blockDim.x) v[i] = A[i + j * m];
-    __syncthreads();
-    const T d = v[j];
-    for (int i = tid; i < j; i += blockDim.x) {
-      T s2 = T(0);
-      for (int l = i; l < j; ++l) s2 += A[i + l * m] * v[l];
-      A[i + j * m] = -s2 / d;
+  } else {
+    T* vu = v + m;
+    // U11^-1 (upper part with the diagonal), columns ascending
+    for (int j = 0; j < k; ++j) {
+      for (int i = gt; i <= j; i += half) vu[i] = A[i + j * m];
+      asm volatile("bar.sync 2, %0;" ::"r"(half) : "memory");
+      const T d = vu[j];
+      for (int i = gt; i < j; i += half) {
+        T s2 = T(0);
+        for (int l = i; l < j; ++l) s2 += A[i + l * m] * vu[l];
+        A[i + j * m] = -s2 / d;
+      }
+      if (gt == 0) A[j + j * m] = T(1) / d;
+      asm volatile("bar.sync 2, %0;" ::"r"(half) : "memory");
     }
-    if (tid == 0) A[j + j * m] = T(1) / d;
-    __syncthreads();
   }
+  __syncthreads();
   for (int t = tid; t < m * m; t += blockDim.x) G[t] = A[t];
 }
 
@@ -795,7 +805,7 @@ void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t
                            const double* rownorm_new, double pivot_tol, long long* err,
                            cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t sm = ((size_t)max_m * max_m + max_m) * sizeof(T);
+  const size_t sm = ((size_t)max_m * max_m + 2 * (size_t)max_m) * sizeof(T);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_front_lu_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_front_lu_small<T><<<nf, kThreads, sm, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
