@@ -34,8 +34,9 @@ struct Cfg<double> {
 
 // T_f = [X rows of the pivots; 0] + sum over children of their update rows.
 // One CTA per (front, 32*V panel columns); each lane owns V consecutive
-// columns, the 8 warps stride over rows; children are added one after the
-// other (their row maps are injective, so rows of one child never collide).
+// columns, each of the 8 warps takes four rows per step (loads first);
+// children are added one after the other (their row maps are injective, so
+// rows of one child never collide).
 template <typename T>
 struct GatherVec;
 template <>
@@ -67,9 +68,18 @@ __global__ void __launch_bounds__(kThreads)
   T* __restrict__ Tf = Tb + F.idx_off[f] * NR;
   const T* __restrict__ Xf = X + F.row0[f] * NR;
   const V zero = {};
-  for (int i = warp; i < m; i += 8)
-    *reinterpret_cast<V*>(Tf + (int64_t)i * NR + col) =
-        i < k ? *reinterpret_cast<const V*>(Xf + (int64_t)i * NR + col) : zero;
+  // each warp handles four rows per step, all their loads issued first
+  for (int i0 = warp * 4; i0 < m; i0 += 32) {
+    V v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u;
+      v[u] = i < k ? *reinterpret_cast<const V*>(Xf + (int64_t)i * NR + col) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < m) *reinterpret_cast<V*>(Tf + (int64_t)(i0 + u) * NR + col) = v[u];
+  }
   __syncthreads();
   for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
     const int32_t c = F.children[ci];
@@ -77,20 +87,32 @@ __global__ void __launch_bounds__(kThreads)
     const int32_t kc = F.k[c], rc = F.m[c] - kc;
     const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
     const T* __restrict__ Tc = Tb + (F.idx_off[c] + kc) * NR;
-    for (int i = warp; i < rc; i += 8) {
-      V* dst = reinterpret_cast<V*>(Tf + (int64_t)rel[i] * NR + col);
-      const V src = *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col);
-      V d = *dst;
-      if constexpr (VN == 4) {
-        d.x += src.x;
-        d.y += src.y;
-        d.z += src.z;
-        d.w += src.w;
-      } else {
-        d.x += src.x;
-        d.y += src.y;
+    for (int i0 = warp * 4; i0 < rc; i0 += 32) {
+      V src[4], d[4];
+      int32_t row[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        row[u] = i < rc ? rel[i] : 0;
+        if (i < rc) {
+          src[u] = *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col);
+          d[u] = *reinterpret_cast<const V*>(Tf + (int64_t)row[u] * NR + col);
+        }
       }
-      *dst = d;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (i0 + u >= rc) continue;
+        if constexpr (VN == 4) {
+          d[u].x += src[u].x;
+          d[u].y += src[u].y;
+          d[u].z += src[u].z;
+          d[u].w += src[u].w;
+        } else {
+          d[u].x += src[u].x;
+          d[u].y += src[u].y;
+        }
+        *reinterpret_cast<V*>(Tf + (int64_t)row[u] * NR + col) = d[u];
+      }
     }
     __syncthreads();
   }
