@@ -50,7 +50,7 @@ size_t prec_size(int prec) { return prec == DDPS_FP64 ? 8 : (prec == DDPS_FP32 ?
 // Fronts of one depth reordered for the LU launches: `nsmall` fronts that fit
 // the shared-memory kernel, then `nlarge` others, starting at `first`.
 struct LevelSplit {
-  int32_t first = 0, nsmall = 0, nlarge = 0, max_small_m = 0;
+  int32_t first = 0, nsmall = 0, nlarge = 0, max_small_m = 0, max_m = 0;
   // multi-CTA LU of the large fronts: per panel step p (columns 32p..32p+31),
   // fronts [pf_ptr[p], pf_ptr[p+1]) of lu_panel_fronts and tiles
   // [pt_ptr[p], pt_ptr[p+1]) of lu_tile_front / lu_tile_ij
@@ -486,10 +486,10 @@ void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s
   launch_permute_in<T>(y, h->perm, A.n, w, s);
   for (int L = A.nlevels - 1; L >= 0; --L)
     launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   (int32_t)A.max_front, arena, w, u, s);
+                   h->split[L].max_m, arena, w, u, s);
   for (int L = 0; L < A.nlevels; ++L)
     launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   (int32_t)A.max_front, arena, w, s);
+                   h->split[L].max_m, arena, w, s);
   launch_permute_out<T>(w, h->perm, A.n, g, s);
   h->launches += 2 + 2 * A.nlevels;
 }
@@ -1089,6 +1089,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       ls.first = (int32_t)order.size();
       for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
         const int32_t f = A.level_fronts[q];
+        ls.max_m = std::max(ls.max_m, A.f_m[f]);
         if (A.f_m[f] <= small) {
           order.push_back(f);
           ls.nsmall++;
@@ -1803,10 +1804,10 @@ void block_solve_scratch(ddps_handle* h, const double* y, double* g, cudaStream_
   launch_permute_in<T>(y, h->perm, A.n, w, s);
   for (int L = A.nlevels - 1; L >= 0; --L)
     launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   (int32_t)A.max_front, arena, w, u, s);
+                   h->split[L].max_m, arena, w, u, s);
   for (int L = 0; L < A.nlevels; ++L)
     launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   (int32_t)A.max_front, arena, w, s);
+                   h->split[L].max_m, arena, w, s);
   launch_permute_out<T>(w, h->perm, A.n, g, s);
   h->launches += 2 + 2 * A.nlevels;
 }

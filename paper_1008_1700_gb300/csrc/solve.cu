@@ -3,12 +3,15 @@
 // Krylov, Fig. 2 step 6) and with R~, and the reduced product w = G^ v of 6.3.
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "krylov.h"
 #include "launch.h"
 
 namespace ddps {
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -37,41 +40,107 @@ __global__ void k_permute_out(const T* __restrict__ w, const int32_t* __restrict
     g[perm[i]] = (double)w[i];
 }
 
-// Forward substitution for one front per CTA, with the inverse of the unit
-// lower diagonal block formed at factor time.  The front vector t (shared
-// memory) starts with the pivot entries of w and zeros and receives the
-// children's update vectors; then y = L11^-1 t(piv) goes back to w and the
-// update entries t(upd) - L21 y go to u for the parent.
-// sum_{j0 <= j < j1} A[i + j m] x[j] (A column-major with leading dimension
-// m, x in shared memory): eight loads in flight and four partial sums, so
-// that a long row costs a few memory latencies rather than one per term.
-template <typename T>
-__device__ __forceinline__ T dot_row(const T* __restrict__ A, int64_t m, int i, int j0, int j1,
-                                     const T* x) {
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  int j = j0;
-  for (; j + 8 <= j1; j += 8) {
-    T a[8];
+// Products of a front's dense blocks with a vector in shared memory, by the
+// whole CTA of NT threads.  Rows [ra, rb) are taken in chunks of CH; within a
+// chunk the work items are (32-row block, column segment) pairs, at most NSEG
+// segments of at least B columns, spread over the warps: the lanes on
+// consecutive rows (a coalesced read of each column), B loads in flight per
+// lane.  Partial sums go to red[segment][row] (NSEG x CH entries) and are
+// added in a fixed order before fin(i, v) receives row i's value.
+// M(i, j) = A[(roff + i) + (coff + j) m]; TRI 0 takes the columns j < ncols,
+// 1 those j < i, 2 those i <= j < ncols.
+template <typename T, int NT, int CH, int NSEG, int B, int TRI, typename Fin>
+__device__ __forceinline__ void cta_matvec(const T* __restrict__ A, int64_t m, int roff, int coff,
+                                           int ra, int rb, int ncols, const T* x, T* red,
+                                           Fin fin) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nseg = min(NSEG, max(1, (ncols + B - 1) / B));
+  for (int c0 = ra; c0 < rb; c0 += CH) {
+    const int c1 = min(rb, c0 + CH);
+    const int nblk = (c1 - c0 + 31) / 32;
+    for (int it = warp; it < nblk * nseg; it += NT / 32) {
+      const int b = it / nseg, sg = it - b * nseg;
+      const int rbase = c0 + b * 32;
+      const int lo = TRI == 2 ? rbase : 0;
+      const int hi = TRI == 1 ? min(ncols, rbase + 32) : ncols;
+      const int wd = (hi - lo + nseg - 1) / nseg;
+      const int i = rbase + lane;
+      int jb = lo + sg * wd, je = min(hi, jb + wd);
+      if (TRI == 1) je = min(je, i);
+      if (TRI == 2) jb = max(jb, i);
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      if (i < c1) {
+        const T* __restrict__ Ai = A + (roff + i) + (int64_t)coff * m;
+        for (int j = jb; j < je; j += B) {
+          T a[B], xv[B];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = A[i + (int64_t)(j + u) * m];
-    s0 += a[0] * x[j] + a[4] * x[j + 4];
-    s1 += a[1] * x[j + 1] + a[5] * x[j + 5];
-    s2 += a[2] * x[j + 2] + a[6] * x[j + 6];
-    s3 += a[3] * x[j + 3] + a[7] * x[j + 7];
+          for (int q = 0; q < B; ++q) {
+            const bool in = j + q < je;
+            a[q] = in ? Ai[(int64_t)(j + q) * m] : T(0);
+            xv[q] = in ? x[j + q] : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < B; q += 4) {
+            s0 += a[q] * xv[q];
+            s1 += a[q + 1] * xv[q + 1];
+            s2 += a[q + 2] * xv[q + 2];
+            s3 += a[q + 3] * xv[q + 3];
+          }
+        }
+      }
+      red[sg * CH + (rbase - c0) + lane] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    for (int i = c0 + threadIdx.x; i < c1; i += NT) {
+      T v = red[i - c0];
+      for (int sg = 1; sg < nseg; ++sg) v += red[sg * CH + (i - c0)];
+      fin(i, v);
+    }
+    __syncthreads();
   }
-  for (; j < j1; ++j) s0 += A[i + (int64_t)j * m] * x[j];
-  return (s0 + s1) + (s2 + s3);
 }
 
+// Rows [*a, *b) of n taken by CTA `rank` of `nct` (32-row multiples).
+__device__ __forceinline__ void cta_rows(int n, int rank, int nct, int* a, int* b) {
+  const int per = ((n + nct - 1) / nct + 31) / 32 * 32;
+  *a = min(n, rank * per);
+  *b = min(n, *a + per);
+}
+
+// Copies the ranges of v that the cluster's other CTAs computed (cta_rows
+// split of n) from their shared memory into this CTA's copy.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void cluster_gather(T* v, int n) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int nct = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  for (int q = 0; q < nct; ++q) {
+    if (q == me) continue;
+    int a, b;
+    cta_rows(n, q, nct, &a, &b);
+    const T* rv = cl.map_shared_rank(v, q);
+    for (int i = a + (int)threadIdx.x; i < b; i += blockDim.x) v[i] = rv[i];
+  }
+}
+
+// Forward substitution for one front per cluster of CTAs (a cluster of one
+// for levels with many fronts), with the inverse of the unit lower diagonal
+// block formed at factor time.  The front vector t (shared memory, built by
+// every CTA of the cluster) starts with the pivot entries of w and zeros and
+// receives the children's update vectors; then y = L11^-1 t(piv), split by
+// rows over the cluster, goes back to w, and the update entries t(upd) - L21 y
+// go to u for the parent.
+template <typename T, int NT, int CH, int NSEG, int B>
+__global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
     k_fwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
            T* __restrict__ w, T* __restrict__ u) {
   extern __shared__ unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);  // m entries
-  const int32_t f = list[blockIdx.x];
+  T* red = reinterpret_cast<T*>(smem_raw);  // NSEG x CH entries
+  T* t = red + NSEG * CH;                   // m entries
+  cg::cluster_group cl = cg::this_cluster();
+  const int nct = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int32_t f = list[blockIdx.x / nct];
   const int32_t k = F.k[f], m = F.m[f];
-  T* y = t + m;                           // k entries
+  T* y = t + m;                             // k entries
   const T* __restrict__ A = arena + F.arena[f];
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
@@ -85,21 +154,35 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = tid; i < rc; i += blockDim.x) t[rel[i]] += uc[i];
     __syncthreads();
   }
-  for (int i = tid; i < k; i += blockDim.x) y[i] = t[i] + dot_row(A, m, i, 0, i, t);
+  int a, b;
+  cta_rows(k, rank, nct, &a, &b);
+  cta_matvec<T, NT, CH, NSEG, B, 1>(A, m, 0, 0, a, b, k, t, red, [&](int i, T v) { y[i] = t[i] + v; });
+  if (nct > 1) {
+    cl.sync();  // every CTA has read w and written its rows of y
+    cluster_gather(y, k);
+  }
+  for (int i = a + tid; i < b; i += blockDim.x) w[row0 + i] = y[i];
   __syncthreads();
-  for (int i = k + tid; i < m; i += blockDim.x) u[F.upd[f] + (i - k)] = t[i] - dot_row(A, m, i, 0, k, y);
-  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = y[i];
+  T* __restrict__ uf = u + F.upd[f];
+  cta_rows(m - k, rank, nct, &a, &b);
+  cta_matvec<T, NT, CH, NSEG, B, 0>(A, m, k, 0, a, b, k, y, red, [&](int i, T v) { uf[i] = t[k + i] - v; });
+  if (nct > 1) cl.sync();  // keep y alive until the other CTAs have copied it
 }
 
-// Backward substitution for one front per CTA: x_piv = U11^-1 (y_piv - U12 x_upd)
-// with the inverse formed at factor time; x_upd are ancestor pivots of w.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+// Backward substitution for one front per cluster of CTAs:
+// x_piv = U11^-1 (y_piv - U12 x_upd) with the inverse formed at factor time;
+// x_upd are ancestor pivots of w.  Both products are split by rows over the
+// cluster; the CTAs exchange their parts of the intermediate vector.
+template <typename T, int NT, int CH, int NSEG, int B>
+__global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
     k_bwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
            T* __restrict__ w) {
   extern __shared__ unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);
-  const int32_t f = list[blockIdx.x];
+  T* red = reinterpret_cast<T*>(smem_raw);  // NSEG x CH entries
+  T* t = red + NSEG * CH;                   // k entries, then x_upd (r entries)
+  cg::cluster_group cl = cg::this_cluster();
+  const int nct = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int32_t f = list[blockIdx.x / nct];
   const int32_t k = F.k[f], m = F.m[f], r = m - k;
   const T* __restrict__ A = arena + F.arena[f];
   const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
@@ -108,9 +191,16 @@ __global__ void __launch_bounds__(kThreads)
   T* xu = t + k;
   for (int j = tid; j < r; j += blockDim.x) xu[j] = w[idx[k + j]];
   __syncthreads();
-  for (int i = tid; i < k; i += blockDim.x) t[i] = w[row0 + i] - dot_row(A + (int64_t)k * m, m, i, 0, r, xu);
-  __syncthreads();
-  for (int i = tid; i < k; i += blockDim.x) w[row0 + i] = dot_row(A, m, i, i, k, t);
+  int a, b;
+  cta_rows(k, rank, nct, &a, &b);
+  cta_matvec<T, NT, CH, NSEG, B, 0>(A, m, 0, k, a, b, r, xu, red, [&](int i, T v) { t[i] = w[row0 + i] - v; });
+  if (nct > 1) {
+    cl.sync();
+    cluster_gather(t, k);
+    __syncthreads();
+  }
+  cta_matvec<T, NT, CH, NSEG, B, 2>(A, m, 0, 0, a, b, k, t, red, [&](int i, T v) { w[row0 + i] = v; });
+  if (nct > 1) cl.sync();
 }
 
 // y = A x, CSR, four lanes per row.
@@ -374,21 +464,68 @@ void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, c
   k_permute_out<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(w, perm, n, g);
 }
 
+static int sm_count() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  return nsm;
+}
+
+// One launch per depth of the elimination forest, 256 threads per front.
+// Levels with more fronts than two per SM keep eight loads in flight per
+// lane (more CTAs resident); the others take a cluster of up to eight CTAs
+// per front, within two CTAs per SM, and sixteen loads per lane.
+template <typename K, typename... Args>
+static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t s, Args... args) {
+  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nf * c));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)c;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+static bool wide_solve_level(int32_t nf) { return nf > 2 * sm_count(); }
+static int solve_cluster(int32_t nf) {
+  int c = 1;
+  while (c < 8 && (int64_t)nf * c * 2 <= 2 * (int64_t)sm_count()) c *= 2;
+  return c;
+}
+constexpr int kSolveCh = 256;
+constexpr int kSolveRed = 8 * kSolveCh;
+
 template <typename T>
 void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, T* u, cudaStream_t s) {
   if (nf <= 0) return;
-  size_t sm = (size_t)2 * max_m * sizeof(T);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_fwd1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_fwd1<T><<<nf, kThreads, sm, s>>>(F, list, arena, w, u);
+  const size_t sm = ((size_t)2 * max_m + kSolveRed) * sizeof(T);
+  if (wide_solve_level(nf))
+    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w, u);
+  else
+    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf), sm, s, F, list,
+                     arena, w, u);
 }
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, cudaStream_t s) {
   if (nf <= 0) return;
-  size_t sm = (size_t)max_m * sizeof(T);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_bwd1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_bwd1<T><<<nf, kThreads, sm, s>>>(F, list, arena, w);
+  const size_t sm = ((size_t)max_m + kSolveRed) * sizeof(T);
+  if (wide_solve_level(nf))
+    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w);
+  else
+    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf), sm, s, F, list,
+                     arena, w);
 }
 
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
