@@ -65,6 +65,13 @@ typedef enum { DDPS_FP64 = 0, DDPS_FP32 = 1, DDPS_BF16 = 2, DDPS_BF16X3 = 3, DDP
  * dropped when ||R_i(:,k)||_inf <= drop_tol * max_j ||R_i(:,j)||_inf.
  * ABS: an entry r_ij is dropped when |r_ij| < drop_tol. */
 typedef enum { DDPS_DROP_NONE = 0, DDPS_DROP_COLUMN = 1, DDPS_DROP_ABS = 2 } ddps_drop_mode;
+/* How the reduced matrix G^ = I(c,c) + G(c,c) of Fig. 3 step 6.2 is applied.
+ * EXPLICIT: Fig. 2 step 4 forms the spikes and stores G^ as dense arrays per
+ * block (Sec. 3); every inner product streams them.
+ * IMPLICIT: a variant that departs from Fig. 2 step 4: no spikes are formed
+ * and G^ v = v + (D~^-1 (R~ v))(c) is computed with one R~ product and one
+ * block solve (the kernels of 6.1) per inner product. */
+typedef enum { DDPS_GHAT_EXPLICIT = 0, DDPS_GHAT_IMPLICIT = 1 } ddps_ghat_mode;
 
 typedef struct {
   int32_t drop_mode;      /* ddps_drop_mode */
@@ -94,6 +101,7 @@ typedef struct {
                              products of the sweep as one GEMM with a precomputed block
                              (0 = the largest supported, 512; -1 = never, every front takes the
                              two tile products) */
+  int32_t ghat_mode;      /* ddps_ghat_mode; 0 = EXPLICIT is the paper's method */
 } ddps_options;
 
 typedef struct {
@@ -208,7 +216,8 @@ ddps_status ddps_block_solve_noalloc(ddps_handle* h, const double* y, double* g,
  * use it as a feature before the solve starts. */
 ddps_status ddps_reduced_rhs(ddps_handle* h, const double* y, double* ghat, void* stream);
 
-/* Fig. 3 step 6.2 product: w = G^ v = v + G(c,c) v (device float64[m] in/out). */
+/* Fig. 3 step 6.2 product: w = G^ v = v + G(c,c) v (device float64[m] in/out);
+ * with ghat_mode IMPLICIT it is computed as v + (D~^-1 (R~ v))(c). */
 ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream);
 
 /* Fig. 3 in full: z = P^-1 y (device float64[n] in/out).  Runs the inner
@@ -234,7 +243,8 @@ ddps_status ddps_get_ghat_layout(const ddps_handle* h, int32_t b, int64_t* q0, i
 
 /* Copies G(c ∩ block b, c_b) — the off-identity part of block b's rows of
  * G^ — row-major, converted to float64, into host memory dst
- * ((q1-q0) * ncols entries).  Synchronises `stream`. */
+ * ((q1-q0) * ncols entries).  Synchronises `stream`.  DDPS_ERR_STATE when
+ * G^ is implicit (ghat_mode IMPLICIT stores no spikes). */
 ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* stream);
 
 /* Number of kernels this handle has launched since ddps_analyze (host

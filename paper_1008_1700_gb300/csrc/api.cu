@@ -157,6 +157,7 @@ struct ddps_handle {
          *o_s = nullptr, *o_shat = nullptr, *o_t = nullptr, *o_xt = nullptr, *o_tmp = nullptr;
   // preconditioner workspace
   double *pc_g = nullptr, *pc_ghat = nullptr, *pc_zhat = nullptr, *pc_t = nullptr;
+  double *im_q = nullptr, *im_g = nullptr;  // implicit G^: R~ v and D~^-1 R~ v
   // host-buffer entry points stage f and x here
   double *io_f = nullptr, *io_x = nullptr;
   // inner workspace (inner precision, m)
@@ -213,7 +214,7 @@ struct Prof {
   cudaStream_t s;
   cudaEvent_t b = nullptr;
   Prof(ddps_handle* hh, int c, cudaStream_t st) : h(hh), cls(c), s(st) {
-    if (h->prof_mask & (1 << cls)) {
+    if (cls >= 0 && (h->prof_mask & (1 << cls))) {
       cudaEvent_t a = next_event(h);
       b = next_event(h);
       CK(cudaEventRecord(a, s));
@@ -417,7 +418,7 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       }
     }
   }
-  if (m > 0) {
+  if (m > 0 && h->opt.ghat_mode == DDPS_GHAT_EXPLICIT) {
     T* X = (T*)h->X;
     T* Tb = (T*)h->U;
     const int32_t NR = h->NR;
@@ -477,12 +478,12 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
 // Fig. 3 step 6.1 (and the second block solve of the retrieval)
 // ---------------------------------------------------------------------------
 template <typename T>
-void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
+void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s, int prof_cls) {
   const Analysis& A = h->A;
   T* w = (T*)h->w;
   T* u = (T*)h->updv;
   const T* arena = (const T*)h->arena;
-  Prof pr(h, DDPS_PROF_BLOCK_SOLVE, s);
+  Prof pr(h, prof_cls, s);
   launch_permute_in<T>(y, h->perm, A.n, w, s);
   for (int L = A.nlevels - 1; L >= 0; --L)
     launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
@@ -494,16 +495,26 @@ void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s
   h->launches += 2 + 2 * A.nlevels;
 }
 
-void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s) {
+void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s,
+                 int prof_cls = DDPS_PROF_BLOCK_SOLVE) {
   if (h->opt.factor_prec == DDPS_FP64)
-    block_solve_impl<double>(h, y, g, s);
+    block_solve_impl<double>(h, y, g, s, prof_cls);
   else
-    block_solve_impl<float>(h, y, g, s);
+    block_solve_impl<float>(h, y, g, s, prof_cls);
 }
 
 template <typename TG, typename TI>
 void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal* sc = nullptr) {
   Prof pr(h, DDPS_PROF_GHAT_MATVEC, s);
+  if (h->opt.ghat_mode == DDPS_GHAT_IMPLICIT) {
+    // G^ v = v + (D~^-1 R~ v)(c): every system is computed (a stopped
+    // system's output is not read by its masked Krylov updates)
+    launch_rt_apply<TI>(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, v, h->im_q, s);
+    block_solve(h, h->im_q, h->im_g, s, -1);
+    launch_add_gathered<TI>(v, h->im_g, h->c, (int64_t)h->A.c.size(), w, s);
+    h->launches += 2;
+    return;
+  }
   using AT = typename std::conditional<std::is_same<TG, double>::value, double, float>::type;
   if (h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024) {
     // every block owning reduced rows has tiles (a block without coupling
@@ -1060,13 +1071,17 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   }
   h->gcols = dupload(h, A.gcols);
   h->block_ncols = dupload(h, ncols);
-  {
+  const bool implicit = h->opt.ghat_mode == DDPS_GHAT_IMPLICIT;
+  if (!implicit) {
     const int64_t gbytes = std::max<int64_t>(A.ghat_off[A.p], 1) * (int64_t)prec_size(h->opt.ghat_prec);
     h->ghat = dalloc_bytes(h, gbytes);
     CK(cudaMemset(h->ghat, 0, gbytes));  // the row padding stays zero
+  } else {
+    h->im_q = dalloc<double>(h, n);
+    h->im_g = dalloc<double>(h, n);
   }
-  // spike panels: NR right-hand sides per pass
-  if (m > 0) {
+  // spike panels: NR right-hand sides per pass (none when G^ is implicit)
+  if (m > 0 && !implicit) {
     // NR: a multiple of 128 columns (the panel kernels move 128-column groups)
     int64_t nr = h->opt.rhs_chunk > 0 ? h->opt.rhs_chunk : 1024;
     nr = std::min<int64_t>(nr, (A.max_rhs + 127) / 128 * 128);
@@ -1154,7 +1169,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();
     const int sp = h->opt.spike_prec;
-    const bool tcp = (sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0;
+    const bool tcp = (sp == DDPS_BF16 || sp == DDPS_BF16X3) && m > 0 && !implicit;
     const int passes = sp == DDPS_BF16X3 ? 3 : 1;
     const int64_t nfr = (int64_t)A.f_k.size();
     // fronts whose output rows fit one CTA take the fused products
@@ -1321,6 +1336,10 @@ bool valid_options(const ddps_options& o, std::string& why) {
   }
   if (!(o.tol_out > 0) || !(o.tol_in > 0) || o.maxit_out < 1 || o.maxit_in < 1 || o.pivot_tol < 0) {
     why = "tolerances must be positive and iteration caps at least 1";
+    return false;
+  }
+  if (o.ghat_mode != DDPS_GHAT_EXPLICIT && o.ghat_mode != DDPS_GHAT_IMPLICIT) {
+    why = "ghat_mode must be EXPLICIT or IMPLICIT";
     return false;
   }
   if (o.fused_rows < -1) {
@@ -1621,7 +1640,7 @@ ddps_status ddps_get_ghat_layout(const ddps_handle* h, int32_t b, int64_t* q0, i
 
 ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* stream) {
   if (!h || b < 0 || b >= h->A.p || !dst) return DDPS_ERR_INVALID_ARG;
-  if (!h->factored) return DDPS_ERR_STATE;
+  if (!h->factored || h->opt.ghat_mode != DDPS_GHAT_EXPLICIT) return DDPS_ERR_STATE;
   try {
     const Analysis& A = h->A;
     const int64_t rows = A.gq1[b] - A.gq0[b];

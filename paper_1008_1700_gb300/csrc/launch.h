@@ -155,6 +155,14 @@ void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* val
 void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
                         int64_t n, const double* y, const double* zhat, double* out,
                         cudaStream_t s);
+// Implicit G^ product: q = R~ v (reduced columns), then w = v + g(c) with
+// g = D~^-1 q from the block solve.
+template <typename TI>
+void launch_rt_apply(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
+                     int64_t n, const TI* v, double* q, cudaStream_t s);
+template <typename TI>
+void launch_add_gathered(const TI* v, const double* g, const int64_t* c, int64_t m, TI* w,
+                         cudaStream_t s);
 template <typename TG, typename TI>
 void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,
                         const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,

@@ -231,6 +231,28 @@ __global__ void k_rt_residual(const int32_t* __restrict__ rp, const int32_t* __r
   }
 }
 
+// q = R~ v for a reduced vector v (the implicit G^ product)
+template <typename TI>
+__global__ void k_rt_apply(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, int64_t n, const TI* __restrict__ v,
+                           double* __restrict__ q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s += val[e] * (double)v[col[e]];
+    q[i] = s;
+  }
+}
+
+// w = v + g(c)
+template <typename TI>
+__global__ void k_add_gathered(const TI* __restrict__ v, const double* __restrict__ g,
+                               const int64_t* __restrict__ c, int64_t m, TI* __restrict__ w) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x)
+    w[j] = (TI)((double)v[j] + g[c[j]]);
+}
+
 template <typename T>
 __device__ __forceinline__ float to_f(T v) {
   return (float)v;
@@ -539,6 +561,27 @@ void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const d
   k_rt_residual<<<grid_for(n, kThreads), kThreads, 0, s>>>(rt_rowptr, rt_col, rt_val, n, y, zhat,
                                                             out);
 }
+
+template <typename TI>
+void launch_rt_apply(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
+                     int64_t n, const TI* v, double* q, cudaStream_t s) {
+  if (n <= 0) return;
+  k_rt_apply<TI><<<grid_for(n, kThreads), kThreads, 0, s>>>(rt_rowptr, rt_col, rt_val, n, v, q);
+}
+template <typename TI>
+void launch_add_gathered(const TI* v, const double* g, const int64_t* c, int64_t m, TI* w,
+                         cudaStream_t s) {
+  if (m <= 0) return;
+  k_add_gathered<TI><<<grid_for(m, kThreads), kThreads, 0, s>>>(v, g, c, m, w);
+}
+template void launch_rt_apply<float>(const int32_t*, const int32_t*, const double*, int64_t,
+                                     const float*, double*, cudaStream_t);
+template void launch_rt_apply<double>(const int32_t*, const int32_t*, const double*, int64_t,
+                                      const double*, double*, cudaStream_t);
+template void launch_add_gathered<float>(const float*, const double*, const int64_t*, int64_t,
+                                         float*, cudaStream_t);
+template void launch_add_gathered<double>(const double*, const double*, const int64_t*, int64_t,
+                                          double*, cudaStream_t);
 
 template <typename TG, typename TI>
 void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq0,

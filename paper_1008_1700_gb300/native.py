@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libddps.so")
 
 DDPS_FP64, DDPS_FP32, DDPS_BF16, DDPS_BF16X3, DDPS_FP16 = 0, 1, 2, 3, 4
 DDPS_DROP_NONE, DDPS_DROP_COLUMN, DDPS_DROP_ABS = 0, 1, 2
+DDPS_GHAT_EXPLICIT, DDPS_GHAT_IMPLICIT = 0, 1
 STATUS = {0: "DDPS_OK", 1: "DDPS_ERR_INVALID_ARG", 2: "DDPS_ERR_SINGULAR_BLOCK",
           3: "DDPS_ERR_NOT_CONVERGED", 4: "DDPS_ERR_OUT_OF_MEMORY", 5: "DDPS_ERR_CUDA",
           6: "DDPS_ERR_TIMEOUT", 7: "DDPS_ERR_STATE"}
@@ -31,7 +32,8 @@ class ddps_options(C.Structure):
                 ("tol_in", C.c_double), ("maxit_in", C.c_int32),
                 ("pivot_tol", C.c_double), ("leaf_size", C.c_int32),
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
-                ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32)]
+                ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
+                ("ghat_mode", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):

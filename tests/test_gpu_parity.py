@@ -31,6 +31,9 @@ TC1 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16, ghat_prec=N.DDPS_BF1
 TC3_TILES = dict(TC3, fused_rows=-1)
 TC3_MIXED = dict(TC3, fused_rows=24)
 FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mixed": TC3_MIXED}
+# G^ applied without storing it: v + (D~^-1 R~ v)(c) by block solves
+IMPLICIT64 = dict(FP64, ghat_mode=N.DDPS_GHAT_IMPLICIT)
+IMPLICIT = dict(MIXED, ghat_mode=N.DDPS_GHAT_IMPLICIT)
 
 
 def test_worked_example_on_gpu():
@@ -121,10 +124,27 @@ def test_ghat_precision_forms(case, form, bound):
         assert np.max(np.abs(S.ghat_block(b) - ob["Ghat"])) <= bound * scale, (name, b)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "tc3", "tc1"])
+@pytest.mark.parametrize("form,bound", [("implicit64", 1e-12), ("implicit", 1e-5)])
+def test_implicit_reduced_matvec(case, form, bound):
+    """The implicit G^ product (one R~ product and one block solve) against the
+    oracle's stored G^; no spikes are kept, so G^'s blocks cannot be read."""
+    name, P, drop, o = case
+    S = make_solver(P, drop, **{"implicit64": IMPLICIT64, "implicit": IMPLICIT}[form])
+    if not o.m:
+        return
+    for seed in (2, 5):
+        v = np.random.default_rng(seed).standard_normal(o.m)
+        assert relerr(host(S.reduced_matvec(dev(v))), o.reduced_matvec(v)) <= bound, (name, seed)
+    with pytest.raises(N.DDPSError, match="STATE"):
+        S.ghat_block(0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "tc3", "tc1", "implicit64",
+                                  "implicit"])
 def test_full_solve_parity(case, prec):
     name, P, drop, o = case
-    opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "tc3": TC3, "tc1": TC1}[prec]
+    opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "tc3": TC3, "tc1": TC1,
+            "implicit64": IMPLICIT64, "implicit": IMPLICIT}[prec]
     S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **opts)
     x, info = S.solve(dev(P.f))
     assert info["status"] == "DDPS_OK", info
@@ -172,6 +192,28 @@ def test_batched_equals_per_system():
         xo, _ = o.solve(p.f, tol=1e-12, eps_in=1e-8)
         assert relerr(xk, xo) <= 1e-8, k
         assert np.max(np.abs(p.f - o.A @ xk)) / np.max(np.abs(p.f)) <= 1e-12
+
+
+def test_batched_implicit_equals_explicit():
+    """A stacked batch with the implicit G^ converges to the same solutions as
+    the oracle; its inner iteration counts stay within one of the explicit
+    FP32 G^ (the same operator, rounded differently)."""
+    from paper_1008_1700_gb300 import Solver
+    probs = [W.small_convdiff_2d(N, 4, seed=k) for k, N in enumerate([16, 21, 32, 19])]
+    systems = [(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs]
+    f = dev(np.concatenate([p.f for p in probs]))
+    infos = {}
+    for form, opts in (("explicit", MIXED), ("implicit", IMPLICIT)):
+        S = Solver.from_systems(systems, tol_out=1e-12, tol_in=1e-8, **opts)
+        S.factor(dev(S.values_host))
+        x, infos[form] = S.solve(f)
+        assert infos[form]["status"] == "DDPS_OK"
+        x = host(x)
+        for k, p in enumerate(probs):
+            o = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr)
+            xo, _ = o.solve(p.f, tol=1e-12, eps_in=1e-8)
+            assert relerr(x[S.sys_row_ptr[k]:S.sys_row_ptr[k + 1]], xo) <= 1e-8, (form, k)
+    assert abs(infos["explicit"]["first_inner_iters"] - infos["implicit"]["first_inner_iters"]) <= 1
 
 
 def test_singular_block_is_reported():
