@@ -122,6 +122,34 @@ __device__ __forceinline__ void cluster_gather(T* v, int n) {
   }
 }
 
+// Programmatic dependent launch: each level's grid lets the next one start
+// as soon as all of its CTAs have begun; the next grid reads the factors and
+// the front structure (written before the sweep) at once and waits for this
+// grid to finish before it reads w or u.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Brings rows [r0, r1) of columns [c0, c1) of a column-major block (leading
+// dimension m) into L2, one 128-byte line per request.
+template <typename T, int NT>
+__device__ __forceinline__ void prefetch_rows(const T* A, int64_t m, int r0, int r1, int c0,
+                                              int c1) {
+  if (r1 <= r0 || c1 <= c0) return;
+  const int per = (int)(((int64_t)(r1 - r0) * (int64_t)sizeof(T) + 127) / 128) + 1;
+  const int64_t total = (int64_t)(c1 - c0) * per;
+  for (int64_t q = threadIdx.x; q < total; q += NT) {
+    const int64_t j = c0 + q / per;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(A + r0 + j * m) >> 7;
+    const uintptr_t hi = reinterpret_cast<uintptr_t>(A + (r1 - 1) + j * m) >> 7;
+    const uintptr_t line = lo + (uintptr_t)(q % per);
+    if (line <= hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(line << 7));
+  }
+}
+
+constexpr int kMaxChildren = 16;
+
 // Forward substitution for one front per cluster of CTAs (a cluster of one
 // for levels with many fronts), with the inverse of the unit lower diagonal
 // block formed at factor time.  The front vector t (shared memory, built by
@@ -136,6 +164,9 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // NSEG x CH entries
   T* t = red + NSEG * CH;                   // m entries
+  __shared__ int32_t ch_rc[kMaxChildren];
+  __shared__ int64_t ch_rel[kMaxChildren], ch_upd[kMaxChildren];
+  pdl_trigger();
   cg::cluster_group cl = cg::this_cluster();
   const int nct = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int32_t f = list[blockIdx.x / nct];
@@ -144,18 +175,39 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   const T* __restrict__ A = arena + F.arena[f];
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
+  const int32_t cb = F.cbeg[f], nch = F.cend[f] - cb;
+  if (tid < min(nch, kMaxChildren)) {
+    const int32_t c = F.children[cb + tid];
+    ch_rc[tid] = F.m[c] - F.k[c];
+    ch_rel[tid] = F.rel_off[c];
+    ch_upd[tid] = F.upd[c];
+  }
+  int a, b, a2, b2;
+  cta_rows(k, rank, nct, &a, &b);
+  cta_rows(m - k, rank, nct, &a2, &b2);
+  prefetch_rows<T, NT>(A, m, a, b, 0, k);
+  prefetch_rows<T, NT>(A, m, k + a2, k + b2, 0, k);
+  pdl_wait();
   for (int i = tid; i < m; i += blockDim.x) t[i] = i < k ? w[row0 + i] : T(0);
   __syncthreads();
-  for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
-    const int32_t c = F.children[ci];
-    const int32_t rc = F.m[c] - F.k[c];
-    const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
-    const T* __restrict__ uc = u + F.upd[c];
+  for (int32_t q = 0; q < nch; ++q) {
+    int32_t rc;
+    int64_t ro, uo;
+    if (q < kMaxChildren) {
+      rc = ch_rc[q];
+      ro = ch_rel[q];
+      uo = ch_upd[q];
+    } else {
+      const int32_t c = F.children[cb + q];
+      rc = F.m[c] - F.k[c];
+      ro = F.rel_off[c];
+      uo = F.upd[c];
+    }
+    const int32_t* __restrict__ rel = F.rel + ro;
+    const T* __restrict__ uc = u + uo;
     for (int i = tid; i < rc; i += blockDim.x) t[rel[i]] += uc[i];
     __syncthreads();
   }
-  int a, b;
-  cta_rows(k, rank, nct, &a, &b);
   cta_matvec<T, NT, CH, NSEG, B, 1>(A, m, 0, 0, a, b, k, t, red, [&](int i, T v) { y[i] = t[i] + v; });
   if (nct > 1) {
     cl.sync();  // every CTA has read w and written its rows of y
@@ -164,8 +216,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   for (int i = a + tid; i < b; i += blockDim.x) w[row0 + i] = y[i];
   __syncthreads();
   T* __restrict__ uf = u + F.upd[f];
-  cta_rows(m - k, rank, nct, &a, &b);
-  cta_matvec<T, NT, CH, NSEG, B, 0>(A, m, k, 0, a, b, k, y, red, [&](int i, T v) { uf[i] = t[k + i] - v; });
+  cta_matvec<T, NT, CH, NSEG, B, 0>(A, m, k, 0, a2, b2, k, y, red, [&](int i, T v) { uf[i] = t[k + i] - v; });
   if (nct > 1) cl.sync();  // keep y alive until the other CTAs have copied it
 }
 
@@ -180,6 +231,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // NSEG x CH entries
   T* t = red + NSEG * CH;                   // k entries, then x_upd (r entries)
+  pdl_trigger();
   cg::cluster_group cl = cg::this_cluster();
   const int nct = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int32_t f = list[blockIdx.x / nct];
@@ -189,10 +241,14 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
   T* xu = t + k;
-  for (int j = tid; j < r; j += blockDim.x) xu[j] = w[idx[k + j]];
-  __syncthreads();
   int a, b;
   cta_rows(k, rank, nct, &a, &b);
+  const int32_t i0 = tid < r ? idx[k + tid] : 0;
+  prefetch_rows<T, NT>(A, m, a, b, 0, m);
+  pdl_wait();
+  if (tid < r) xu[tid] = w[i0];
+  for (int j = tid + NT; j < r; j += NT) xu[j] = w[idx[k + j]];
+  __syncthreads();
   cta_matvec<T, NT, CH, NSEG, B, 0>(A, m, 0, k, a, b, r, xu, red, [&](int i, T v) { t[i] = w[row0 + i] - v; });
   if (nct > 1) {
     cl.sync();
@@ -509,13 +565,15 @@ static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t 
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = (unsigned)c;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 static bool wide_solve_level(int32_t nf) { return nf > 2 * sm_count(); }
