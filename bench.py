@@ -49,7 +49,10 @@ def parse_args():
     ap.add_argument("--workload", default="cd3d_64_slabs16",
                     choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8", "cd2d_batch256",
                              "randband_1m", "cd3d_48_seq"])
-    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64"], default="mixed")
+    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64", "implicit"], default="mixed",
+                    help="mixed: the paper's method with FP32 factors, tensor-core spikes and "
+                         "FP16 G^; implicit: the variant that applies G^ by block solves "
+                         "instead of forming the spikes")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the plain-FP64 comparison run (0 skips it; default 1, "
                          "0 for randband_1m whose FP64 factor takes over a minute)")
@@ -102,6 +105,10 @@ def form_options(form):
         # accumulation, FP32 inner vectors, FP64 outer
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
                     inner_prec=N.DDPS_FP32)
+    elif form == "implicit":
+        # variant (departs from Fig. 2 step 4): no spikes, G^ v = v + (D~^-1 R~ v)(c)
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
+                    inner_prec=N.DDPS_FP32, ghat_mode=N.DDPS_GHAT_IMPLICIT)
     elif form == "mixed_simt":
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
                     inner_prec=N.DDPS_FP32)
@@ -208,7 +215,12 @@ def algorithmic_work(sizes, P, form, steps, prof):
     # per call of the solve phase
     calls = {k: v[1] for k, v in prof.items()}
     out["block_solve"] = ("bytes", (sizes["factor_lu_entries"] * sf + n * 16) * calls["block_solve"])
-    out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sg + 2 * m * si) * calls["ghat_matvec"])
+    if form == "implicit":
+        # R~ product, one block solve (factors once, permuted in/out) and the gathered add
+        out["ghat_matvec"] = ("bytes", (sizes["nnz_rt"] * 12 + n * 8 + sizes["factor_lu_entries"] * sf +
+                                        n * 16 + m * (2 * si + 8)) * calls["ghat_matvec"])
+    else:
+        out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sg + 2 * m * si) * calls["ghat_matvec"])
     out["spmv"] = ("bytes", (nnz * 12 + (n + 1) * 4 + n * 16) * calls["spmv"])
     return out
 
@@ -451,14 +463,18 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.form == "fp64" else ("bf16x3+f16+f32+f64" if args.form == "mixed" else "f32+f64"),
+        "variant": ("implicit G^: block solves instead of stored spikes (departs from Fig. 2 "
+                    "step 4)" if args.form == "implicit" else None),
         "data": "synthetic",
         "config": {"workload": args.workload, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz,
                    "blocks": P.p,
                    "m_interface": sizes["m"], "ghat_entries": sizes["ghat_entries"],
                    "form": args.form, "parallelism": f"replicas{world}",
-                   "l2": "working set (G^ %.1f GB) larger than L2" %
-                         (sizes["ghat_entries"] * (8 if args.form == "fp64" else
-                                                   (2 if args.form == "mixed" else 4)) / 1e9),
+                   "l2": ("working set (fronts %.2f GB) larger than L2" %
+                          (sizes["factor_entries"] * 4 / 1e9) if args.form == "implicit" else
+                          "working set (G^ %.1f GB) larger than L2" %
+                          (sizes["ghat_entries"] * (8 if args.form == "fp64" else
+                                                    (2 if args.form == "mixed" else 4)) / 1e9)),
                    "tol_out": opts["tol_out"], "tol_in": opts["tol_in"]},
         "analyze_ms": round(analyze_ms, 1),
         "accuracy": {"relres_inf": relres, "rel_err_vs_xtrue": err_xtrue, "converged": converged,
