@@ -100,11 +100,12 @@ def form_options(form):
     from paper_1008_1700_gb300 import native as N
     base = dict(tol_out=1e-10, maxit_out=1000, tol_in=1e-4, maxit_in=100)
     if form == "mixed":
-        # FP32 block factors and spike solves, spike products on the tensor cores
-        # (bf16x3 operands, fp32 accumulation), FP16 G^ storage with FP32
+        # FP32 block factors and spike solves, spike products and the block-LU
+        # updates of large fronts on the tensor cores (bf16x3 operands, fp32
+        # accumulation), FP16 G^ storage with FP32
         # accumulation, FP32 inner vectors, FP64 outer
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
-                    inner_prec=N.DDPS_FP32)
+                    inner_prec=N.DDPS_FP32, update_prec=N.DDPS_BF16X3)
     elif form == "implicit":
         # variant (departs from Fig. 2 step 4): no spikes, G^ v = v + (D~^-1 R~ v)(c)
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,

@@ -55,7 +55,12 @@ struct LevelSplit {
   // fronts [pf_ptr[p], pf_ptr[p+1]) of lu_panel_fronts and tiles
   // [pt_ptr[p], pt_ptr[p+1]) of lu_tile_front / lu_tile_ij
   std::vector<int64_t> pf_ptr, pt_ptr;
-  std::vector<int32_t> pf_rows;  // per panel step: the largest m - j0 of its fronts
+  // tensor-core block updates (update_prec BF16X3): per panel step p, tiles
+  // [pc_ptr[p], pc_ptr[p+1]) of lu_tc_front / lu_tc_ij
+  std::vector<int64_t> pc_ptr;
+  // per panel step p: L21-row / U12-column chunks [pq_ptr[p], pq_ptr[p+1]) of
+  // lu_pc_front / lu_pc_word
+  std::vector<int64_t> pq_ptr;
   int32_t inv_first = 0, inv_ntiles = 0;  // multi-CTA inverse tiles of the large fronts
 };
 
@@ -111,6 +116,9 @@ struct ddps_handle {
   int32_t* lu_order = nullptr;
   std::vector<LevelSplit> split;
   int32_t *lu_panel_fronts = nullptr, *lu_tile_front = nullptr, *lu_tile_ij = nullptr;
+  int32_t *lu_tc_front = nullptr, *lu_tc_ij = nullptr;  // tensor-core block-update tiles
+  int32_t *lu_pc_front = nullptr, *lu_pc_word = nullptr;  // panel row / column chunks
+  bool lu_tc = false;
   int32_t *inv_tile_front = nullptr, *inv_tile_cb = nullptr;
   int64_t* inv_off = nullptr;  // per front, offset of its 2 k^2 inverse entries in inv
   void* inv = nullptr;
@@ -376,13 +384,24 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       for (size_t pstep = 0; pstep + 1 < ls.pf_ptr.size(); ++pstep) {
         const int32_t j0 = (int32_t)pstep * kLuPanel;
         launch_lu_panel<T>(h->F, h->lu_panel_fronts + ls.pf_ptr[pstep],
-                           (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]), j0,
-                           ls.pf_rows[pstep], arena,
+                           (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]),
+                           h->lu_pc_front + ls.pq_ptr[pstep], h->lu_pc_word + ls.pq_ptr[pstep],
+                           (int32_t)(ls.pq_ptr[pstep + 1] - ls.pq_ptr[pstep]), j0, arena,
                            h->rownorm, h->opt.pivot_tol, h->derr, s);
         launch_lu_trailing<T>(h->F, h->lu_tile_front + ls.pt_ptr[pstep],
                               h->lu_tile_ij + ls.pt_ptr[pstep],
-                              (int32_t)(ls.pt_ptr[pstep + 1] - ls.pt_ptr[pstep]), j0, arena, s);
-        h->launches += 2;
+                              (int32_t)(ls.pt_ptr[pstep + 1] - ls.pt_ptr[pstep]), j0,
+                              h->lu_tc ? 1 : 0, arena, s);
+        h->launches += 1 + (ls.pq_ptr[pstep + 1] > ls.pq_ptr[pstep]) +
+                       (ls.pt_ptr[pstep + 1] > ls.pt_ptr[pstep]);
+        if constexpr (std::is_same<T, float>::value) {
+          const int32_t nc = (int32_t)(ls.pc_ptr[pstep + 1] - ls.pc_ptr[pstep]);
+          if (h->lu_tc && nc > 0) {
+            launch_lu_update_tc(h->F, h->lu_tc_front + ls.pc_ptr[pstep], h->lu_tc_ij + ls.pc_ptr[pstep],
+                                nc, j0, arena, h->derr, s);
+            h->launches++;
+          }
+        }
       }
       launch_tri_inverse_mc<T>(h->F, h->inv_tile_front + ls.inv_first, h->inv_tile_cb + ls.inv_first,
                                ls.inv_ntiles, h->lu_order + ls.first + ls.nsmall, ls.nlarge, h->max_k,
@@ -1095,7 +1114,8 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
   {
     const int small = h->opt.factor_prec == DDPS_FP64 ? small_front_max<double>() : small_front_max<float>();
-    std::vector<int32_t> order, pfronts, tfront, tij, ivf, ivc;
+    std::vector<int32_t> order, pfronts, tfront, tij, ivf, ivc, cfront, cij, qfront, qword;
+    h->lu_tc = h->opt.update_prec == DDPS_BF16X3 && h->opt.factor_prec == DDPS_FP32;
     std::vector<int64_t> ioff(A.f_k.size(), 0);
     int64_t inv_total = 0;
     h->split.assign(A.nlevels, LevelSplit{});
@@ -1136,25 +1156,46 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       const int npanel = (kmax + kLuPanel - 1) / kLuPanel;
       ls.pf_ptr.assign(1, (int64_t)pfronts.size());
       ls.pt_ptr.assign(1, (int64_t)tfront.size());
+      ls.pc_ptr.assign(1, (int64_t)cfront.size());
+      ls.pq_ptr.assign(1, (int64_t)qfront.size());
       for (int pstep = 0; pstep < npanel; ++pstep) {
         const int32_t j0 = pstep * kLuPanel;
-        int32_t rows = 0;
         for (int32_t i = ls.first + ls.nsmall; i < (int32_t)order.size(); ++i) {
           const int32_t f = order[i];
           if (A.f_k[f] <= j0) continue;
           pfronts.push_back(f);
-          rows = std::max(rows, A.f_m[f] - j0);
           const int32_t t0 = std::min(j0 + kLuPanel, A.f_k[f]);
+          for (int32_t q = 0; q * 256 < A.f_m[f] - t0; ++q) {
+            qfront.push_back(f);
+            qword.push_back(q);
+            qfront.push_back(f);
+            qword.push_back(q | (1 << 30));
+          }
           const int32_t nt = (A.f_m[f] - t0 + kLuTile - 1) / kLuTile;
+          // blocks of 128 pivots: inside a block the rank-32 updates stop at
+          // the block's rows and columns; the block's last panel step hands the
+          // rest of the front to one tensor-core update
+          const int32_t jend = std::min((j0 & ~(kLuTcBlock - 1)) + kLuTcBlock, A.f_k[f]);
+          if (h->lu_tc && t0 >= jend) {
+            const int32_t nc = (A.f_m[f] - jend + kLuTcTile - 1) / kLuTcTile;
+            for (int32_t ti = 0; ti < nc; ++ti)
+              for (int32_t tj = 0; tj < nc; ++tj) {
+                cfront.push_back(f);
+                cij.push_back((ti << 16) | tj);
+              }
+            continue;
+          }
           for (int32_t ti = 0; ti < nt; ++ti)
             for (int32_t tj = 0; tj < nt; ++tj) {
+              if (h->lu_tc && t0 + ti * kLuTile >= jend && t0 + tj * kLuTile >= jend) continue;
               tfront.push_back(f);
               tij.push_back((ti << 16) | tj);
             }
         }
         ls.pf_ptr.push_back((int64_t)pfronts.size());
         ls.pt_ptr.push_back((int64_t)tfront.size());
-        ls.pf_rows.push_back(rows);
+        ls.pc_ptr.push_back((int64_t)cfront.size());
+        ls.pq_ptr.push_back((int64_t)qfront.size());
       }
     }
     h->lu_order = dupload(h, order);
@@ -1165,6 +1206,10 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->lu_panel_fronts = dupload(h, pfronts);
     h->lu_tile_front = dupload(h, tfront);
     h->lu_tile_ij = dupload(h, tij);
+    h->lu_tc_front = dupload(h, cfront);
+    h->lu_tc_ij = dupload(h, cij);
+    h->lu_pc_front = dupload(h, qfront);
+    h->lu_pc_word = dupload(h, qword);
   }
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();
@@ -1336,6 +1381,14 @@ bool valid_options(const ddps_options& o, std::string& why) {
   }
   if (!(o.tol_out > 0) || !(o.tol_in > 0) || o.maxit_out < 1 || o.maxit_in < 1 || o.pivot_tol < 0) {
     why = "tolerances must be positive and iteration caps at least 1";
+    return false;
+  }
+  if (o.update_prec != DDPS_FP64 && o.update_prec != DDPS_FP32 && o.update_prec != DDPS_BF16X3) {
+    why = "update_prec must be FP64, FP32 or BF16X3";
+    return false;
+  }
+  if (o.update_prec == DDPS_BF16X3 && o.factor_prec != DDPS_FP32) {
+    why = "update_prec BF16X3 needs factor_prec FP32";
     return false;
   }
   if (o.ghat_mode != DDPS_GHAT_EXPLICIT && o.ghat_mode != DDPS_GHAT_IMPLICIT) {

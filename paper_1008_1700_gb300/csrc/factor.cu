@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "launch.h"
 
@@ -199,98 +200,33 @@ __global__ void __launch_bounds__(kThreads)
 
 // ---------------------------------------------------------------------------
 // Large fronts, several CTAs per front: the same blocked right-looking LU as
-// k_front_lu, split into one launch per 32-column panel for the panel and
-// its U12 row panel (one CTA per front) and one launch for the trailing
-// update over 64 x 64 tiles of every front of the depth.
+// k_front_lu, one panel of 32 pivots at a time.  Without pivoting the panel
+// splits into independent parts: the 32 x 32 diagonal block is factored
+// first (k_lu_diag, one CTA per front), then every row below it solves
+// x U11 = a for its L21 row and every column to the right solves
+// L11 x = a for its U12 column (k_lu_panel_rows, CTAs over chunks of 256
+// rows or columns of every front of the depth), then the trailing update
+// (k_lu_trailing, and the tensor-core block update).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_lu_panel(DevFronts F, const int32_t* __restrict__ list, int32_t j0, T* __restrict__ arena,
-               const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
+    k_lu_diag(DevFronts F, const int32_t* __restrict__ list, int32_t j0, T* __restrict__ arena,
+              const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
   const int32_t f = list[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   if (j0 >= k) return;
   T* __restrict__ A = arena + F.arena[f];
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
-  __shared__ T Ls[NB][NB + 1];
   const int jb = min(NB, k - j0);
-  for (int j = j0; j < j0 + jb; ++j) {
-    T piv = A[j + (int64_t)j * m];
-    const double thr = pivot_tol * rownorm[row0 + j];
-    if (!(fabs((double)piv) > thr)) {
-      const double rep = thr > 0.0 ? thr : 1e-300;
-      piv = (T)((double)piv < 0.0 ? -rep : rep);
-      if (tid == 0) {
-        if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
-          err[1] = f;
-          err[2] = row0 + j;
-        }
-        A[j + (int64_t)j * m] = piv;
-      }
-    }
-    const T inv = T(1) / piv;
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
-    __syncthreads();
-    for (int c = j + 1 + (tid >> 5); c < j0 + jb; c += blockDim.x >> 5) {
-      const T u = A[j + (int64_t)c * m];
-      for (int i = j + 1 + (tid & 31); i < m; i += 32)
-        A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * u;
-    }
-    __syncthreads();
-  }
-  const int t0 = j0 + jb;
-  if (t0 >= m) return;
+  __shared__ T D[NB][NB + 1];
   for (int t = tid; t < jb * jb; t += blockDim.x) {
-    const int r = t % jb, q = t / jb;
-    Ls[r][q] = A[j0 + r + (int64_t)(j0 + q) * m];
+    const int r = t % jb, c = t / jb;
+    D[r][c] = A[(j0 + r) + (int64_t)(j0 + c) * m];
   }
-  __syncthreads();
-  for (int c = t0 + tid; c < m; c += blockDim.x) {
-    T x[NB];
-#pragma unroll
-    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
-#pragma unroll
-    for (int r = 1; r < NB; ++r) {
-      T sacc = x[r];
-#pragma unroll
-      for (int q = 0; q < r; ++q) sacc -= Ls[r][q] * x[q];
-      x[r] = sacc;
-    }
-#pragma unroll
-    for (int r = 0; r < NB; ++r)
-      if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
-  }
-}
-
-// The same panel step with the panel (rows j0 .. m-1 of its <= 32 columns,
-// column-major with leading dimension ldp) factored in shared memory: one
-// load and one store of the panel instead of global traffic and latency on
-// every column step.  ldp >= m - j0 for every front of the launch; the
-// launch passes (NB ldp + NB (NB + 1)) elements of dynamic shared memory.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_lu_panel_smem(DevFronts F, const int32_t* __restrict__ list, int32_t j0, int32_t ldp,
-                    T* __restrict__ arena, const double* __restrict__ rownorm, double pivot_tol,
-                    long long* __restrict__ err) {
-  // all shared memory is dynamic (panel, then the L11 block), so that the
-  // launch's size is the whole request
-  extern __shared__ unsigned char smem_raw[];
-  T* P = reinterpret_cast<T*>(smem_raw);
-  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(P + (size_t)NB * ldp);
-  const int32_t f = list[blockIdx.x];
-  const int32_t k = F.k[f], m = F.m[f];
-  if (j0 >= k) return;
-  T* __restrict__ A = arena + F.arena[f];
-  const int64_t row0 = F.row0[f];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int jb = min(NB, k - j0);
-  const int nrows = m - j0;
-  for (int c = warp; c < jb; c += nw)
-    for (int r = lane; r < nrows; r += 32) P[c * ldp + r] = A[(j0 + r) + (int64_t)(j0 + c) * m];
   __syncthreads();
   for (int j = 0; j < jb; ++j) {
-    T piv = P[j * ldp + j];
+    T piv = D[j][j];
     const double thr = pivot_tol * rownorm[row0 + j0 + j];
     const bool small = !(fabs((double)piv) > thr);
     if (small) {
@@ -303,50 +239,92 @@ __global__ void __launch_bounds__(kThreads)
         err[1] = f;
         err[2] = row0 + j0 + j;
       }
-      P[j * ldp + j] = piv;
+      D[j][j] = piv;
     }
     const T inv = T(1) / piv;
-    for (int r = j + 1 + tid; r < nrows; r += blockDim.x) P[j * ldp + r] *= inv;
+    if (tid > j && tid < jb) D[tid][j] *= inv;
     __syncthreads();
-    for (int c = j + 1 + warp; c < jb; c += nw) {
-      const T u = P[c * ldp + j];
-      for (int r = j + 1 + lane; r < nrows; r += 32) P[c * ldp + r] -= P[j * ldp + r] * u;
+    const int w = jb - 1 - j;
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      const int r = j + 1 + t % w, c = j + 1 + t / w;
+      D[r][c] -= D[r][j] * D[j][c];
     }
     __syncthreads();
   }
-  for (int c = warp; c < jb; c += nw)
-    for (int r = lane; r < nrows; r += 32) A[(j0 + r) + (int64_t)(j0 + c) * m] = P[c * ldp + r];
+  for (int t = tid; t < jb * jb; t += blockDim.x) {
+    const int r = t % jb, c = t / jb;
+    A[(j0 + r) + (int64_t)(j0 + c) * m] = D[r][c];
+  }
+}
+
+// chunk word: bit 30 set = columns (U12), else rows (L21); low bits = chunk of 256
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_lu_panel_rows(DevFronts F, const int32_t* __restrict__ chunk_front,
+                    const int32_t* __restrict__ chunk_word, int32_t j0, T* __restrict__ arena) {
+  const int32_t f = chunk_front[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const int jb = min(NB, k - j0);
   const int t0 = j0 + jb;
-  if (t0 >= m) return;
-  for (int q = warp; q < jb; q += nw)
-    for (int r = lane; r < jb; r += 32) Ls[r][q] = P[q * ldp + r];
+  const bool cols = (chunk_word[blockIdx.x] >> 30) & 1;
+  const int q = chunk_word[blockIdx.x] & 0x3fffffff;
+  T* __restrict__ A = arena + F.arena[f];
+  const int tid = threadIdx.x;
+  __shared__ T D[NB][NB + 1];
+  for (int t = tid; t < jb * jb; t += blockDim.x) {
+    const int r = t % jb, c = t / jb;
+    D[r][c] = A[(j0 + r) + (int64_t)(j0 + c) * m];
+  }
   __syncthreads();
-  for (int c = t0 + tid; c < m; c += blockDim.x) {
-    T x[NB];
+  const int i = t0 + q * kThreads + tid;
+  if (i >= m) return;
+  T x[NB];
+  if (!cols) {
+    // L21 row i: x U11 = a (U11 upper, with its diagonal)
 #pragma unroll
-    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
+    for (int c = 0; c < NB; ++c) x[c] = c < jb ? A[i + (int64_t)(j0 + c) * m] : T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+      if (c < jb) {
+        T sacc = x[c];
+#pragma unroll
+        for (int p = 0; p < c; ++p) sacc -= x[p] * D[p][c];
+        x[c] = sacc / D[c][c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c < jb) A[i + (int64_t)(j0 + c) * m] = x[c];
+  } else {
+    // U12 column i: L11 x = a (L11 unit lower)
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[(j0 + r) + (int64_t)i * m] : T(0);
 #pragma unroll
     for (int r = 1; r < NB; ++r) {
       T sacc = x[r];
 #pragma unroll
-      for (int q = 0; q < r; ++q) sacc -= Ls[r][q] * x[q];
+      for (int p = 0; p < r; ++p) sacc -= D[r][p] * x[p];
       x[r] = sacc;
     }
 #pragma unroll
     for (int r = 0; r < NB; ++r)
-      if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
+      if (r < jb) A[(j0 + r) + (int64_t)i * m] = x[r];
   }
 }
 
-// tile word: front in tile_front, (ti << 16) | tj in tile_ij, rows/cols from t0 = j0 + 32
+// tile word: front in tile_front, (ti << 16) | tj in tile_ij, rows/cols from t0 = j0 + 32.
+// blocked: entries with row and column >= skip (the end of the current block
+// of 128 pivots) are left to the block's tensor-core update.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_lu_trailing(DevFronts F, const int32_t* __restrict__ tile_front,
-                  const int32_t* __restrict__ tile_ij, int32_t j0, T* __restrict__ arena) {
+                  const int32_t* __restrict__ tile_ij, int32_t j0, int blocked,
+                  T* __restrict__ arena) {
   const int32_t f = tile_front[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   const int jb = min(NB, k - j0);
   const int t0 = j0 + jb;
+  const int skip = blocked ? min((j0 & ~127) + 128, k) : INT_MAX;
   const int ti = tile_ij[blockIdx.x] >> 16, tj = tile_ij[blockIdx.x] & 0xffff;
   const int rb = t0 + ti * TT, cb = t0 + tj * TT;
   T* __restrict__ A = arena + F.arena[f];
@@ -385,7 +363,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) {
       const int r = rb + tr + 16 * a2;
-      if (r < m) A[r + (int64_t)c * m] -= acc[a2][b2];
+      if (r < m && (r < skip || c < skip)) A[r + (int64_t)c * m] -= acc[a2][b2];
     }
   }
 }
@@ -764,26 +742,20 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 }
 
 template <typename T>
-void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, int32_t max_rows,
-                     T* arena, const double* rownorm_new, double pivot_tol, long long* err,
-                     cudaStream_t s) {
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t* chunk_front,
+                     const int32_t* chunk_word, int32_t nchunks, int32_t j0, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t sm = ((size_t)std::max(max_rows, 1) * NB + NB * (NB + 1)) * sizeof(T);
-  if (sm <= 200 * 1024) {  // the panel fits in shared memory
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_lu_panel_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_lu_panel_smem<T><<<nf, kThreads, sm, s>>>(F, list, j0, std::max(max_rows, 1), arena,
-                                                rownorm_new, pivot_tol, err);
-  } else {
-    k_lu_panel<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
-  }
+  k_lu_diag<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
+  if (nchunks > 0)
+    k_lu_panel_rows<T><<<nchunks, kThreads, 0, s>>>(F, chunk_front, chunk_word, j0, arena);
 }
 
 template <typename T>
 void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
-                        int32_t ntiles, int32_t j0, T* arena, cudaStream_t s) {
+                        int32_t ntiles, int32_t j0, int blocked, T* arena, cudaStream_t s) {
   if (ntiles <= 0) return;
-  k_lu_trailing<T><<<ntiles, kThreads, 0, s>>>(F, tile_front, tile_ij, j0, arena);
+  k_lu_trailing<T><<<ntiles, kThreads, 0, s>>>(F, tile_front, tile_ij, j0, blocked, arena);
 }
 
 template <typename T>
@@ -846,10 +818,11 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
   template void launch_tri_inverse_mc<T>(DevFronts, const int32_t*, const int32_t*, int32_t,    \
                                          const int32_t*, int32_t, int32_t, T*, T*,              \
                                          const int64_t*, cudaStream_t);                         \
-  template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, int32_t, int32_t, T*,   \
+  template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, const int32_t*,          \
+                                   const int32_t*, int32_t, int32_t, T*,                        \
                                    const double*, double, long long*, cudaStream_t);            \
   template void launch_lu_trailing<T>(DevFronts, const int32_t*, const int32_t*, int32_t,      \
-                                      int32_t, T*, cudaStream_t);
+                                      int32_t, int, T*, cudaStream_t);
 
 DDPS_INST_T(double)
 DDPS_INST_T(float)

@@ -72,13 +72,18 @@ template <typename T>
 void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t* tile_cb,
                            int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                            T* inv, const int64_t* inv_off, cudaStream_t s);
+// Panel step j0 of the large fronts in `list`: the diagonal block (one CTA
+// per front), then L21 rows and U12 columns over chunks of 256 (chunk_word
+// bit 30 = columns, low bits = chunk index; rows and columns from j0 + 32).
 template <typename T>
-void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, int32_t j0, int32_t max_rows,
-                     T* arena, const double* rownorm_new, double pivot_tol, long long* err,
-                     cudaStream_t s);
+void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t* chunk_front,
+                     const int32_t* chunk_word, int32_t nchunks, int32_t j0, T* arena,
+                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
+// blocked = 1: the fronts run in blocks of 128 pivots (see launch_lu_update_tc)
+// and the update skips the entries with row and column >= Jend.
 template <typename T>
 void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
-                        int32_t ntiles, int32_t j0, T* arena, cudaStream_t s);
+                        int32_t ntiles, int32_t j0, int blocked, T* arena, cudaStream_t s);
 template <typename T>
 void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                         cudaStream_t s);
@@ -102,6 +107,15 @@ void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int
 // bf16 blocks of 128 rows x tc_tile_bk() K-columns, tc_a_block_bytes(passes)
 // bytes each; tile_aoff[t] is the byte offset of tile t's first block.
 int tc_tile_bk();
+// Block LU update on the tensor cores (fp32 factors, bf16 hi/lo split, fp32
+// accumulation): after the panel step at column j0 that ends a block of 128
+// pivots, A[Jend:m, Jend:m] -= L[Jend:m, J:Jend] U[J:Jend, Jend:m] over
+// 128 x 128 tiles (tile_ij = (ti << 16) | tj from Jend), J = j0 rounded down
+// to 128, Jend = min(J + 128, k).  A wait that runs out writes 2 into err[0].
+constexpr int kLuTcBlock = 128;
+constexpr int kLuTcTile = 128;
+void launch_lu_update_tc(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
+                         int32_t ntiles, int32_t j0, float* arena, long long* err, cudaStream_t s);
 int64_t tc_a_block_bytes(int passes);
 void launch_tc_pack_a(int op, int passes, DevFronts F, const int32_t* tile_front,
                       const int32_t* tile_m0, const int64_t* tile_aoff, int32_t ntiles,

@@ -387,6 +387,155 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
+// Block LU trailing update on the tensor cores.  The multi-CTA LU of a large
+// front runs its 32-column panels in blocks of 128 pivots: within a block the
+// rank-32 updates touch only the block's columns and rows (k_lu_trailing
+// with its mask), and when the block ends, this kernel applies the whole
+// block at once to the rest of the front,
+//   A[Jend:m, Jend:m] -= L[Jend:m, J:Jend] * U[J:Jend, Jend:m],
+// J = j0 rounded down to 128, Jend = min(J + 128, k).  One CTA per 128 x 128
+// tile of the region (tile word (ti << 16) | tj): the 256 threads load the
+// L and U chunks of 32 pivots (fp32, coalesced), split them into bf16 high
+// parts and remainders in the K-major layout, thread 0 issues hi*hi + hi*lo
+// + lo*hi per 16 pivots into a 128 x 128 fp32 accumulator in tensor memory
+// (two stages; the next chunk is loaded into registers meanwhile), and the
+// epilogue subtracts the accumulator from the tile.  Waits are bounded.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_lu_update_tc(DevFronts F, const int32_t* __restrict__ tile_front,
+                   const int32_t* __restrict__ tile_ij, int32_t j0, float* __restrict__ arena,
+                   long long* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t empty[2];
+  __shared__ uint32_t tmem_slot;
+  constexpr uint32_t kAB = 2u * TC_TILE_BYTES;  // one operand, high part then remainder
+  constexpr uint32_t kStageBytes = 2 * kAB;
+  constexpr int kItems = (TC_BM * TC_BK / 8) / TC_THREADS;  // runs of 8 per thread and operand
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int32_t f = tile_front[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const int32_t J = j0 & ~127;
+  const int32_t Jend = min(J + 128, k);
+  const int32_t K = Jend - J;
+  const int32_t i0 = Jend + (tile_ij[blockIdx.x] >> 16) * TC_BM;
+  const int32_t c0 = Jend + (tile_ij[blockIdx.x] & 0xffff) * TC_BN;
+  float* __restrict__ A = arena + F.arena[f];
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"((uint32_t)TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+  bool timed_out = false;
+
+  const int nk = (K + TC_BK - 1) / TC_BK;
+  float areg[kItems][8], breg[kItems][8];
+  auto load = [&](int kt) {
+    const int p0 = J + kt * TC_BK;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const int e = tid + q * TC_THREADS;
+      // L: rows on the lanes, 8 pivots of one row per run
+      const int row = e % TC_BM, kc = e / TC_BM;
+      const int gi = i0 + row;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int p = p0 + kc * 8 + t;
+        areg[q][t] = (gi < m && p < Jend) ? A[gi + (int64_t)p * m] : 0.f;
+      }
+      // U: 8 consecutive pivots (contiguous) of one column per run
+      const int col = e / (TC_BK / 8), kc2 = e % (TC_BK / 8);
+      const int gc = c0 + col;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int p = p0 + kc2 * 8 + t;
+        breg[q][t] = (gc < m && p < Jend) ? A[p + (int64_t)gc * m] : 0.f;
+      }
+    }
+  };
+  if (nk > 0) load(0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    if (kt >= 2 && !timed_out)
+      timed_out = !mbar_wait(smem_u32(&empty[st]), ((kt - 2) >> 1) & 1, err);
+    unsigned char* sA = smem + st * kStageBytes;
+    unsigned char* sB = sA + kAB;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const int e = tid + q * TC_THREADS;
+      const uint32_t offa = chunk_off(e % TC_BM, e / TC_BM);
+      store_split_x2(sA + offa, sA + TC_TILE_BYTES + offa, areg[q], true);
+      const uint32_t offb = chunk_off(e / (TC_BK / 8), e % (TC_BK / 8));
+      store_split_x2(sB + offb, sB + TC_TILE_BYTES + offb, breg[q], true);
+    }
+    if (kt + 1 < nk) load(kt + 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t aS = sbase + st * kStageBytes;
+      const uint32_t aLo = aS + TC_TILE_BYTES;
+      const uint32_t bS = aS + kAB;
+      const uint32_t bLo = bS + TC_TILE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint32_t ko = kk * 256;
+        const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+        mma_bf16(tmem, make_desc(aS + ko, 128, kSBO), make_desc(bS + ko, 128, kSBO), acc0);
+        mma_bf16(tmem, make_desc(aS + ko, 128, kSBO), make_desc(bLo + ko, 128, kSBO), 1u);
+        mma_bf16(tmem, make_desc(aLo + ko, 128, kSBO), make_desc(bS + ko, 128, kSBO), 1u);
+      }
+      mma_commit(smem_u32(&empty[st]));
+    }
+  }
+  if (nk > 0 && !timed_out)
+    timed_out = !mbar_wait(smem_u32(&empty[(nk - 1) & 1]), ((nk - 1) >> 1) & 1, err);
+  if (timed_out && lane == 0) atomicCAS((unsigned long long*)&err[0], 0ull, 2ull);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // epilogue: warp w reads lanes 32*(w%4).. (rows) and columns 64*(w/4)..+64
+  const int quarter = warp & 3, half = warp >> 2;
+  const int gi = i0 + quarter * 32 + lane;
+#pragma unroll
+  for (int c = 0; c < 64; c += 16) {
+    uint32_t rv[16];
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64 + c);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(rv[0]), "=r"(rv[1]), "=r"(rv[2]), "=r"(rv[3]), "=r"(rv[4]), "=r"(rv[5]),
+          "=r"(rv[6]), "=r"(rv[7]), "=r"(rv[8]), "=r"(rv[9]), "=r"(rv[10]), "=r"(rv[11]),
+          "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (gi < m && nk > 0 && !timed_out) {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int gc = c0 + half * 64 + c + t;
+        if (gc < m) A[gi + (int64_t)gc * m] -= __uint_as_float(rv[t]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TC_BN));
+}
+
+// ---------------------------------------------------------------------------
 // Fused front products.  For a front whose output rows fit one CTA, the two
 // products of each sweep are folded into one GEMM over the front's rows:
 //   forward:  [X_piv; dT_upd] = W_f T_piv,        W_f = [L11^-1; -L21 L11^-1]   (m x k)
@@ -1127,6 +1276,14 @@ void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32
 }
 
 int tc_tile_bk() { return TC_BK; }
+
+void launch_lu_update_tc(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
+                         int32_t ntiles, int32_t j0, float* arena, long long* err, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  const size_t sm = 2 * 4 * (size_t)TC_TILE_BYTES;  // two stages of L and U, high and low parts
+  cudaFuncSetAttribute(k_lu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_lu_update_tc<<<ntiles, TC_THREADS, sm, s>>>(F, tile_front, tile_ij, j0, arena, err);
+}
 int64_t tc_a_block_bytes(int passes) { return (passes == 3 ? 2 : 1) * (int64_t)TC_TILE_BYTES; }
 
 void launch_tc_pack_a(int op, int passes, DevFronts F, const int32_t* tile_front,

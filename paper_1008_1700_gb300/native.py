@@ -33,7 +33,7 @@ class ddps_options(C.Structure):
                 ("pivot_tol", C.c_double), ("leaf_size", C.c_int32),
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
                 ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
-                ("ghat_mode", C.c_int32)]
+                ("ghat_mode", C.c_int32), ("update_prec", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):

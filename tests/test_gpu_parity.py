@@ -34,6 +34,9 @@ FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mi
 # G^ applied without storing it: v + (D~^-1 R~ v)(c) by block solves
 IMPLICIT64 = dict(FP64, ghat_mode=N.DDPS_GHAT_IMPLICIT)
 IMPLICIT = dict(MIXED, ghat_mode=N.DDPS_GHAT_IMPLICIT)
+# block LU of large fronts in blocks of 128 pivots, each block's update of the
+# rest of the front on the tensor cores (bf16 high part + remainder)
+TCLU = dict(TC3, update_prec=N.DDPS_BF16X3)
 
 
 def test_worked_example_on_gpu():
@@ -192,6 +195,34 @@ def test_batched_equals_per_system():
         xo, _ = o.solve(p.f, tol=1e-12, eps_in=1e-8)
         assert relerr(xk, xo) <= 1e-8, k
         assert np.max(np.abs(p.f - o.A @ xk)) / np.max(np.abs(p.f)) <= 1e-12
+
+
+LARGE_FRONTS = {
+    # separators of up to 339 pivots (roots) and fronts of up to 428 rows
+    "band_3000_abs": (lambda: W.small_random_band(3000, 5, 200, seed=2), ("abs", 1e-4)),
+    # up to 619 pivots and 1,107 rows: five blocks of 128 pivots per front
+    "band_6000_abs": (lambda: W.small_random_band(6000, 3, 400, seed=4), ("abs", 1e-4)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LARGE_FRONTS))
+def test_lu_tensor_core_block_updates(name):
+    """Block LU with the tensor-core block updates (ragged blocks, tiles and
+    K): the block solve stays within the bf16x3 arithmetic's accuracy of the
+    FP64 oracle (products good to about 2^-16, amplified by the blocks'
+    condition numbers), and the outer FP64 iteration recovers the full
+    solution."""
+    make, drop = LARGE_FRONTS[name]
+    P = make()
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=drop)
+    S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **TCLU)
+    y = np.random.default_rng(4).standard_normal(P.n)
+    assert relerr(host(S.block_solve(dev(y))), o.block_solve(y)) <= 2e-3
+    x, info = S.solve(dev(P.f))
+    assert info["status"] == "DDPS_OK", info
+    xo, _ = o.solve(P.f, tol=1e-12, eps_in=1e-6, maxit_in=200)
+    assert relerr(host(x), xo) <= 1e-8
+    assert np.max(np.abs(P.f - o.A @ host(x))) / np.max(np.abs(P.f)) <= 1e-12
 
 
 def test_batched_implicit_equals_explicit():
