@@ -505,26 +505,38 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (timed_out && lane == 0) atomicCAS((unsigned long long*)&err[0], 0ull, 2ull);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  // epilogue: warp w reads lanes 32*(w%4).. (rows) and columns 64*(w/4)..+64
+  // epilogue: warp w reads lanes 32*(w%4).. (rows) and columns 64*(w/4)..+64;
+  // the thread's entries of C are loaded 16 at a time before any is stored
   const int quarter = warp & 3, half = warp >> 2;
   const int gi = i0 + quarter * 32 + lane;
+  const bool live = gi < m && nk > 0 && !timed_out;
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) {
-    uint32_t rv[16];
-    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64 + c);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(rv[0]), "=r"(rv[1]), "=r"(rv[2]), "=r"(rv[3]), "=r"(rv[4]), "=r"(rv[5]),
-          "=r"(rv[6]), "=r"(rv[7]), "=r"(rv[8]), "=r"(rv[9]), "=r"(rv[10]), "=r"(rv[11]),
-          "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (gi < m && nk > 0 && !timed_out) {
+  for (int cb = 0; cb < 64; cb += 16) {
+    float cv[16];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int gc = c0 + half * 64 + c + t;
-        if (gc < m) A[gi + (int64_t)gc * m] -= __uint_as_float(rv[t]);
+    for (int t = 0; t < 16; ++t) {
+      const int gc = c0 + half * 64 + cb + t;
+      cv[t] = (live && gc < m) ? A[gi + (int64_t)gc * m] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 16; c += 16) {
+      uint32_t rv[16];
+      const uint32_t taddr =
+          tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64 + cb + c);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+          "%11, %12, %13, %14, %15}, [%16];"
+          : "=r"(rv[0]), "=r"(rv[1]), "=r"(rv[2]), "=r"(rv[3]), "=r"(rv[4]), "=r"(rv[5]),
+            "=r"(rv[6]), "=r"(rv[7]), "=r"(rv[8]), "=r"(rv[9]), "=r"(rv[10]), "=r"(rv[11]),
+            "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (live) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int gc = c0 + half * 64 + cb + c + t;
+          if (gc < m) A[gi + (int64_t)gc * m] = cv[c + t] - __uint_as_float(rv[t]);
+        }
       }
     }
   }
