@@ -117,7 +117,8 @@ struct ddps_handle {
   std::vector<LevelSplit> split;
   int32_t *lu_panel_fronts = nullptr, *lu_tile_front = nullptr, *lu_tile_ij = nullptr;
   int32_t *lu_tc_front = nullptr, *lu_tc_ij = nullptr;  // tensor-core block-update tiles
-  int32_t *lu_pc_front = nullptr, *lu_pc_word = nullptr;  // panel row / column chunks
+  int32_t *lu_pc_front = nullptr, *lu_pc_word = nullptr, *lu_pc_slot = nullptr;  // panel chunks
+  void* lu_dinv = nullptr;  // 32 x 32 inverses of the panel's diagonal triangles, per front
   bool lu_tc = false;
   int32_t *inv_tile_front = nullptr, *inv_tile_cb = nullptr;
   int64_t* inv_off = nullptr;  // per front, offset of its 2 k^2 inverse entries in inv
@@ -386,8 +387,9 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
         launch_lu_panel<T>(h->F, h->lu_panel_fronts + ls.pf_ptr[pstep],
                            (int32_t)(ls.pf_ptr[pstep + 1] - ls.pf_ptr[pstep]),
                            h->lu_pc_front + ls.pq_ptr[pstep], h->lu_pc_word + ls.pq_ptr[pstep],
+                           h->lu_pc_slot + ls.pq_ptr[pstep],
                            (int32_t)(ls.pq_ptr[pstep + 1] - ls.pq_ptr[pstep]), j0, arena,
-                           h->rownorm, h->opt.pivot_tol, h->derr, s);
+                           (T*)h->lu_dinv, h->rownorm, h->opt.pivot_tol, h->derr, s);
         launch_lu_trailing<T>(h->F, h->lu_tile_front + ls.pt_ptr[pstep],
                               h->lu_tile_ij + ls.pt_ptr[pstep],
                               (int32_t)(ls.pt_ptr[pstep + 1] - ls.pt_ptr[pstep]), j0,
@@ -1114,7 +1116,8 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
   {
     const int small = h->opt.factor_prec == DDPS_FP64 ? small_front_max<double>() : small_front_max<float>();
-    std::vector<int32_t> order, pfronts, tfront, tij, ivf, ivc, cfront, cij, qfront, qword;
+    std::vector<int32_t> order, pfronts, tfront, tij, ivf, ivc, cfront, cij, qfront, qword, qslot;
+    int64_t max_step_fronts = 0;
     h->lu_tc = h->opt.update_prec == DDPS_BF16X3 && h->opt.factor_prec == DDPS_FP32;
     std::vector<int64_t> ioff(A.f_k.size(), 0);
     int64_t inv_total = 0;
@@ -1163,13 +1166,16 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
         for (int32_t i = ls.first + ls.nsmall; i < (int32_t)order.size(); ++i) {
           const int32_t f = order[i];
           if (A.f_k[f] <= j0) continue;
+          const int32_t slot = (int32_t)(pfronts.size() - ls.pf_ptr.back());
           pfronts.push_back(f);
+          max_step_fronts = std::max<int64_t>(max_step_fronts, slot + 1);
           const int32_t t0 = std::min(j0 + kLuPanel, A.f_k[f]);
           for (int32_t q = 0; q * 256 < A.f_m[f] - t0; ++q) {
-            qfront.push_back(f);
-            qword.push_back(q);
-            qfront.push_back(f);
-            qword.push_back(q | (1 << 30));
+            for (int32_t side = 0; side < 2; ++side) {
+              qfront.push_back(f);
+              qword.push_back(q | (side << 30));
+              qslot.push_back(slot);
+            }
           }
           const int32_t nt = (A.f_m[f] - t0 + kLuTile - 1) / kLuTile;
           // blocks of 128 pivots: inside a block the rank-32 updates stop at
@@ -1210,6 +1216,9 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->lu_tc_ij = dupload(h, cij);
     h->lu_pc_front = dupload(h, qfront);
     h->lu_pc_word = dupload(h, qword);
+    h->lu_pc_slot = dupload(h, qslot);
+    h->lu_dinv = dalloc_bytes(h, std::max<int64_t>(max_step_fronts, 1) * 2 * 32 * 32 *
+                                     (int64_t)prec_size(h->opt.factor_prec));
   }
   {
     const int BM = h->opt.factor_prec == DDPS_FP64 ? spike_tile_m<double>() : spike_tile_m<float>();

@@ -202,16 +202,20 @@ __global__ void __launch_bounds__(kThreads)
 // Large fronts, several CTAs per front: the same blocked right-looking LU as
 // k_front_lu, one panel of 32 pivots at a time.  Without pivoting the panel
 // splits into independent parts: the 32 x 32 diagonal block is factored
-// first (k_lu_diag, one CTA per front), then every row below it solves
-// x U11 = a for its L21 row and every column to the right solves
-// L11 x = a for its U12 column (k_lu_panel_rows, CTAs over chunks of 256
-// rows or columns of every front of the depth), then the trailing update
+// first (k_lu_diag, one CTA per front, which also forms the inverses of its
+// two triangles into a scratch block per front), then every row below it
+// takes its L21 row as a U11^-1 and every column to the right its U12
+// column as L11^-1 a (k_lu_panel_rows, CTAs over chunks of 256 rows or
+// columns of every front of the depth), then the trailing update
 // (k_lu_trailing, and the tensor-core block update).
+// dinv: per entry of the launch's front list, 2 x 32 x 32 entries:
+// U11^-1 (row-major, upper) then L11^-1 (row-major, unit lower).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_lu_diag(DevFronts F, const int32_t* __restrict__ list, int32_t j0, T* __restrict__ arena,
-              const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
+              const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err,
+              T* __restrict__ dinv) {
   const int32_t f = list[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   if (j0 >= k) return;
@@ -220,9 +224,9 @@ __global__ void __launch_bounds__(kThreads)
   const int tid = threadIdx.x;
   const int jb = min(NB, k - j0);
   __shared__ T D[NB][NB + 1];
-  for (int t = tid; t < jb * jb; t += blockDim.x) {
-    const int r = t % jb, c = t / jb;
-    D[r][c] = A[(j0 + r) + (int64_t)(j0 + c) * m];
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    const int r = t % NB, c = t / NB;
+    D[r][c] = (r < jb && c < jb) ? A[(j0 + r) + (int64_t)(j0 + c) * m] : T(r == c ? 1 : 0);
   }
   __syncthreads();
   for (int j = 0; j < jb; ++j) {
@@ -255,13 +259,44 @@ __global__ void __launch_bounds__(kThreads)
     const int r = t % jb, c = t / jb;
     A[(j0 + r) + (int64_t)(j0 + c) * m] = D[r][c];
   }
+  // inverses of the 32 x 32 triangles (identity beyond jb): warp 0 forms
+  // column c of U11^-1 (lane c, backward substitution), warp 1 column c of
+  // L11^-1 (forward substitution)
+  T* Ui = dinv + (int64_t)blockIdx.x * 2 * NB * NB;
+  T* Li = Ui + NB * NB;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    T x[NB];
+#pragma unroll
+    for (int r = NB - 1; r >= 0; --r) {
+      T sacc = r == lane ? T(1) : T(0);
+#pragma unroll
+      for (int p = r + 1; p < NB; ++p) sacc -= D[r][p] * x[p];
+      x[r] = r <= lane ? sacc / D[r][r] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) Ui[r * NB + lane] = x[r];
+  } else if (warp == 1) {
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      T sacc = r == lane ? T(1) : T(0);
+#pragma unroll
+      for (int p = 0; p < r; ++p) sacc -= D[r][p] * x[p];
+      x[r] = r >= lane ? sacc : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r) Li[r * NB + lane] = x[r];
+  }
 }
 
-// chunk word: bit 30 set = columns (U12), else rows (L21); low bits = chunk of 256
+// chunk word: bit 30 set = columns (U12), else rows (L21); bits 0-29 = chunk of
+// 256; chunk_slot: the front's position in the diagonal launch's list (dinv)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_lu_panel_rows(DevFronts F, const int32_t* __restrict__ chunk_front,
-                    const int32_t* __restrict__ chunk_word, int32_t j0, T* __restrict__ arena) {
+                    const int32_t* __restrict__ chunk_word, const int32_t* __restrict__ chunk_slot,
+                    int32_t j0, T* __restrict__ arena, const T* __restrict__ dinv) {
   const int32_t f = chunk_front[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   const int jb = min(NB, k - j0);
@@ -270,45 +305,45 @@ __global__ void __launch_bounds__(kThreads)
   const int q = chunk_word[blockIdx.x] & 0x3fffffff;
   T* __restrict__ A = arena + F.arena[f];
   const int tid = threadIdx.x;
-  __shared__ T D[NB][NB + 1];
-  for (int t = tid; t < jb * jb; t += blockDim.x) {
-    const int r = t % jb, c = t / jb;
-    D[r][c] = A[(j0 + r) + (int64_t)(j0 + c) * m];
-  }
+  __shared__ T Mi[NB][NB + 1];  // U11^-1 (rows) or L11^-1 (columns), row-major
+  const T* src = dinv + (int64_t)chunk_slot[blockIdx.x] * 2 * NB * NB + (cols ? NB * NB : 0);
+  for (int t = tid; t < NB * NB; t += blockDim.x) Mi[t / NB][t % NB] = src[t];
   __syncthreads();
   const int i = t0 + q * kThreads + tid;
   if (i >= m) return;
-  T x[NB];
+  T a[NB];
   if (!cols) {
-    // L21 row i: x U11 = a (U11 upper, with its diagonal)
+    // L21 row i = a U11^-1
 #pragma unroll
-    for (int c = 0; c < NB; ++c) x[c] = c < jb ? A[i + (int64_t)(j0 + c) * m] : T(0);
+    for (int c = 0; c < NB; ++c) a[c] = c < jb ? A[i + (int64_t)(j0 + c) * m] : T(0);
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
       if (c < jb) {
-        T sacc = x[c];
+        T s0 = T(0), s1 = T(0);
 #pragma unroll
-        for (int p = 0; p < c; ++p) sacc -= x[p] * D[p][c];
-        x[c] = sacc / D[c][c];
+        for (int p = 0; p <= c; p += 2) {
+          s0 += a[p] * Mi[p][c];
+          if (p + 1 <= c) s1 += a[p + 1] * Mi[p + 1][c];
+        }
+        A[i + (int64_t)(j0 + c) * m] = s0 + s1;
       }
     }
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c < jb) A[i + (int64_t)(j0 + c) * m] = x[c];
   } else {
-    // U12 column i: L11 x = a (L11 unit lower)
+    // U12 column i = L11^-1 a
 #pragma unroll
-    for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[(j0 + r) + (int64_t)i * m] : T(0);
+    for (int r = 0; r < NB; ++r) a[r] = r < jb ? A[(j0 + r) + (int64_t)i * m] : T(0);
 #pragma unroll
-    for (int r = 1; r < NB; ++r) {
-      T sacc = x[r];
+    for (int r = 0; r < NB; ++r) {
+      if (r < jb) {
+        T s0 = a[r], s1 = T(0);
 #pragma unroll
-      for (int p = 0; p < r; ++p) sacc -= D[r][p] * x[p];
-      x[r] = sacc;
+        for (int p = 0; p < r; p += 2) {
+          s0 += Mi[r][p] * a[p];
+          if (p + 1 < r) s1 += Mi[r][p + 1] * a[p + 1];
+        }
+        A[(j0 + r) + (int64_t)i * m] = s0 + s1;
+      }
     }
-#pragma unroll
-    for (int r = 0; r < NB; ++r)
-      if (r < jb) A[(j0 + r) + (int64_t)i * m] = x[r];
   }
 }
 
@@ -743,12 +778,14 @@ void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const 
 
 template <typename T>
 void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t* chunk_front,
-                     const int32_t* chunk_word, int32_t nchunks, int32_t j0, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
+                     const int32_t* chunk_word, const int32_t* chunk_slot, int32_t nchunks,
+                     int32_t j0, T* arena, T* dinv, const double* rownorm_new, double pivot_tol,
+                     long long* err, cudaStream_t s) {
   if (nf <= 0) return;
-  k_lu_diag<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err);
+  k_lu_diag<T><<<nf, kThreads, 0, s>>>(F, list, j0, arena, rownorm_new, pivot_tol, err, dinv);
   if (nchunks > 0)
-    k_lu_panel_rows<T><<<nchunks, kThreads, 0, s>>>(F, chunk_front, chunk_word, j0, arena);
+    k_lu_panel_rows<T><<<nchunks, kThreads, 0, s>>>(F, chunk_front, chunk_word, chunk_slot, j0,
+                                                    arena, dinv);
 }
 
 template <typename T>
@@ -819,7 +856,7 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
                                          const int32_t*, int32_t, int32_t, T*, T*,              \
                                          const int64_t*, cudaStream_t);                         \
   template void launch_lu_panel<T>(DevFronts, const int32_t*, int32_t, const int32_t*,          \
-                                   const int32_t*, int32_t, int32_t, T*,                        \
+                                   const int32_t*, const int32_t*, int32_t, int32_t, T*, T*,    \
                                    const double*, double, long long*, cudaStream_t);            \
   template void launch_lu_trailing<T>(DevFronts, const int32_t*, const int32_t*, int32_t,      \
                                       int32_t, int, T*, cudaStream_t);

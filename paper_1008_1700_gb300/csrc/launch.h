@@ -72,13 +72,16 @@ template <typename T>
 void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t* tile_cb,
                            int32_t ntiles, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
                            T* inv, const int64_t* inv_off, cudaStream_t s);
-// Panel step j0 of the large fronts in `list`: the diagonal block (one CTA
-// per front), then L21 rows and U12 columns over chunks of 256 (chunk_word
-// bit 30 = columns, low bits = chunk index; rows and columns from j0 + 32).
+// Panel step j0 of the large fronts in `list`: the diagonal block and the
+// inverses of its triangles (one CTA per front; dinv holds 2 x 32 x 32
+// entries per list entry), then L21 rows and U12 columns over chunks of 256
+// (chunk_word bit 30 = columns, low bits = chunk index; rows and columns
+// from j0 + 32; chunk_slot = the front's position in `list`).
 template <typename T>
 void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t* chunk_front,
-                     const int32_t* chunk_word, int32_t nchunks, int32_t j0, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
+                     const int32_t* chunk_word, const int32_t* chunk_slot, int32_t nchunks,
+                     int32_t j0, T* arena, T* dinv, const double* rownorm_new, double pivot_tol,
+                     long long* err, cudaStream_t s);
 // blocked = 1: the fronts run in blocks of 128 pivots (see launch_lu_update_tc)
 // and the update skips the entries with row and column >= Jend.
 template <typename T>

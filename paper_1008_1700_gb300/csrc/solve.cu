@@ -556,7 +556,8 @@ static int sm_count() {
 // One launch per depth of the elimination forest, 256 threads per front.
 // Levels with more fronts than two per SM keep eight loads in flight per
 // lane (more CTAs resident); the others take a cluster of up to eight CTAs
-// per front, within two CTAs per SM, and sixteen loads per lane.
+// per front, within two CTAs per SM (always eight for very large fronts),
+// and sixteen loads per lane.
 template <typename K, typename... Args>
 static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t s, Args... args) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -576,8 +577,14 @@ static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t 
   cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
-static bool wide_solve_level(int32_t nf) { return nf > 2 * sm_count(); }
-static int solve_cluster(int32_t nf) {
+// Fronts of 1024 rows or more always take a full cluster: one CTA cannot
+// stream their blocks fast enough, however many fronts share the depth.
+constexpr int kHugeSolveM = 1024;
+static bool wide_solve_level(int32_t nf, int32_t max_m) {
+  return nf > 2 * sm_count() && max_m < kHugeSolveM;
+}
+static int solve_cluster(int32_t nf, int32_t max_m) {
+  if (max_m >= kHugeSolveM) return 8;
   int c = 1;
   while (c < 8 && (int64_t)nf * c * 2 <= 2 * (int64_t)sm_count()) c *= 2;
   return c;
@@ -590,22 +597,22 @@ void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
                  T* w, T* u, cudaStream_t s) {
   if (nf <= 0) return;
   const size_t sm = ((size_t)2 * max_m + kSolveRed) * sizeof(T);
-  if (wide_solve_level(nf))
+  if (wide_solve_level(nf, max_m))
     launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w, u);
   else
-    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf), sm, s, F, list,
-                     arena, w, u);
+    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf, max_m), sm, s, F,
+                     list, arena, w, u);
 }
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, cudaStream_t s) {
   if (nf <= 0) return;
   const size_t sm = ((size_t)max_m + kSolveRed) * sizeof(T);
-  if (wide_solve_level(nf))
+  if (wide_solve_level(nf, max_m))
     launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w);
   else
-    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf), sm, s, F, list,
-                     arena, w);
+    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf, max_m), sm, s, F,
+                     list, arena, w);
 }
 
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
