@@ -404,14 +404,66 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Triangular inverses of large fronts with many CTAs: CTA (front, column
-// block of 64) computes those columns of L11^-1 (forward substitution over
-// 64-row tiles; the rows already solved enter through a tile GEMM) or of
-// U11^-1 (backward substitution), out of place into `inv` (k x k column-major
-// per front, at inv_off[f]); k_tri_inverse_copy then writes the strictly
-// lower part of L11^-1 and the upper part of U11^-1 back into the front.
+// Triangular inverses of large fronts with many CTAs, out of place into
+// `inv` (k x k column-major per front at inv_off[f]; L11^-1, then U11^-1).
+// The diagonal 64 x 64 tiles of an inverse are the inverses of the diagonal
+// tiles of the triangle: k_tri_inverse_diag forms them first, one CTA per
+// tile.  Then CTA (front, column block of 64) of k_tri_inverse_mc walks its
+// column block away from the diagonal: tile X(i, j) = -D(i)^-1 sum_l A(i, l)
+// X(l, j) over the tiles l already solved, as two tile GEMMs (D(i)^-1 is the
+// diagonal tile of X).  k_tri_inverse_copy then writes the strictly lower
+// part of L11^-1 and the upper part of U11^-1 back into the front.
 // ---------------------------------------------------------------------------
 constexpr int IB = 64;  // columns per CTA and rows per tile
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_tri_inverse_diag(DevFronts F, const int32_t* __restrict__ tile_front,
+                       const int32_t* __restrict__ tile_cb, const T* __restrict__ arena,
+                       T* __restrict__ inv, const int64_t* __restrict__ inv_off) {
+  const int32_t f = tile_front[blockIdx.x];
+  const int32_t k = F.k[f], m = F.m[f];
+  const int i0 = tile_cb[blockIdx.x] * IB;
+  const bool upper = blockIdx.y == 1;
+  const T* __restrict__ A = arena + F.arena[f];
+  T* __restrict__ X = inv + inv_off[f] + (upper ? (int64_t)k * k : 0);
+  const int tid = threadIdx.x;
+  // two 64 x 65 tiles of dynamic shared memory (the triangle's tile, the inverse)
+  extern __shared__ unsigned char smem_raw[];
+  T(*Ds)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw);
+  T(*Ts)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * IB * (IB + 1));
+  const int rows = min(IB, k - i0);
+  for (int t = tid; t < IB * IB; t += blockDim.x) {
+    const int r = t % IB, c = t / IB;
+    Ds[r][c] = (r < rows && c < rows) ? A[(i0 + r) + (int64_t)(i0 + c) * m] : T(0);
+    Ts[r][c] = r == c ? T(1) : T(0);
+  }
+  __syncthreads();
+  if (!upper) {
+    for (int r = 0; r < rows; ++r) {  // unit diagonal: row r is final now
+      for (int t = tid; t < (rows - r - 1) * IB; t += blockDim.x) {
+        const int r2 = r + 1 + t / IB, c = t % IB;
+        Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int r = rows - 1; r >= 0; --r) {
+      const T d = Ds[r][r];
+      for (int c = tid; c < IB; c += blockDim.x) Ts[r][c] /= d;
+      __syncthreads();
+      for (int t = tid; t < r * IB; t += blockDim.x) {
+        const int r2 = t / IB, c = t % IB;
+        Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = tid; t < IB * IB; t += blockDim.x) {
+    const int r = t % IB, c = t / IB;
+    if (r < rows && c < rows) X[(i0 + r) + (int64_t)(i0 + c) * k] = Ts[r][c];
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -429,13 +481,14 @@ __global__ void __launch_bounds__(kThreads)
   T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
   T(*Bs)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * IB * (NB + 1));
   T(*Ts)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(smem_raw + sizeof(T) * (IB * (NB + 1) + NB * (IB + 1)));
-  // the diagonal tile of A, staged once per row tile for the in-tile solve
+  // the diagonal tile of the inverse, D(i)^-1
   T(*Ds)[IB + 1] = reinterpret_cast<T(*)[IB + 1]>(
       smem_raw + sizeof(T) * (IB * (NB + 1) + NB * (IB + 1) + IB * (IB + 1)));
   const int tr = tid % 16, tc = tid / 16;
   const int ntile_rows = upper ? (min(j0 + IB, k) + IB - 1) / IB : (k - j0 + IB - 1) / IB;
-  for (int it = 0; it < ntile_rows; ++it) {
-    // lower: row tiles from j0 downwards; upper: from the diagonal tile upwards
+  // it = 0 is the diagonal tile, formed by k_tri_inverse_diag
+  for (int it = 1; it < ntile_rows; ++it) {
+    // lower: row tiles below j0 downwards; upper: above the diagonal tile upwards
     const int i0 = upper ? ((min(j0 + IB, k) - 1) / IB - it) * IB : j0 + it * IB;
     // acc = sum over the solved rows l of A(i0.., l) X(l, j0..)
     const int l_begin = upper ? i0 + IB : j0;
@@ -469,44 +522,40 @@ __global__ void __launch_bounds__(kThreads)
       }
       __syncthreads();
     }
-    // T = E - acc on the tile, then the triangular solve inside the tile
+    // X(i0, j0) = -D(i0)^-1 acc
+    const int rows = min(IB, k - i0);
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) Ts[tr + 16 * a2][tc + 16 * b2] = -acc[a2][b2];
+    for (int t = tid; t < IB * IB; t += blockDim.x) {
+      const int r = t % IB, c = t / IB;
+      Ds[r][c] = (r < rows && c < rows) ? X[(i0 + r) + (int64_t)(i0 + c) * k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = T(0);
+#pragma unroll 8
+    for (int q = 0; q < IB; ++q) {
+      T lv[4], uv[4];
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) lv[a2] = Ds[tr + 16 * a2][q];
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) uv[b2] = Ts[q][tc + 16 * b2];
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] += lv[a2] * uv[b2];
+    }
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
       for (int b2 = 0; b2 < 4; ++b2) {
         const int r = tr + 16 * a2, c = tc + 16 * b2;
-        Ts[r][c] = ((i0 + r == j0 + c) ? T(1) : T(0)) - acc[a2][b2];
+        if (r < rows && j0 + c < k) X[(i0 + r) + (int64_t)(j0 + c) * k] = acc[a2][b2];
       }
-    const int rows = min(IB, k - i0);
-    for (int t = tid; t < IB * IB; t += blockDim.x) {
-      const int r = t % IB, c = t / IB;
-      Ds[r][c] = (r < rows && c < rows) ? A[(i0 + r) + (int64_t)(i0 + c) * m] : T(0);
-    }
-    __syncthreads();
-    if (!upper) {
-      for (int r = 0; r < rows; ++r) {  // unit diagonal: row r is final now
-        for (int t = tid; t < (rows - r - 1) * IB; t += blockDim.x) {
-          const int r2 = r + 1 + t / IB, c = t % IB;
-          Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
-        }
-        __syncthreads();
-      }
-    } else {
-      for (int r = rows - 1; r >= 0; --r) {
-        const T d = Ds[r][r];
-        for (int c = tid; c < IB; c += blockDim.x) Ts[r][c] /= d;
-        __syncthreads();
-        for (int t = tid; t < r * IB; t += blockDim.x) {
-          const int r2 = t / IB, c = t % IB;
-          Ts[r2][c] -= Ds[r2][r] * Ts[r][c];
-        }
-        __syncthreads();
-      }
-    }
-    for (int t = tid; t < IB * IB; t += blockDim.x) {
-      const int r = t % IB, c = t / IB;
-      if (r < rows && j0 + c < k) X[(i0 + r) + (int64_t)(j0 + c) * k] = Ts[r][c];
-    }
     __syncthreads();
   }
 }
@@ -802,6 +851,10 @@ void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t
   if (ntiles <= 0) return;
   const size_t sm = sizeof(T) * ((size_t)IB * (NB + 1) + (size_t)NB * (IB + 1) + 2 * (size_t)IB * (IB + 1));
   cudaFuncSetAttribute(k_tri_inverse_mc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t smd = sizeof(T) * 2 * (size_t)IB * (IB + 1);
+  cudaFuncSetAttribute(k_tri_inverse_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+  k_tri_inverse_diag<T><<<dim3(ntiles, 2), kThreads, smd, s>>>(F, tile_front, tile_cb, arena, inv,
+                                                                inv_off);
   k_tri_inverse_mc<T><<<dim3(ntiles, 2), kThreads, sm, s>>>(F, tile_front, tile_cb, arena, inv,
                                                              inv_off);
   const int64_t per = (int64_t)max_k * max_k;
