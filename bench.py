@@ -437,12 +437,14 @@ def run_ours(args):
         peak = peaks["hbm_gbs"]
         bound = "hbm"
         peak_note = f"{peaks['source']} HBM copy bandwidth"
-    elif args.form == "mixed" and dom in ("spike_fwd", "spike_bwd"):
+    elif args.form == "mixed" and dom in ("spike_fwd", "spike_bwd", "front_lu"):
         # bf16 tensor-core products (3 passes per algorithmic product): sustained bf16 peak
         peak = peaks["bf16_tflops_sustained"]
         bound = "tensor"
         peak_note = (f"{peaks['source']} sustained dense bf16 (cuBLAS); achieved counts the "
-                     "algorithmic flops once, the tensor cores run 3 bf16 passes")
+                     "algorithmic flops once, the tensor cores run 3 bf16 passes" +
+                     ("; the LU's block updates run there, its panels and triangular "
+                      "inverses on the SIMT cores" if dom == "front_lu" else ""))
     else:
         # FP32 (mixed) or FP64 (plain) SIMT: 152 SMs x lanes x 2 flops x max SM clock
         lanes = 2 if args.form == "fp64" else 128
