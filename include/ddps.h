@@ -104,7 +104,7 @@ typedef struct {
   int32_t ghat_mode;      /* ddps_ghat_mode; 0 = EXPLICIT is the paper's method */
   int32_t update_prec;    /* dense trailing updates of the block LU of large fronts (Fig. 2
                              step 2): FP64 or FP32 = SIMT in factor_prec (either value);
-                             BF16X3 = with FP32 factors, blocks of 128 pivots whose update of
+                             BF16X3 = with FP32 factors, blocks of 256 pivots whose update of
                              the rest of the front runs on the tensor cores (bf16 high part and
                              remainder, fp32 accumulation, about 16 correct bits per product) */
 } ddps_options;

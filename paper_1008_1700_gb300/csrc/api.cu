@@ -1178,7 +1178,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
             }
           }
           const int32_t nt = (A.f_m[f] - t0 + kLuTile - 1) / kLuTile;
-          // blocks of 128 pivots: inside a block the rank-32 updates stop at
+          // blocks of kLuTcBlock (256) pivots: inside a block the rank-32 updates stop at
           // the block's rows and columns; the block's last panel step hands the
           // rest of the front to one tensor-core update
           const int32_t jend = std::min((j0 & ~(kLuTcBlock - 1)) + kLuTcBlock, A.f_k[f]);

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // tile word: front in tile_front, (ti << 16) | tj in tile_ij, rows/cols from t0 = j0 + 32.
 // blocked: entries with row and column >= skip (the end of the current block
-// of 128 pivots) are left to the block's tensor-core update.
+// of 256 pivots) are left to the block's tensor-core update.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_lu_trailing(DevFronts F, const int32_t* __restrict__ tile_front,
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kThreads)
   const int32_t k = F.k[f], m = F.m[f];
   const int jb = min(NB, k - j0);
   const int t0 = j0 + jb;
-  const int skip = blocked ? min((j0 & ~127) + 128, k) : INT_MAX;
+  const int skip = blocked ? min((j0 & ~(kLuTcBlock - 1)) + kLuTcBlock, k) : INT_MAX;
   const int ti = tile_ij[blockIdx.x] >> 16, tj = tile_ij[blockIdx.x] & 0xffff;
   const int rb = t0 + ti * TT, cb = t0 + tj * TT;
   T* __restrict__ A = arena + F.arena[f];

@@ -82,7 +82,7 @@ void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t
                      const int32_t* chunk_word, const int32_t* chunk_slot, int32_t nchunks,
                      int32_t j0, T* arena, T* dinv, const double* rownorm_new, double pivot_tol,
                      long long* err, cudaStream_t s);
-// blocked = 1: the fronts run in blocks of 128 pivots (see launch_lu_update_tc)
+// blocked = 1: the fronts run in blocks of 256 pivots (see launch_lu_update_tc)
 // and the update skips the entries with row and column >= Jend.
 template <typename T>
 void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
@@ -111,11 +111,11 @@ void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int
 // bytes each; tile_aoff[t] is the byte offset of tile t's first block.
 int tc_tile_bk();
 // Block LU update on the tensor cores (fp32 factors, bf16 hi/lo split, fp32
-// accumulation): after the panel step at column j0 that ends a block of 128
+// accumulation): after the panel step at column j0 that ends a block of 256
 // pivots, A[Jend:m, Jend:m] -= L[Jend:m, J:Jend] U[J:Jend, Jend:m] over
 // 128 x 128 tiles (tile_ij = (ti << 16) | tj from Jend), J = j0 rounded down
-// to 128, Jend = min(J + 128, k).  A wait that runs out writes 2 into err[0].
-constexpr int kLuTcBlock = 128;
+// to 256, Jend = min(J + 256, k).  A wait that runs out writes 2 into err[0].
+constexpr int kLuTcBlock = 256;
 constexpr int kLuTcTile = 128;
 void launch_lu_update_tc(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
                          int32_t ntiles, int32_t j0, float* arena, long long* err, cudaStream_t s);

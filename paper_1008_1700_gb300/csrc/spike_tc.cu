@@ -388,12 +388,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 
 // ---------------------------------------------------------------------------
 // Block LU trailing update on the tensor cores.  The multi-CTA LU of a large
-// front runs its 32-column panels in blocks of 128 pivots: within a block the
+// front runs its 32-column panels in blocks of 256 pivots: within a block the
 // rank-32 updates touch only the block's columns and rows (k_lu_trailing
 // with its mask), and when the block ends, this kernel applies the whole
 // block at once to the rest of the front,
 //   A[Jend:m, Jend:m] -= L[Jend:m, J:Jend] * U[J:Jend, Jend:m],
-// J = j0 rounded down to 128, Jend = min(J + 128, k).  One CTA per 128 x 128
+// J = j0 rounded down to 256, Jend = min(J + 256, k).  One CTA per 128 x 128
 // tile of the region (tile word (ti << 16) | tj): the 256 threads load the
 // L and U chunks of 32 pivots (fp32, coalesced), split them into bf16 high
 // parts and remainders in the K-major layout, thread 0 issues hi*hi + hi*lo
@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int32_t f = tile_front[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
-  const int32_t J = j0 & ~127;
-  const int32_t Jend = min(J + 128, k);
+  const int32_t J = j0 & ~(kLuTcBlock - 1);
+  const int32_t Jend = min(J + kLuTcBlock, k);
   const int32_t K = Jend - J;
   const int32_t i0 = Jend + (tile_ij[blockIdx.x] >> 16) * TC_BM;
   const int32_t c0 = Jend + (tile_ij[blockIdx.x] & 0xffff) * TC_BN;

@@ -34,7 +34,7 @@ FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mi
 # G^ applied without storing it: v + (D~^-1 R~ v)(c) by block solves
 IMPLICIT64 = dict(FP64, ghat_mode=N.DDPS_GHAT_IMPLICIT)
 IMPLICIT = dict(MIXED, ghat_mode=N.DDPS_GHAT_IMPLICIT)
-# block LU of large fronts in blocks of 128 pivots, each block's update of the
+# block LU of large fronts in blocks of 256 pivots, each block's update of the
 # rest of the front on the tensor cores (bf16 high part + remainder)
 TCLU = dict(TC3, update_prec=N.DDPS_BF16X3)
 
@@ -200,7 +200,7 @@ def test_batched_equals_per_system():
 LARGE_FRONTS = {
     # separators of up to 339 pivots (roots) and fronts of up to 428 rows
     "band_3000_abs": (lambda: W.small_random_band(3000, 5, 200, seed=2), ("abs", 1e-4)),
-    # up to 619 pivots and 1,107 rows: five blocks of 128 pivots per front
+    # up to 619 pivots and 1,107 rows: three blocks of 256 pivots per front
     "band_6000_abs": (lambda: W.small_random_band(6000, 3, 400, seed=4), ("abs", 1e-4)),
 }
 
