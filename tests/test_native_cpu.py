@@ -81,3 +81,16 @@ def test_stack_systems_and_cross_system_entries():
     ci2[rp[0]:rp[1]] = np.sort(ci2[rp[0]:rp[1]])
     with pytest.raises(N.DDPSError, match="couples two systems"):
         N.ddps_symbolic(rp, ci2, bp, sbp)
+
+
+def test_analyze_rejects_bad_options_before_any_device_work():
+    """Option checks run before the analysis touches the device, so they hold
+    on a machine without a GPU."""
+    P = W.small_random_dd(40, 2, seed=1)
+    bad = [dict(update_prec=N.DDPS_BF16X3),  # tensor-core updates need FP32 factors
+           dict(factor_prec=N.DDPS_FP32, update_prec=N.DDPS_BF16),
+           dict(ghat_mode=2),
+           dict(fused_rows=-2)]
+    for kw in bad:
+        with pytest.raises(N.DDPSError, match="INVALID_ARG"):
+            N.ddps_analyze(P.rowptr, P.colind, P.block_ptr, options=N.default_options(**kw))
