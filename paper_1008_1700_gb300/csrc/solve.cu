@@ -259,6 +259,101 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   if (nct > 1) cl.sync();
 }
 
+// The same two sweeps with one warp per front (eight fronts per CTA), for
+// depths of many small fronts: the lanes take consecutive rows (coalesced
+// column reads), each lane runs its rows' dot products with eight loads in
+// flight, and the front vector lives in the warp's slice of shared memory
+// (ldt entries).  Only warp-level synchronisation after the dependent wait.
+template <typename T>
+__device__ __forceinline__ T warp_row_dot(const T* __restrict__ Ai, int64_t m, int jb, int je,
+                                          const T* x) {
+  T s0 = T(0), s1 = T(0);
+  for (int j = jb; j < je; j += 8) {
+    T a[8], xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool in = j + q < je;
+      a[q] = in ? Ai[(int64_t)(j + q) * m] : T(0);
+      xv[q] = in ? x[j + q] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      s0 += a[q] * xv[q];
+      s1 += a[q + 1] * xv[q + 1];
+    }
+  }
+  return s0 + s1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd1w(DevFronts F, const int32_t* __restrict__ list, int32_t nf, int32_t ldt,
+            const T* __restrict__ arena, T* __restrict__ w, T* __restrict__ u) {
+  extern __shared__ unsigned char smem_raw[];
+  pdl_trigger();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (kThreads / 32) + warp;
+  T* t = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * ldt;  // m entries, then y (k)
+  const bool live = q < nf;
+  int32_t f = 0, k = 0, m = 0;
+  if (live) {
+    f = list[q];
+    k = F.k[f];
+    m = F.m[f];
+  }
+  pdl_wait();
+  if (!live) return;
+  const T* __restrict__ A = arena + F.arena[f];
+  const int64_t row0 = F.row0[f];
+  T* y = t + m;
+  for (int i = lane; i < m; i += 32) t[i] = i < k ? w[row0 + i] : T(0);
+  __syncwarp();
+  for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
+    const int32_t c = F.children[ci];
+    const int32_t rc = F.m[c] - F.k[c];
+    const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
+    const T* __restrict__ uc = u + F.upd[c];
+    for (int i = lane; i < rc; i += 32) t[rel[i]] += uc[i];
+    __syncwarp();
+  }
+  for (int i = lane; i < k; i += 32) y[i] = t[i] + warp_row_dot(A + i, m, 0, i, t);
+  __syncwarp();
+  T* __restrict__ uf = u + F.upd[f];
+  for (int i = lane; i < m - k; i += 32) uf[i] = t[k + i] - warp_row_dot(A + k + i, m, 0, k, y);
+  for (int i = lane; i < k; i += 32) w[row0 + i] = y[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_bwd1w(DevFronts F, const int32_t* __restrict__ list, int32_t nf, int32_t ldt,
+            const T* __restrict__ arena, T* __restrict__ w) {
+  extern __shared__ unsigned char smem_raw[];
+  pdl_trigger();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (kThreads / 32) + warp;
+  T* t = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * ldt;  // k entries, then x_upd (r)
+  const bool live = q < nf;
+  int32_t f = 0, k = 0, m = 0;
+  if (live) {
+    f = list[q];
+    k = F.k[f];
+    m = F.m[f];
+  }
+  pdl_wait();
+  if (!live) return;
+  const int32_t r = m - k;
+  const T* __restrict__ A = arena + F.arena[f];
+  const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
+  const int64_t row0 = F.row0[f];
+  T* xu = t + k;
+  for (int j = lane; j < r; j += 32) xu[j] = w[idx[k + j]];
+  __syncwarp();
+  for (int i = lane; i < k; i += 32)
+    t[i] = w[row0 + i] - warp_row_dot(A + i + (int64_t)k * m, m, 0, r, xu);
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) w[row0 + i] = warp_row_dot(A + i, m, i, k, t);
+}
+
 // y = A x, CSR, four lanes per row.
 __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                        const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
@@ -592,10 +687,23 @@ static int solve_cluster(int32_t nf, int32_t max_m) {
 constexpr int kSolveCh = 256;
 constexpr int kSolveRed = 8 * kSolveCh;
 
+// Depths of many fronts of at most kWarpSolveM rows take a warp per front.
+constexpr int kWarpSolveM = 128;
+static bool warp_solve_level(int32_t nf, int32_t max_m) {
+  return max_m <= kWarpSolveM && nf > 2 * sm_count();
+}
+
 template <typename T>
 void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, T* u, cudaStream_t s) {
   if (nf <= 0) return;
+  if (warp_solve_level(nf, max_m)) {
+    const int32_t ldt = 2 * max_m;
+    const size_t smw = (size_t)(kThreads / 32) * ldt * sizeof(T);
+    const int32_t grid = (nf + kThreads / 32 - 1) / (kThreads / 32);
+    launch_clustered(k_fwd1w<T>, grid, 1, smw, s, F, list, nf, ldt, arena, w, u);
+    return;
+  }
   const size_t sm = ((size_t)2 * max_m + kSolveRed) * sizeof(T);
   if (wide_solve_level(nf, max_m))
     launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w, u);
@@ -607,6 +715,13 @@ template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, cudaStream_t s) {
   if (nf <= 0) return;
+  if (warp_solve_level(nf, max_m)) {
+    const int32_t ldt = max_m;
+    const size_t smw = (size_t)(kThreads / 32) * ldt * sizeof(T);
+    const int32_t grid = (nf + kThreads / 32 - 1) / (kThreads / 32);
+    launch_clustered(k_bwd1w<T>, grid, 1, smw, s, F, list, nf, ldt, arena, w);
+    return;
+  }
   const size_t sm = ((size_t)max_m + kSolveRed) * sizeof(T);
   if (wide_solve_level(nf, max_m))
     launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w);

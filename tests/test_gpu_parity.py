@@ -225,6 +225,23 @@ def test_lu_tensor_core_block_updates(name):
     assert np.max(np.abs(P.f - o.A @ host(x))) / np.max(np.abs(P.f)) <= 1e-12
 
 
+@pytest.mark.parametrize("opts", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_block_solve_of_a_wide_batch(opts):
+    """A batch whose depths hold more fronts than two per SM: the block solve
+    takes one warp per front there; it matches the oracle system by system."""
+    from paper_1008_1700_gb300 import Solver
+    probs = [W.small_convdiff_2d(24, 8, seed=50 + k) for k in range(48)]
+    S = Solver.from_systems([(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs], **opts)
+    S.factor(dev(S.values_host))
+    y = np.random.default_rng(8).standard_normal(S.n)
+    g = host(S.block_solve(dev(y)))
+    bound = 1e-12 if opts is FP64 else 1e-5
+    for k, p in enumerate(probs):
+        a, b = S.sys_row_ptr[k], S.sys_row_ptr[k + 1]
+        o = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr, spikes=False)
+        assert relerr(g[a:b], o.block_solve(y[a:b])) <= bound, k
+
+
 def test_batched_implicit_equals_explicit():
     """A stacked batch with the implicit G^ converges to the same solutions as
     the oracle; its inner iteration counts stay within one of the explicit
