@@ -83,124 +83,15 @@ __global__ void k_extend_add_p(DevFronts F, const int32_t* __restrict__ parent,
 // ---------------------------------------------------------------------------
 // Partial LU of a front (no pivoting): the first k columns/rows become
 // L11\U11, L21 and U12; the trailing r x r block becomes the Schur complement
-// passed to the parent.  One CTA per front; blocked right-looking with panel
-// width NB and 64 x 64 shared-memory tiles for the trailing update.
+// passed to the parent.  Blocked right-looking with panels of NB pivots and
+// TT x TT tiles for the trailing update.
 // ---------------------------------------------------------------------------
 constexpr int NB = 32;
 constexpr int TT = 64;
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_front_lu(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena,
-               const double* __restrict__ rownorm, double pivot_tol, long long* __restrict__ err) {
-  const int32_t f = list[blockIdx.x];
-  const int32_t k = F.k[f], m = F.m[f];
-  T* __restrict__ A = arena + F.arena[f];
-  const int64_t row0 = F.row0[f];
-  const int tid = threadIdx.x;
-  __shared__ T Ls[NB][NB + 1];
-  __shared__ T Lt[TT][NB + 1];
-  __shared__ T Ut[NB][TT + 1];
-  for (int j0 = 0; j0 < k; j0 += NB) {
-    const int jb = min(NB, k - j0);
-    // (1) panel j0 .. j0+jb-1 over all rows below the diagonal
-    for (int j = j0; j < j0 + jb; ++j) {
-      T piv = A[j + (int64_t)j * m];
-      const double thr = pivot_tol * rownorm[row0 + j];
-      if (!(fabs((double)piv) > thr)) {
-        const double rep = thr > 0.0 ? thr : 1e-300;
-        piv = (T)((double)piv < 0.0 ? -rep : rep);
-        if (tid == 0) {
-          if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
-            err[1] = f;
-            err[2] = row0 + j;
-          }
-          A[j + (int64_t)j * m] = piv;
-        }
-      }
-      const T inv = T(1) / piv;
-      for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + (int64_t)j * m] *= inv;
-      __syncthreads();
-      for (int c = j + 1 + (tid >> 5); c < j0 + jb; c += blockDim.x >> 5) {
-        const T u = A[j + (int64_t)c * m];
-        for (int i = j + 1 + (tid & 31); i < m; i += 32)
-          A[i + (int64_t)c * m] -= A[i + (int64_t)j * m] * u;
-      }
-      __syncthreads();
-    }
-    const int t0 = j0 + jb;
-    if (t0 >= m) break;
-    // (2) U12 = L11^-1 A12 for the columns right of the panel
-    for (int t = tid; t < jb * jb; t += blockDim.x) {
-      const int r = t % jb, q = t / jb;
-      Ls[r][q] = A[j0 + r + (int64_t)(j0 + q) * m];
-    }
-    __syncthreads();
-    for (int c = t0 + tid; c < m; c += blockDim.x) {
-      T x[NB];
-#pragma unroll
-      for (int r = 0; r < NB; ++r) x[r] = r < jb ? A[j0 + r + (int64_t)c * m] : T(0);
-#pragma unroll
-      for (int r = 1; r < NB; ++r) {
-        T s = x[r];
-#pragma unroll
-        for (int q = 0; q < r; ++q) s -= Ls[r][q] * x[q];
-        x[r] = s;
-      }
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r < jb) A[j0 + r + (int64_t)c * m] = x[r];
-    }
-    __syncthreads();
-    // (3) trailing update A22 -= L21 U12 over TT x TT tiles
-    const int nt = m - t0;
-    const int ntiles = (nt + TT - 1) / TT;
-    for (int tile = 0; tile < ntiles * ntiles; ++tile) {
-      const int ti = tile % ntiles, tj = tile / ntiles;
-      const int rb = t0 + ti * TT, cb = t0 + tj * TT;
-      for (int t = tid; t < TT * NB; t += blockDim.x) {
-        const int r = t % TT, q = t / TT;
-        Lt[r][q] = (rb + r < m && q < jb) ? A[rb + r + (int64_t)(j0 + q) * m] : T(0);
-        const int q2 = t % NB, c2 = t / NB;
-        Ut[q2][c2] = (cb + c2 < m && q2 < jb) ? A[j0 + q2 + (int64_t)(cb + c2) * m] : T(0);
-      }
-      __syncthreads();
-      const int tr = tid % 16, tc = tid / 16;
-      T acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-#pragma unroll 8
-      for (int q = 0; q < NB; ++q) {
-        T lv[4], uv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) lv[a] = Lt[tr + 16 * a][q];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) uv[b] = Ut[q][tc + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = cb + tc + 16 * b;
-        if (c >= m) continue;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int r = rb + tr + 16 * a;
-          if (r < m) A[r + (int64_t)c * m] -= acc[a][b];
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Large fronts, several CTAs per front: the same blocked right-looking LU as
-// k_front_lu, one panel of 32 pivots at a time.  Without pivoting the panel
+// Large fronts, several CTAs per front: blocked right-looking LU, one panel
+// of 32 pivots at a time.  Without pivoting the panel
 // splits into independent parts: the 32 x 32 diagonal block is factored
 // first (k_lu_diag, one CTA per front, which also forms the inverses of its
 // two triangles into a scratch block per front), then every row below it
@@ -579,8 +470,7 @@ __global__ void k_tri_inverse_copy(DevFronts F, const int32_t* __restrict__ list
 // ---------------------------------------------------------------------------
 // Small fronts (m*m entries fit in shared memory): partial LU and the
 // inversion of the diagonal triangles done in shared memory by one CTA, then
-// written back once.  Same arithmetic as k_front_lu followed by
-// k_tri_inverse, without the round trips through global memory.
+// written back once.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -669,45 +559,6 @@ __global__ void k_spike_rhs(const int32_t* __restrict__ rt_rownew, const int32_t
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = rt_rhscol[e] - j0;
     if (j >= 0 && j < NR) X[(int64_t)rt_rownew[e] * NR + j] = (T)values[rt_src[e]];
-  }
-}
-
-// In-place inversion of the diagonal block of each front after its partial
-// LU: the strictly lower part (unit L11) becomes that of L11^-1 and the upper
-// part with the diagonal becomes U11^-1.  The triangular solves of the block
-// solves and of the spikes then become products with these inverses.
-//   L^-1(i,j) = -( L(i,j) + sum_{j<l<i} L^-1(i,l) L(l,j) ),  columns j descending;
-//   U^-1(i,j) = -( sum_{i<=l<j} U^-1(i,l) U(l,j) ) / U(j,j),  columns j ascending.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_tri_inverse(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena) {
-  extern __shared__ unsigned char smem_raw[];
-  T* v = reinterpret_cast<T*>(smem_raw);
-  const int32_t f = list[blockIdx.x];
-  const int32_t k = F.k[f], m = F.m[f];
-  T* __restrict__ A = arena + F.arena[f];
-  const int tid = threadIdx.x;
-  for (int j = k - 2; j >= 0; --j) {
-    for (int i = j + 1 + tid; i < k; i += blockDim.x) v[i] = A[i + (int64_t)j * m];
-    __syncthreads();
-    for (int i = j + 1 + tid; i < k; i += blockDim.x) {
-      T s = v[i];
-      for (int l = j + 1; l < i; ++l) s += A[i + (int64_t)l * m] * v[l];
-      A[i + (int64_t)j * m] = -s;
-    }
-    __syncthreads();
-  }
-  for (int j = 0; j < k; ++j) {
-    for (int i = tid; i <= j; i += blockDim.x) v[i] = A[i + (int64_t)j * m];
-    __syncthreads();
-    const T d = v[j];
-    for (int i = tid; i < j; i += blockDim.x) {
-      T s = T(0);
-      for (int l = i; l < j; ++l) s += A[i + (int64_t)l * m] * v[l];
-      A[i + (int64_t)j * m] = -s / d;
-    }
-    if (tid == 0) A[j + (int64_t)j * m] = T(1) / d;
-    __syncthreads();
   }
 }
 
@@ -810,13 +661,6 @@ void launch_extend_add_p(DevFronts F, const int32_t* parent, const int32_t* chil
 }
 
 template <typename T>
-void launch_front_lu(DevFronts F, const int32_t* list, int32_t nf, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s) {
-  if (nf <= 0) return;
-  k_front_lu<T><<<nf, kThreads, 0, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
-}
-
-template <typename T>
 void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const int64_t* rt_src,
                       int64_t nrt, const double* values, int64_t j0, int32_t NR, T* X,
                       cudaStream_t s) {
@@ -873,16 +717,6 @@ void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t
   k_front_lu_small<T><<<nf, kThreads, sm, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
 }
 
-template <typename T>
-void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
-                        cudaStream_t s) {
-  if (nf <= 0) return;
-  const size_t sm = (size_t)std::max(max_k, 1) * sizeof(T);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_tri_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_tri_inverse<T><<<nf, kThreads, sm, s>>>(F, list, arena);
-}
-
 template <typename T, typename TG>
 void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const int64_t* gq0,
                          const int64_t* gcol_ptr, const int64_t* ghat_off, const int64_t* gld,
@@ -897,12 +731,8 @@ void launch_ghat_extract(const int32_t* qblock, const int32_t* c_rownew, const i
   template void launch_assemble<T>(const double*, const int64_t*, int64_t, T*, cudaStream_t);  \
   template void launch_extend_add_p<T>(DevFronts, const int32_t*, const int32_t*, int32_t,     \
                                        int32_t, T*, cudaStream_t);                             \
-  template void launch_front_lu<T>(DevFronts, const int32_t*, int32_t, T*, const double*,      \
-                                   double, long long*, cudaStream_t);                          \
   template void launch_spike_rhs<T>(const int32_t*, const int32_t*, const int64_t*, int64_t,   \
                                     const double*, int64_t, int32_t, T*, cudaStream_t);        \
-  template void launch_tri_inverse<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,         \
-                                      cudaStream_t);                                            \
   template void launch_front_lu_small<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,      \
                                          const double*, double, long long*, cudaStream_t);      \
   template void launch_tri_inverse_mc<T>(DevFronts, const int32_t*, const int32_t*, int32_t,    \

@@ -44,9 +44,6 @@ void launch_row_absmax(const int32_t* rowptr, const int64_t* amap, const double*
 template <typename T>
 void launch_extend_add_p(DevFronts F, const int32_t* parent, const int32_t* child_list,
                          int32_t nchild, int32_t max_r, T* arena, cudaStream_t s);
-template <typename T>
-void launch_front_lu(DevFronts F, const int32_t* list, int32_t nf, T* arena,
-                     const double* rownorm_new, double pivot_tol, long long* err, cudaStream_t s);
 // multi-RHS spike solves on a row-major panel X (n x NR) and update rows U (upd_size x NR)
 template <typename T>
 void launch_spike_rhs(const int32_t* rt_rownew, const int32_t* rt_rhscol, const int64_t* rt_src,
@@ -87,9 +84,6 @@ void launch_lu_panel(DevFronts F, const int32_t* list, int32_t nf, const int32_t
 template <typename T>
 void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* tile_ij,
                         int32_t ntiles, int32_t j0, int blocked, T* arena, cudaStream_t s);
-template <typename T>
-void launch_tri_inverse(DevFronts F, const int32_t* list, int32_t nf, int32_t max_k, T* arena,
-                        cudaStream_t s);
 
 // ---- spike.cu: multi-RHS forward/backward substitution as per-level GEMMs ----
 // Panel X (n x NR, row-major) holds the right-hand sides and receives the
