@@ -120,6 +120,29 @@ def test_spikes_against_dense_inverse():
     assert np.allclose(o.reduced_dense(), Gh, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("make,drop", [
+    (lambda: W.small_convdiff_3d(8, [3, 3, 2]), None),
+    (lambda: W.small_random_band(600, 4, 40, seed=3), ("abs", 1e-4)),
+])
+def test_implicit_reduced_product_identity(make, drop):
+    """The identity the implicit G^ variant applies: for v on c,
+    (I + G(c,c)) v = v + (D~^-1 (R~ v))(c), with R~ the dropped coupling and
+    the dense inverse of D standing in for the factors."""
+    P = make()
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=drop)
+    A = _dense(P)
+    D = np.zeros_like(A)
+    bp = P.block_ptr
+    for i in range(P.p):
+        D[bp[i]:bp[i + 1], bp[i]:bp[i + 1]] = A[bp[i]:bp[i + 1], bp[i]:bp[i + 1]]
+    Rt = o.Rt.toarray()
+    v = np.random.default_rng(11).standard_normal(o.m)
+    vfull = np.zeros(P.n)
+    vfull[o.c] = v
+    w = v + np.linalg.solve(D, Rt @ vfull)[o.c]
+    assert np.linalg.norm(o.reduced_matvec(v) - w) <= 1e-12 * np.linalg.norm(w)
+
+
 def test_retrieval_forms_agree_with_inexact_inner():
     """6.5 (z = g - G z) and z = D^-1 (y - R z^) agree for any z^."""
     P = W.small_convdiff_2d(12, 4)
