@@ -291,6 +291,28 @@ def cpu_threads():
 
 
 # ----------------------------------------------------------------------------
+# replicas: one rank per GPU, no data-path collective; the step time is the
+# slowest rank's and the value counts every rank's systems
+# ----------------------------------------------------------------------------
+
+def max_over_ranks_of(v, dist=None, device="cuda"):
+    """Largest value of v over the ranks of the process group (v itself
+    without one)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ms_max, world, units_per_rank, steps):
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the oracle as it stands, on the host cores
 # ----------------------------------------------------------------------------
 
@@ -360,11 +382,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(v, dist, "cuda")
 
     P, sbp, nsys, drop = make_workload(args.workload)
     opts = form_options(args.form)
@@ -408,7 +426,7 @@ def run_ours(args):
     launches = S.launch_count() - launches0
     S.set_profiling(0)
     ms_max = max_over_ranks(ms)
-    value = world * nsys * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(ms_max, world, nsys, args.steps)
 
     # accuracy of the last step against the known solution and the residual
     xh = x.cpu().numpy()
@@ -513,7 +531,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(a0.elapsed_time(a1))
-        line["e2e"] = {"value": world * nsys * args.steps / (ems / 1e3), "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(ems, world, nsys, args.steps), "unit": UNIT,
                        "h2d_bytes_per_step": int(P.nnz * 8 + P.n * 8),
                        "d2h_bytes_per_step": int(P.n * 8)}
 
@@ -537,7 +555,7 @@ def run_ours(args):
         b1.record(stream)
         torch.cuda.synchronize()
         fms = max_over_ranks(b0.elapsed_time(b1))
-        v64 = world * nsys * args.fp64_steps / (fms / 1e3)
+        v64 = whole_job_rate(fms, world, nsys, args.fp64_steps)
         line["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": fms / args.fp64_steps,
                               "relres_inf": i64["relres_inf"],
                               "outer_iterations": i64["outer_iterations"]}

@@ -1,0 +1,61 @@
+"""The multi-rank bench path on the CPU: two gloo ranks, as torchrun would run
+two replicas.  Every rank solves its own systems with no collective on the
+data path; the only exchange is the maximum of the timed region, and the
+whole-job value counts every rank's systems over that slowest time."""
+
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _replica(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        ms = 10.0 + 5.0 * rank  # the second rank is the slow one
+        ms_max = bench.max_over_ranks_of(ms, dist, "cpu")
+        out[rank] = (ms_max, bench.whole_job_rate(ms_max, world, 3, 4))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank_and_count_every_rank():
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_replica, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert sorted(res) == [0, 1]
+    for rank in (0, 1):
+        ms_max, value = res[rank]
+        assert ms_max == 15.0
+        assert value == pytest.approx(2 * 3 * 4 / 0.015)
+
+
+def test_single_process_needs_no_group():
+    import bench
+    assert bench.max_over_ranks_of(7.5) == 7.5
+    assert bench.whole_job_rate(250.0, 1, 1, 5) == pytest.approx(20.0)
+
+
+def test_reference_arm_prints_only_on_rank_zero(capsys, monkeypatch):
+    """Under torchrun the reference arm runs on rank 0 alone; the other ranks
+    exit without work or output."""
+    import argparse
+
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    args = argparse.Namespace(workload="cd2d_64_p4", steps=1, warmup=0, gpus=2, impl="reference")
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
