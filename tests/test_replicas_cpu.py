@@ -59,3 +59,25 @@ def test_reference_arm_prints_only_on_rank_zero(capsys, monkeypatch):
     args = argparse.Namespace(workload="cd2d_64_p4", steps=1, warmup=0, gpus=2, impl="reference")
     bench.run_reference(args)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(capsys, monkeypatch):
+    """Rank 0 of the reference arm prints one JSON line with the bench keys,
+    the oracle as its CPU baseline and an e2e object without copies."""
+    import argparse
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(workload="cd2d_64_p4", steps=1, warmup=0, gpus=1, impl="reference")
+    bench.run_reference(args)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
