@@ -35,6 +35,28 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The CPU oracle legs run on one host thread: BLAS pools are sized from these
+# variables when numpy first loads (nothing on the GPU path uses host BLAS).
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+
+class _one_thread:
+    """Holds the host BLAS pools to one thread where threadpoolctl is
+    installed; otherwise the variables above already did."""
+
+    def __enter__(self):
+        try:
+            from threadpoolctl import threadpool_limits
+            self._lim = threadpool_limits(1)
+        except ImportError:
+            self._lim = None
+        return self
+
+    def __exit__(self, *exc):
+        if self._lim is not None:
+            self._lim.restore_original_limits()
+        return False
 
 METRIC = "solves/s at rel. residual 1e-10, mixed/batched/learned vs plain FP64 DDPS on GB300"
 UNIT = "solves/s"
@@ -54,10 +76,13 @@ def parse_args():
                          "FP16 G^; implicit: the variant that applies G^ by block solves "
                          "instead of forming the spikes")
     ap.add_argument("--fp64-steps", type=int, default=None,
-                    help="steps of the plain-FP64 comparison run (0 skips it; default 1, "
+                    help="steps of the plain-FP64 comparison run (0 skips it; default 3, "
                          "0 for randband_1m whose FP64 factor takes over a minute)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads' sub-results (256-system batch, 1M random "
+                         "band, 48^3 learned sequence) and the FP32-G^ and solve-only lines")
     ap.add_argument("--drop-sweep", action="store_true",
                     help="instead of the bench line: the Sec. 3 column rule on the random-band "
                          "workload for several delta (outer/inner iterations, |c|, solves/s)")
@@ -230,64 +255,119 @@ def algorithmic_work(sizes, P, form, steps, prof):
 # CPU oracle sample (bench's CPU-baseline leg and the reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(P, nblocks=4, ncols=1024):
-    """Times the oracle's Fig. 2 steps 1-5 on `nblocks` blocks with `ncols`
-    spike columns each and scales to every block and column.  The solve phase
-    (Fig. 2 step 6) is not included, so the scaled time is a lower bound on the
-    oracle's seconds per solve."""
+def oracle_sample(P, nblocks=2, ncols=256, counts=None):
+    """Times the oracle, as it stands, on a bounded sample of one DDPS solve
+    of the workload and scales each measured piece to the whole solve.
+
+    Measured on the sample (one thread: BLAS is held to one thread, SuperLU
+    is single-threaded):
+      * Fig. 2 step 1 and 5 (split, c) on the whole matrix;
+      * step 2 (LU) of `nblocks` blocks, scaled by the number of blocks;
+      * step 4 (spikes) of `ncols` columns of those blocks, scaled by the
+        blocks' coupling-column counts;
+      * step 6 pieces: one block solve of each sampled block (scaled to all
+        blocks), one product of each sampled block's G^ rows with a vector
+        (scaled by the G^ entries), one product with A;
+    and combined with the iteration counts of a whole solve (`counts`:
+    outer products with A, Fig. 3 applications, inner iterations).
+    Returns (seconds per solve, wall seconds of the sample, description)."""
     import numpy as np
+
     from oracle.ddps_oracle import csr, factor_blocks, interface_columns, split_block_rows
 
-    t0 = time.perf_counter()
-    A = csr(P.n, P.rowptr, P.colind, P.values)
-    D, R = split_block_rows(A, P.block_ptr)
-    interface_columns(R)
-    t_split = time.perf_counter() - t0
-    bp = P.block_ptr
-    est = t_split
-    per_block = []
-    for i in range(min(nblocks, P.p)):
-        t1 = time.perf_counter()
-        lu = factor_blocks([D[i]])[0]
-        t_lu = time.perf_counter() - t1
-        Ri = R[bp[i]:bp[i + 1], :]
-        ci = np.unique(Ri.indices)
-        k = min(ncols, len(ci))
-        t2 = time.perf_counter()
-        if k:
-            cols = Ri.tocsc()[:, ci[:k]]
-            lu.solve(cols.toarray())
-        t_sp = time.perf_counter() - t2
-        per_block.append(t_lu + (t_sp * len(ci) / k if k else 0.0))
-    est += statistics.mean(per_block) * P.p
-    wall = time.perf_counter() - t0
-    return est, wall
+    counts = counts or DEFAULT_ORACLE_COUNTS
+    with _one_thread():
+        t0 = time.perf_counter()
+        A = csr(P.n, P.rowptr, P.colind, P.values)
+        D, R = split_block_rows(A, P.block_ptr)
+        c = interface_columns(R)
+        t_split = time.perf_counter() - t0
+        bp = P.block_ptr
+        lu_t, sp_t, bs_t, mv_t = [], [], [], []
+        pick = np.linspace(0, P.p - 1, min(nblocks, P.p)).round().astype(int)
+        g_entries_tot = 0
+        for i in range(P.p):
+            Ri = R[bp[i]:bp[i + 1], :]
+            rows_c = np.count_nonzero((c >= bp[i]) & (c < bp[i + 1]))
+            g_entries_tot += rows_c * len(np.unique(Ri.indices))
+        g_entries_samp = 0
+        for i in pick:
+            t1 = time.perf_counter()
+            lu = factor_blocks([D[i]])[0]
+            lu_t.append(time.perf_counter() - t1)
+            Ri = R[bp[i]:bp[i + 1], :]
+            ci = np.unique(Ri.indices)
+            k = min(ncols, len(ci))
+            if k:
+                t2 = time.perf_counter()
+                cols = Ri.tocsc()[:, ci[:k]].toarray()
+                G = lu.solve(cols)
+                sp_t.append((time.perf_counter() - t2) * len(ci) / k)
+                rows_c = c[(c >= bp[i]) & (c < bp[i + 1])] - bp[i]
+                Gh = G[rows_c, :]
+                v = np.ones(k)
+                t3 = time.perf_counter()
+                for _ in range(3):
+                    Gh @ v
+                mv_t.append((time.perf_counter() - t3) / 3 * len(ci) / k)
+                g_entries_samp += len(rows_c) * len(ci)
+            y = np.ones(bp[i + 1] - bp[i])
+            t4 = time.perf_counter()
+            lu.solve(y)
+            bs_t.append(time.perf_counter() - t4)
+        xv = np.ones(P.n)
+        t5 = time.perf_counter()
+        for _ in range(3):
+            A @ xv
+        t_spmv = (time.perf_counter() - t5) / 3
+        wall = time.perf_counter() - t0
+    scale_b = P.p / len(pick)
+    t_factor = t_split + sum(lu_t) * scale_b + sum(sp_t) * scale_b
+    t_block_solve = sum(bs_t) * scale_b
+    t_ghat = (sum(mv_t) * g_entries_tot / g_entries_samp) if g_entries_samp else 0.0
+    t_solve = (counts["spmv"] * t_spmv + 2 * counts["applies"] * t_block_solve +
+               2 * counts["inner"] * t_ghat)
+    desc = ("oracle (numpy/scipy, one thread) timed on a sample: split and c of the whole "
+            "matrix, LU and %d spike columns of %d of the %d blocks, one block solve and one "
+            "G^-row product of those blocks, one product with A; scaled to the whole solve "
+            "(factor %.1f s, solve %.1f s per solve) with the iteration counts of a whole "
+            "oracle solve (%d products with A, %d Fig. 3 applications, %d inner iterations); "
+            "sample wall %.1f s" % (ncols, len(pick), P.p, t_factor, t_solve, counts["spmv"],
+                                    counts["applies"], counts["inner"], wall))
+    return t_factor + t_solve, wall, desc
+
+
+# Iteration counts of one whole oracle solve (eps_in 1e-4, tol 1e-10) of the
+# 64^3 slab workload: 1.5 outer iterations = 3 Fig. 3 applications; products
+# with A: 2 per outer iteration plus the true-residual checks.
+DEFAULT_ORACLE_COUNTS = {"spmv": 5, "applies": 3, "inner": 46}
 
 
 def oracle_batch_sample(systems, count=3):
     """Whole oracle solves (Fig. 2 and 3, eps_in 1e-4, tol 1e-10) of the first
     `count` systems of a batch, scaled to the batch by the number of unknowns."""
     from oracle.ddps_oracle import DDPSOracle
-    t0 = time.perf_counter()
-    nsamp = 0
-    for p in systems[:count]:
-        DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr).solve(p.f, tol=1e-10,
-                                                                          eps_in=1e-4)
-        nsamp += p.n
-    wall = time.perf_counter() - t0
+    with _one_thread():
+        t0 = time.perf_counter()
+        nsamp = 0
+        for p in systems[:count]:
+            DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr).solve(p.f, tol=1e-10,
+                                                                              eps_in=1e-4)
+            nsamp += p.n
+        wall = time.perf_counter() - t0
     ntot = sum(p.n for p in systems)
     est = wall * ntot / nsamp
-    return est, wall, ("whole oracle solves of %d of the %d systems (%.1f s wall), scaled by "
-                       "unknowns to the batch" % (count, len(systems), wall))
+    return est, wall, ("whole oracle solves (Fig. 2 and 3, one thread) of %d of the %d systems "
+                       "(%.1f s wall), scaled by unknowns to the batch" % (count, len(systems), wall))
 
 
-def cpu_threads():
-    try:
-        from threadpoolctl import threadpool_info
-        th = [i.get("num_threads", 1) for i in threadpool_info()]
-        return max(th) if th else 1
-    except Exception:
-        return os.cpu_count() or 1
+def cpu_baseline_entry(P, nsys, workload):
+    if nsys > 1:
+        est, wall, sample = oracle_batch_sample(P.systems)
+    else:
+        nb, nc = (1, 64) if workload == "randband_1m" else (2, 256)
+        est, wall, sample = oracle_sample(P, nblocks=nb, ncols=nc)
+    return {"value": nsys / est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
 
 # ----------------------------------------------------------------------------
@@ -321,19 +401,18 @@ def run_reference(args):
     if rank != 0:
         return
     P, sbp, nsys, drop = make_workload(args.workload)
-    nb, nc = (1, 64) if args.workload == "randband_1m" else (2, 256)
+    nb, nc = (1, 32) if args.workload == "randband_1m" else (1, 128)
 
     def sample():
         if nsys > 1:
-            e, w, _ = oracle_batch_sample(P.systems, count=1)
-            return e, w
+            return oracle_batch_sample(P.systems, count=1)
         return oracle_sample(P, nblocks=nb, ncols=nc)
 
     for _ in range(args.warmup):
         sample()
-    ests, walls = [], []
+    ests, walls, desc = [], [], ""
     for _ in range(args.steps):
-        e, w = sample()
+        e, w, desc = sample()
         ests.append(e)
         walls.append(w)
     sec = statistics.mean(ests)
@@ -341,18 +420,14 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        # each step is one bounded sample of a solve; its wall time is the step time
+        "ms_per_step": statistics.mean(walls) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz,
-                   "blocks": P.p,
-                   "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": ("whole oracle solve of 1 of the systems, scaled by unknowns "
-                                    "to the batch" if nsys > 1 else
-                                    "oracle Fig. 2 steps 1-5 on %d of the blocks with %d spike "
-                                    "columns each, scaled to all blocks and columns; solve phase "
-                                    "not counted" % (nb, nc)) +
-                                   " (per step wall %.1f s)" % statistics.mean(walls)},
+                   "blocks": P.p, "parallelism": "host cores"},
+        "seconds_per_solve_scaled": sec,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -361,6 +436,82 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+
+def timed(stream, fn, steps):
+    """CUDA-event milliseconds of `steps` calls of fn on `stream` (synchronised on
+    both sides); returns (ms, list of fn's results)."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def kernel_table(prof, work, ms_total, peaks):
+    """Per kernel class: time, launch groups, share of the profiled steps and
+    achieved rate (plus the fraction of the HBM peak for memory-bound ones)."""
+    kern = {}
+    for cls, (kms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        kind, amount = work.get(cls, ("bytes", 0.0))
+        rate = amount / (kms / 1e3) if kms > 0 else 0.0
+        e = {"ms": round(kms, 3), "groups": cnt, "share": round(kms / ms_total, 4),
+             "achieved": round(rate / (1e9 if kind == "bytes" else 1e12), 3),
+             "unit": "GB/s" if kind == "bytes" else "TFLOP/s"}
+        if kind == "bytes":
+            e["frac_hbm"] = round(e["achieved"] / peaks["hbm_gbs"], 4)
+        kern[cls] = e
+    return kern
+
+
+def measure_workload(name, form, steps, warmup, stream, extra_opts=None):
+    """Factor + solve steps of one workload in one form (profiling off):
+    solves/s and accuracy; used for the sub-results of the bench line."""
+    import numpy as np
+    import torch
+
+    from paper_1008_1700_gb300 import Solver, native as N
+
+    P, sbp, nsys, drop = make_workload(name)
+    opts = form_options(form)
+    if drop is not None:
+        opts.update(drop_mode=N.DDPS_DROP_ABS, drop_tol=drop[1])
+    if extra_opts:
+        opts.update(extra_opts)
+    t0 = time.perf_counter()
+    S = Solver(P.rowptr, P.colind, P.block_ptr, sbp, P.values if drop else None, **opts)
+    analyze_ms = (time.perf_counter() - t0) * 1e3
+    vals = torch.tensor(P.values, device="cuda")
+    f = torch.tensor(P.f, device="cuda")
+    x = torch.empty_like(f)
+
+    def step():
+        S.factor(vals)
+        return S.solve(f, x)[1]
+
+    for _ in range(warmup):
+        step()
+    ms, infos = timed(stream, step, steps)
+    xh = x.cpu().numpy()
+    out = {"value": nsys * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "systems_per_step": nsys, "form": form, "n": P.n,
+           "blocks": P.p, "m_interface": S.m, "analyze_ms": round(analyze_ms, 1),
+           "relres_inf": max(i["relres_inf"] for i in infos),
+           "converged": all(i["status"] == "DDPS_OK" for i in infos),
+           "outer_iterations": infos[-1]["outer_iterations"],
+           "inner_iterations": infos[-1]["inner_iterations"]}
+    if P.x_true is not None:
+        out["rel_err_vs_xtrue"] = float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))
+    S.close()
+    del vals, f, x
+    torch.cuda.empty_cache()
+    return out
+
 
 def run_ours(args):
     import numpy as np
@@ -402,29 +553,18 @@ def run_ours(args):
         _, info = S.solve(f, x)
         return info
 
-    info = None
     for _ in range(args.warmup):
-        info = step()
-    S.set_profiling((1 << len(N.PROF_CLASSES)) - 1)
-    S.profile(reset=True)
+        step()
+
+    # timed region: profiling off, inputs resident in HBM (G^ and the fronts
+    # are larger than L2, so every product streams them from HBM)
     launches0 = S.launch_count()
     clocks = ClockSampler(local)
     barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    infos = []
-    for _ in range(args.steps):
-        infos.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, infos = timed(stream, step, args.steps)
     barrier()
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    prof = S.profile(reset=True)
     launches = S.launch_count() - launches0
-    S.set_profiling(0)
     ms_max = max_over_ranks(ms)
     value = whole_job_rate(ms_max, world, nsys, args.steps)
 
@@ -435,19 +575,17 @@ def run_ours(args):
     relres = max(i["relres_inf"] for i in infos)
     converged = all(i["status"] == "DDPS_OK" for i in infos)
 
-    # roofline of the dominant kernel class
+    # per-class split from a separate pass of the same steps with every
+    # kernel class bracketed by CUDA events on the launching stream
+    psteps = min(args.steps, 5)
+    S.set_profiling((1 << len(N.PROF_CLASSES)) - 1)
+    S.profile(reset=True)
+    pms, _ = timed(stream, step, psteps)
+    prof = S.profile(reset=True)
+    S.set_profiling(0)
     peaks = load_peaks()
-    work = algorithmic_work(sizes, P, args.form, args.steps, prof)
-    total_prof = sum(v[0] for v in prof.values())
-    kern = {}
-    for cls, (kms, cnt) in prof.items():
-        if cnt == 0:
-            continue
-        kind, amount = work.get(cls, ("bytes", 0.0))
-        rate = amount / (kms / 1e3) if kms > 0 else 0.0
-        kern[cls] = {"ms": round(kms, 3), "groups": cnt, "share": round(kms / ms, 4),
-                     "achieved": round(rate / (1e9 if kind == "bytes" else 1e12), 3),
-                     "unit": "GB/s" if kind == "bytes" else "TFLOP/s"}
+    work = algorithmic_work(sizes, P, args.form, psteps, prof)
+    kern = kernel_table(prof, work, pms, peaks)
     dom = max(kern, key=lambda k: kern[k]["ms"])
     dk = kern[dom]
     sm_mhz = peaks["sm_max_mhz"]
@@ -477,7 +615,9 @@ def run_ours(args):
         traffic = int(ratio * per_launch)
     roof = {"kernel": dom, "bound": bound, "achieved": dk["achieved"], "peak": round(peak, 2),
             "unit": dk["unit"], "frac": round(dk["achieved"] / peak, 4), "traffic": traffic,
-            "traffic_source": traffic_note, "peak_source": peak_note}
+            "traffic_source": traffic_note, "peak_source": peak_note,
+            "timing": "CUDA events per kernel class on the launching stream, over a pass of "
+                      "%d steps after the timed region (the timed region runs unprofiled)" % psteps}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -505,35 +645,45 @@ def run_ours(args):
         "clocks": clk,
         "roofline": roof,
         "kernels": kern,
+        "hbm_targets": {k: kern[k].get("frac_hbm") for k in ("block_solve", "spmv", "ghat_matvec")
+                        if k in kern},
     }
 
-    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    # e2e through the C ABI with host buffers (pinned): ddps_factor_host copies
+    # the values, ddps_solve_host copies f in and x out, all inside the timed region
     if not args.no_e2e:
         vals_h = torch.tensor(P.values).pin_memory()
-        f_h = np.ascontiguousarray(P.f)
-        x_h = np.empty_like(f_h)
-        vals_d2 = torch.empty_like(vals)
+        f_h = torch.tensor(P.f).pin_memory()
+        x_h = torch.empty_like(f_h).pin_memory()
 
         def e2e_step():
-            vals_d2.copy_(vals_h, non_blocking=True)
-            S.factor(vals_d2)
+            N.ddps_factor_host(S.h, vals_h)
             N.ddps_solve_host(S.h, f_h, x_h)
 
         e2e_step()
         barrier()
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        a1.record(stream)
-        torch.cuda.synchronize()
+        ems, _ = timed(stream, e2e_step, args.steps)
         barrier()
-        ems = max_over_ranks(a0.elapsed_time(a1))
+        ems = max_over_ranks(ems)
         line["e2e"] = {"value": whole_job_rate(ems, world, nsys, args.steps), "unit": UNIT,
                        "h2d_bytes_per_step": int(P.nnz * 8 + P.n * 8),
-                       "d2h_bytes_per_step": int(P.n * 8)}
+                       "d2h_bytes_per_step": int(P.n * 8),
+                       "path": "ddps_factor_host + ddps_solve_host (pinned host buffers)"}
+
+    extras = not args.no_extras and world == 1
+    if extras and args.form == "mixed":
+        # solve-only throughput with the factors kept (repeated right-hand sides,
+        # the factor phase needs none: Sec. 3); 4 right-hand sides per call
+        nr = 4
+        F4 = torch.tensor(np.stack([P.f * (1.0 + 0.25 * j) for j in range(nr)]), device="cuda")
+        X4 = torch.empty_like(F4)
+        S.factor(vals)
+        S.solve(F4, X4)
+        sms, sinf = timed(stream, lambda: S.solve(F4, X4)[1], 2)
+        line["solve_only"] = {"value": 2 * nr * nsys / (sms / 1e3), "unit": UNIT,
+                              "ms_per_solve": sms / (2 * nr), "nrhs_per_call": nr,
+                              "relres_inf": max(i["relres_inf"] for i in sinf)}
+        del F4, X4
 
     # plain FP64 DDPS on the same GPU and workload (the comparison the metric names)
     if args.form != "fp64" and args.fp64_steps > 0:
@@ -542,51 +692,59 @@ def run_ours(args):
             o64.update(drop_mode=N.DDPS_DROP_ABS, drop_tol=drop[1])
         S64 = Solver(P.rowptr, P.colind, P.block_ptr, sbp, P.values if drop else None, **o64)
         x64 = torch.empty_like(f)
-        S64.factor(vals)
-        S64.solve(f, x64)
-        torch.cuda.synchronize()
-        b0 = torch.cuda.Event(enable_timing=True)
-        b1 = torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        i64 = None
-        for _ in range(args.fp64_steps):
+
+        def step64():
             S64.factor(vals)
-            _, i64 = S64.solve(f, x64)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        fms = max_over_ranks(b0.elapsed_time(b1))
+            return S64.solve(f, x64)[1]
+
+        step64()
+        fms, i64 = timed(stream, step64, args.fp64_steps)
+        fms = max_over_ranks(fms)
         v64 = whole_job_rate(fms, world, nsys, args.fp64_steps)
         line["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": fms / args.fp64_steps,
-                              "relres_inf": i64["relres_inf"],
-                              "outer_iterations": i64["outer_iterations"]}
+                              "steps": args.fp64_steps,
+                              "relres_inf": max(i["relres_inf"] for i in i64),
+                              "outer_iterations": i64[-1]["outer_iterations"]}
         line["speedup_vs_plain_fp64"] = value / v64
         S64.close()
 
+    if extras and args.form == "mixed":
+        # the benchmark spec's named precision form: FP32 G^ instead of FP16 storage
+        line["fp32_ghat"] = measure_workload(args.workload, "mixed", 3, 1, stream,
+                                             {"ghat_prec": N.DDPS_FP32})
+    S.close()
+    del vals, f, x
+    torch.cuda.empty_cache()
+
+    if extras and args.workload == "cd3d_64_slabs16":
+        # the other workloads, driver-visible: a short timed run of each
+        line["workloads"] = {
+            "cd2d_batch256": measure_workload("cd2d_batch256", "mixed", 3, 2, stream),
+            "randband_1m": measure_workload("randband_1m", "mixed", 2, 1, stream),
+        }
+        line["workloads"]["cd3d_48_seq"] = sequence_result(args.form, 10, stream)
+
     # CPU oracle, bounded sample, rank 0 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if nsys > 1:
-            est, wall, sample = oracle_batch_sample(P.systems)
-        else:
-            nb, nc = (1, 128) if args.workload == "randband_1m" else (4, 1024)
-            est, wall = oracle_sample(P, nblocks=nb, ncols=nc)
-            sample = ("oracle Fig. 2 steps 1-5 on %d of the %d blocks with %d spike columns "
-                      "each, scaled to all blocks and columns (%.1f s wall); the solve phase is "
-                      "not counted, so this overstates the oracle's solves/s" % (nb, P.p, nc, wall))
-        line["cpu_baseline"] = {"value": nsys / est, "unit": UNIT, "cores": cpu_threads(),
-                                "kind": "oracle", "sample": sample}
+        try:
+            line["cpu_baseline"] = cpu_baseline_entry(P, nsys, args.workload)
+        except Exception as ex:  # the GPU line is still printed
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: %s" % ex}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    S.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_sequence_bench(args):
+def sequence_result(form, eval_steps, stream, train_steps=100):
     """Time sequence of 48^3 systems, b(t) = 20 + 10 sin(2 pi t / 200), fixed
-    source: zero-guess solves of steps 1-100 train the step-change network
-    (not timed); the timed region is `steps` evaluation steps from t = 101,
-    each factor + predicted guess + solve; the same steps with a zero guess
-    are timed for comparison."""
+    source: zero-guess solves of steps 1..train_steps collect the reduced
+    solutions z^(t), on which the step-change network is trained (the
+    library's MLP kernels); then `eval_steps` steps from t = train_steps + 1
+    are timed three times, each step factor + guess + solve: with the
+    network's guess, with the previous step's z^ (warm start) and with z^ = 0
+    (the paper's start)."""
     import numpy as np
     import torch
 
@@ -594,14 +752,14 @@ def run_sequence_bench(args):
     from paper_1008_1700_gb300 import Solver
     from paper_1008_1700_gb300.learned import StepGuess
 
-    opts = form_options(args.form)
+    opts = form_options(form)
     P0 = W.cfg5(1)
     S = Solver(P0.rowptr, P0.colind, P0.block_ptr, **opts)
     f = torch.tensor(P0.f, device="cuda")
     x = torch.empty_like(f)
     t0 = time.perf_counter()
     zs, bs = [], []
-    for t in range(1, 101):
+    for t in range(1, train_steps + 1):
         S.factor(torch.tensor(W.cfg5(t).values, device="cuda"))
         S.set_reduced_guess(None)
         S.solve(f, x)
@@ -609,50 +767,64 @@ def run_sequence_bench(args):
         bs.append(W.cfg5_coeff(t))
     model = StepGuess(torch.stack(zs), bs)
     train_s = time.perf_counter() - t0
-    ts = list(range(101, 101 + args.steps))
+    ts = list(range(train_steps + 1, train_steps + 1 + eval_steps))
     vals = [torch.tensor(W.cfg5(t).values, device="cuda") for t in ts]
-    stream = torch.cuda.current_stream()
 
-    def run(learned):
-        z_prev, b_prev = zs[-1], bs[-1]
-        infos = []
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for t, v in zip(ts, vals):
-            S.factor(v)
+    def run(mode):
+        state = {"z": zs[-1], "b": bs[-1], "i": 0, "infos": []}
+
+        def one():
+            i = state["i"]
+            t = ts[i]
+            S.factor(vals[i])
             bt = W.cfg5_coeff(t)
-            S.set_reduced_guess(model.predict(z_prev, bt, b_prev) if learned else None)
+            if mode == "learned":
+                S.set_reduced_guess(model.predict(state["z"], bt, state["b"]))
+            elif mode == "warm":
+                S.set_reduced_guess(state["z"])
+            else:
+                S.set_reduced_guess(None)
             _, info = S.solve(f, x)
-            infos.append(info)
-            z_prev = S.reduced_solution()[0].clone()
-            b_prev = bt
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), infos
+            state["z"] = S.reduced_solution()[0].clone()
+            state["b"] = bt
+            state["i"] += 1
+            return info
 
-    run(True)  # warm-up of the prediction path
-    ms_l, inf_l = run(True)
-    ms_0, inf_0 = run(False)
+        ms, infos = timed(stream, one, len(ts))
+        return {"value": len(ts) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / len(ts),
+                "first_inner_mean": float(np.mean([i["first_inner_iters"] for i in infos])),
+                "inner_mean": float(np.mean([i["inner_iterations"] for i in infos])),
+                "relres_max": float(max(i["relres_inf"] for i in infos)),
+                "converged": all(i["status"] == "DDPS_OK" for i in infos)}
+
+    run("learned")  # warm-up of the prediction path
+    out = {"n": P0.n, "blocks": P0.p, "form": form, "train_steps": f"1-{train_steps}",
+           "timed_steps": f"{ts[0]}-{ts[-1]}", "train_s": round(train_s, 2),
+           "learned": run("learned"), "warm_start": run("warm"), "zero_guess": run("zero")}
+    out["value"] = out["learned"]["value"]
+    out["unit"] = UNIT
+    S.close()
+    return out
+
+
+def run_sequence_bench(args):
+    """The 48^3 learned-guess sequence as its own bench line (timed region:
+    `steps` evaluation steps per guess strategy)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    r = sequence_result(args.form, args.steps, stream)
     line = {
-        "metric": METRIC, "value": args.steps / (ms_l / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": 1, "ms_per_step": ms_l / args.steps,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": r["learned"]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3+f16+f32+f64", "data": "synthetic",
-        "config": {"workload": "cd3d_48_seq", "n": P0.n, "blocks": P0.p,
-                   "train_steps": "1-100", "timed_steps": f"{ts[0]}-{ts[-1]}", "form": args.form},
-        "train_s": round(train_s, 2),
-        "learned": {"first_inner_mean": float(np.mean([i["first_inner_iters"] for i in inf_l])),
-                    "inner_mean": float(np.mean([i["inner_iterations"] for i in inf_l])),
-                    "relres_max": float(max(i["relres_inf"] for i in inf_l))},
-        "zero_guess": {"value": args.steps / (ms_0 / 1e3), "ms_per_step": ms_0 / args.steps,
-                       "first_inner_mean": float(np.mean([i["first_inner_iters"] for i in inf_0])),
-                       "inner_mean": float(np.mean([i["inner_iterations"] for i in inf_0])),
-                       "relres_max": float(max(i["relres_inf"] for i in inf_0))},
+        "config": {"workload": "cd3d_48_seq", "n": r["n"], "blocks": r["blocks"],
+                   "train_steps": r["train_steps"], "timed_steps": r["timed_steps"],
+                   "form": args.form},
+        "train_s": r["train_s"], "learned": r["learned"], "warm_start": r["warm_start"],
+        "zero_guess": r["zero_guess"],
     }
     print(json.dumps(line), flush=True)
-    S.close()
 
 
 def run_drop_sweep(args):
@@ -720,7 +892,7 @@ def main():
         run_drop_sweep(args)
         return
     if args.fp64_steps is None:
-        args.fp64_steps = 0 if args.workload == "randband_1m" else 1
+        args.fp64_steps = 0 if args.workload == "randband_1m" else 3
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "cd3d_48_seq":

@@ -165,21 +165,36 @@ ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const in
  * pivot fails the threshold. */
 ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream);
 
+/* Same as ddps_factor with the values in host memory (host float64[nnz],
+ * read during the call; pinned memory makes the copy asynchronous).  The
+ * copy into the handle's value array is enqueued on `stream`. */
+ddps_status ddps_factor_host(ddps_handle* h, const double* values_host, void* stream);
+
 /* Fig. 2 step 6: right-preconditioned BiCGStab on A x = f with the DDPS
- * preconditioner, x0 = 0, per-system scalars, stopping on the recomputed
- * true residual (tol_out, infinity norm).
- *   f  device float64[n];  x  device float64[n] (output)
- *   info  host, may be NULL.
+ * preconditioner, per-system scalars, stopping on the recomputed true
+ * residual (tol_out, infinity norm, relative to ||f||_inf).
+ *   f     device float64[n * nrhs]: nrhs right-hand sides, each n contiguous
+ *         entries (column-major n x nrhs)
+ *   x     device float64[n * nrhs] (output), same layout
+ *   nrhs  number of right-hand sides (>= 1); they are solved one after the
+ *         other with the same factors (the factor phase needs no right-hand
+ *         side, Sec. 3)
+ *   x0    device float64[n * nrhs] initial guesses, or NULL for x0 = 0; a
+ *         guess that already meets tol_out is returned after no iteration
+ *   info  host, may be NULL: iterations are the largest over the right-hand
+ *         sides, inner iterations and applications the totals, relres_inf
+ *         the worst, first_inner_iters that of the first right-hand side.
  * Synchronises `stream` (convergence is read on the host between iterations).
  * Returns DDPS_ERR_NOT_CONVERGED when some system misses tol_out within
  * maxit_out (x then holds the last iterate). */
-ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, void* stream,
-                       ddps_solve_info* info);
+ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, int32_t nrhs, const double* x0,
+                       void* stream, ddps_solve_info* info);
 
-/* Same as ddps_solve with host buffers: copies f to the device, solves and
- * copies x back (f, x: host float64[n]).  Synchronises. */
-ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, void* stream,
-                            ddps_solve_info* info);
+/* Same as ddps_solve with host buffers: copies f (and x0) to the device,
+ * solves and copies x back (f, x, x0: host float64[n * nrhs]; x0 may be
+ * NULL).  Synchronises. */
+ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, int32_t nrhs,
+                            const double* x0_host, void* stream, ddps_solve_info* info);
 
 /* Initial guess for the reduced unknowns z^ of the first preconditioner
  * application of the next solves (the hook a learned predictor fills).
@@ -209,8 +224,10 @@ ddps_status ddps_block_solve(ddps_handle* h, const double* y, double* g, void* s
  * than the array holds (n + the multifrontal update entries, times the
  * factor element size, must fit in 16 MiB).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
- * calls share the one array: calls whose work overlaps on the GPU (other
+ * device current; make that first call before any stream capture.  The
+ * address is cached per device and per context: after a device reset
+ * (cudaDeviceReset) the first call in the new context looks it up again.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
  * streams, other handles, other threads) race on it and must be ordered by
  * the caller. */
 ddps_status ddps_block_solve_noalloc(ddps_handle* h, const double* y, double* g, void* stream);

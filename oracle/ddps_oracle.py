@@ -86,9 +86,11 @@ def split_block_rows(A: sp.csr_matrix, block_ptr):
 # Fig. 2, step 2: L_i U_i = A_ii (exact)
 # ----------------------------------------------------------------------------
 
-def factor_blocks(D_blocks):
-    """Exact sparse LU of each diagonal block (the library step of Fig. 2 step 2)."""
-    return [spla.splu(Dii.tocsc()) for Dii in D_blocks]
+def factor_blocks(D_blocks, permc_spec="COLAMD"):
+    """Exact sparse LU of each diagonal block (the library step of Fig. 2 step 2).
+    ``permc_spec`` is SuperLU's column ordering; it changes the fill (and so
+    the time and memory) and the rounding, not the factored matrix."""
+    return [spla.splu(Dii.tocsc(), permc_spec=permc_spec) for Dii in D_blocks]
 
 
 # ----------------------------------------------------------------------------
@@ -257,7 +259,7 @@ class DDPSOracle:
     """
 
     def __init__(self, n, rowptr, colind, values, block_ptr, drop=None, keep_full_G=True,
-                 spikes=True):
+                 spikes=True, permc_spec="COLAMD"):
         self.n = int(n)
         self.A = csr(n, rowptr, colind, values)
         self.block_ptr = np.asarray(block_ptr, dtype=np.int64)
@@ -265,7 +267,7 @@ class DDPSOracle:
         # step 1
         self.D_blocks, self.R = split_block_rows(self.A, self.block_ptr)
         # step 2
-        self.lu = factor_blocks(self.D_blocks)
+        self.lu = factor_blocks(self.D_blocks, permc_spec)
         # step 3
         if drop is None:
             self.Rt = self.R
@@ -388,6 +390,39 @@ class DDPSOracle:
         info["inner_iterations"] = inner
         info["relres_inf"] = float(np.max(np.abs(f - self.A @ x)) / max(np.max(np.abs(f)), 1e-300))
         return x, info
+
+
+# ----------------------------------------------------------------------------
+# The plain definition x = A^-1 f for strictly diagonally dominant systems too
+# large for one sparse LU
+# ----------------------------------------------------------------------------
+
+def jacobi_solution(A: sp.csr_matrix, f, tol=1e-16, maxit=5000):
+    """x = A^-1 f by Jacobi iteration x <- D^-1 (f - (A - D) x), with a
+    certified bound.  For A strictly diagonally dominant by rows, the
+    iteration matrix B = -D^-1 (A - D) has q = ||B||_inf < 1 and every step
+    satisfies ||x - x_k||_inf <= q / (1 - q) ||x_k - x_(k-1)||_inf; the loop
+    stops once that bound is at most tol * ||x_k||_inf.  Returns (x, bound)
+    where bound is the certified ||x - x_k||_inf (exact arithmetic; FP64
+    rounding adds about n_row * eps * ||x||_inf).  This is the textbook
+    stationary method; DDPS reaches the same x = A^-1 f in its direct mode
+    (Sec. 3), which is the definition both are compared against."""
+    A = sp.csr_matrix(A)
+    d = A.diagonal()
+    off = (A - sp.diags(d)).tocsr()
+    q = float(np.max(np.asarray(abs(off).sum(axis=1)).ravel() / np.abs(d)))
+    if not q < 1.0:
+        raise ValueError("jacobi_solution needs a strictly row-diagonally dominant matrix")
+    f = np.asarray(f, dtype=np.float64)
+    x = f / d
+    bound = np.inf
+    for _ in range(maxit):
+        xn = (f - off @ x) / d
+        bound = q / (1.0 - q) * float(np.max(np.abs(xn - x)))
+        x = xn
+        if bound <= tol * float(np.max(np.abs(x))):
+            break
+    return x, bound
 
 
 def relres_inf(A: sp.csr_matrix, x, f) -> float:

@@ -308,7 +308,9 @@ SegView make_segview(ddps_handle* h, const std::vector<int64_t>& seg_ptr) {
 inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 void check_launch() {
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = take_launch_error();
+  const cudaError_t last = cudaGetLastError();
+  if (e == cudaSuccess) e = last;
   if (e != cudaSuccess) throw Fail{DDPS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
@@ -498,11 +500,14 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Fig. 3 step 6.1 (and the second block solve of the retrieval)
 // ---------------------------------------------------------------------------
+// w, u: the permuted vector (n entries) and the fronts' update vectors; the
+// handle's workspace unless the caller passes its own scratch.
 template <typename T>
-void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s, int prof_cls) {
+void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s, int prof_cls,
+                      T* w = nullptr, T* u = nullptr) {
   const Analysis& A = h->A;
-  T* w = (T*)h->w;
-  T* u = (T*)h->updv;
+  if (!w) w = (T*)h->w;
+  if (!u) u = (T*)h->updv;
   const T* arena = (const T*)h->arena;
   Prof pr(h, prof_cls, s);
   launch_permute_in<T>(y, h->perm, A.n, w, s);
@@ -726,8 +731,8 @@ void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, b
 // Fig. 2 step 6: right-preconditioned BiCGStab on A x = f (FP64), per system,
 // convergence on the recomputed true residual ||f - A x||_inf <= tol ||f||_inf.
 // ---------------------------------------------------------------------------
-ddps_status solve_impl(ddps_handle* h, const double* f, double* x, cudaStream_t s,
-                       ddps_solve_info* info) {
+ddps_status solve_impl(ddps_handle* h, const double* f, double* x, const double* x0,
+                       cudaStream_t s, ddps_solve_info* info) {
   const Analysis& A = h->A;
   const int64_t n = A.n;
   const SegView& S = h->Sn;
@@ -742,25 +747,44 @@ ddps_status solve_impl(ddps_handle* h, const double* f, double* x, cudaStream_t 
   h->stat_precond = 0;
   h->stat_first_inner = 0;
   h->stat_guess_used = false;
-  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   CK(cudaMemsetAsync(h->o_p, 0, n * sizeof(double), s));
   CK(cudaMemsetAsync(h->o_v, 0, n * sizeof(double), s));
   CK(cudaMemsetAsync(sc, 0, ns * sizeof(KScal), s));
-  CK(cudaMemcpyAsync(h->o_r, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->o_rhat, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  seg_reduce<double>(S, 1, red(f, nullptr, 2, &sc[0].ref), nored(), nored(), h->partial, s);
+  if (x0) {  // r0 = f - A x0
+    CK(cudaMemcpyAsync(x, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    spmv(x, h->o_tmp);
+    vec_sub<double>(S, sc, 1, f, h->o_tmp, h->o_r, s);
+    h->launches++;
+  } else {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    CK(cudaMemcpyAsync(h->o_r, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaMemcpyAsync(h->o_rhat, h->o_r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  seg_reduce<double>(S, 2, red(f, nullptr, 2, &sc[0].ref), red(h->o_r, nullptr, 2, &sc[0].nrm2),
+                     nored(), h->partial, s);
   h->launches += 2;
   download_sc(h, sc, s);
   const double tol = h->opt.tol_out;
   std::vector<double> iters(ns, 0.0);
   std::vector<int> conv(ns, 0);
+  bool zero_rhs = false;
   for (int q = 0; q < ns; ++q) {
     KScal& k = h->hsc[q];
-    k.active = k.ref > 0.0;
+    // a zero right-hand side has the solution 0; a guess that already meets
+    // the tolerance is the answer
+    k.active = k.ref > 0.0 && k.nrm2 > tol * k.ref;
+    k.flag = x0 && k.ref == 0.0;
+    zero_rhs |= k.flag != 0;
     conv[q] = !k.active;
     k.rho_old = k.alpha = k.omega = 1.0;
   }
   upload_sc(h, sc, s);
+  if (zero_rhs) {
+    masked_zero<double>(S, sc, x, s);
+    h->launches++;
+    for (int q = 0; q < ns; ++q) h->hsc[q].flag = 0;
+    upload_sc(h, sc, s);
+  }
   auto any_active = [&]() {
     for (int q = 0; q < ns; ++q)
       if (h->hsc[q].active) return true;
@@ -1476,12 +1500,13 @@ ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const in
   return DDPS_OK;
 }
 
-ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream) {
+static ddps_status factor_values(ddps_handle* h, const double* values, bool host, void* stream) {
   if (!h || !values) return DDPS_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   try {
     h->factored = false;
-    CK(cudaMemcpyAsync(h->vals, values, h->A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->vals, values, h->A.nnz * sizeof(double),
+                       host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     const int fp = h->opt.factor_prec, gp = h->opt.ghat_prec;
     if (fp == DDPS_FP64) {
       if (gp == DDPS_FP64)
@@ -1507,28 +1532,60 @@ ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream) {
   return DDPS_OK;
 }
 
-ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, void* stream,
-                       ddps_solve_info* info) {
-  if (!h || !f || !x) return DDPS_ERR_INVALID_ARG;
+ddps_status ddps_factor(ddps_handle* h, const double* values, void* stream) {
+  return factor_values(h, values, false, stream);
+}
+
+ddps_status ddps_factor_host(ddps_handle* h, const double* values_host, void* stream) {
+  return factor_values(h, values_host, true, stream);
+}
+
+// Folds the statistics of one right-hand side into those of the call.
+static void merge_info(ddps_solve_info* acc, const ddps_solve_info& one, bool first) {
+  if (first) {
+    *acc = one;
+    return;
+  }
+  acc->outer_iterations = std::max(acc->outer_iterations, one.outer_iterations);
+  acc->inner_iterations += one.inner_iterations;
+  acc->precond_applies += one.precond_applies;
+  acc->converged = acc->converged && one.converged;
+  acc->guess_used = acc->guess_used || one.guess_used;
+  acc->relres_inf = std::max(acc->relres_inf, one.relres_inf);
+}
+
+ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, int32_t nrhs, const double* x0,
+                       void* stream, ddps_solve_info* info) {
+  if (!h || !f || !x || nrhs < 1) return DDPS_ERR_INVALID_ARG;
   if (!h->factored) {
     h->err = "ddps_solve: call ddps_factor first";
     return DDPS_ERR_STATE;
   }
   auto t0 = std::chrono::steady_clock::now();
   try {
-    ddps_status st = solve_impl(h, f, x, as_stream(stream), info);
-    if (info)
+    const int64_t n = h->A.n;
+    ddps_status worst = DDPS_OK;
+    ddps_solve_info acc{}, one{};
+    for (int32_t j = 0; j < nrhs; ++j) {
+      ddps_status st = solve_impl(h, f + j * n, x + j * n, x0 ? x0 + j * n : nullptr,
+                                  as_stream(stream), &one);
+      merge_info(&acc, one, j == 0);
+      if (st != DDPS_OK) worst = st;
+    }
+    if (info) {
+      *info = acc;
       info->ms_solve =
           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return st;
+    }
+    return worst;
   } catch (const Fail& e) {
     return fail(h, e);
   }
 }
 
-ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, void* stream,
-                            ddps_solve_info* info) {
-  if (!h || !f_host || !x_host) return DDPS_ERR_INVALID_ARG;
+ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host, int32_t nrhs,
+                            const double* x0_host, void* stream, ddps_solve_info* info) {
+  if (!h || !f_host || !x_host || nrhs < 1) return DDPS_ERR_INVALID_ARG;
   if (!h->factored) {
     h->err = "ddps_solve_host: call ddps_factor first";
     return DDPS_ERR_STATE;
@@ -1536,15 +1593,27 @@ ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host
   cudaStream_t s = as_stream(stream);
   auto t0 = std::chrono::steady_clock::now();
   try {
-    const size_t bytes = h->A.n * sizeof(double);
-    CK(cudaMemcpyAsync(h->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
-    ddps_status st = solve_impl(h, h->io_f, h->io_x, s, info);
-    CK(cudaMemcpyAsync(x_host, h->io_x, bytes, cudaMemcpyDeviceToHost, s));
+    const int64_t n = h->A.n;
+    const size_t bytes = n * sizeof(double);
+    ddps_status worst = DDPS_OK;
+    ddps_solve_info acc{}, one{};
+    for (int32_t j = 0; j < nrhs; ++j) {
+      CK(cudaMemcpyAsync(h->io_f, f_host + j * n, bytes, cudaMemcpyHostToDevice, s));
+      if (x0_host) CK(cudaMemcpyAsync(h->io_x, x0_host + j * n, bytes, cudaMemcpyHostToDevice, s));
+      ddps_status st = solve_impl(h, h->io_f, h->io_x, x0_host ? h->io_x : nullptr, s, &one);
+      CK(cudaMemcpyAsync(x_host + j * n, h->io_x, bytes, cudaMemcpyDeviceToHost, s));
+      merge_info(&acc, one, j == 0);
+      if (st != DDPS_OK) worst = st;
+    }
     CK(cudaStreamSynchronize(s));
-    if (info)
+    if (info) {
+      *info = acc;
       info->ms_solve =
           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return st;
+    }
+    if (worst == DDPS_ERR_NOT_CONVERGED)
+      h->err = "outer BiCGStab did not reach tol_out within maxit_out for some right-hand side";
+    return worst;
   } catch (const Fail& e) {
     return fail(h, e);
   }
@@ -1861,36 +1930,59 @@ constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[256] = {};
+struct NoAllocAddr {
+  unsigned long long ctx_id = 0;  // unique id of the context the address belongs to
+  void* addr = nullptr;
+};
+NoAllocAddr g_noalloc_addr[256];
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device.  (In host code the symbol's name only stands in for the array.)
+// Unique id of the calling thread's current context (cuCtxGetId through the
+// runtime's driver entry point, so the library does not link libcuda);
+// 0 when it cannot be read.  Ids are never reused in a process, so a device
+// reset, which destroys the context and reloads the module in a new one,
+// changes the id and the array's address is looked up again.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)fn;
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)fn;
+    cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_noalloc_scratch in the current device's context,
+// looked up once per device and context.  (In host code the symbol's name
+// only stands in for the array.)
 void* noalloc_scratch_address() {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) throw Fail{DDPS_ERR_CUDA, "device ordinal out of range"};
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+  NoAllocAddr& e = g_noalloc_addr[dev];
+  if (!e.addr || id == 0 || e.ctx_id != id) {
     void* p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = p;
+    e.addr = p;
+    e.ctx_id = id;
   }
-  return g_noalloc_addr[dev];
-}
-
-template <typename T>
-void block_solve_scratch(ddps_handle* h, const double* y, double* g, cudaStream_t s, T* w, T* u) {
-  const Analysis& A = h->A;
-  const T* arena = (const T*)h->arena;
-  launch_permute_in<T>(y, h->perm, A.n, w, s);
-  for (int L = A.nlevels - 1; L >= 0; --L)
-    launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   h->split[L].max_m, arena, w, u, s);
-  for (int L = 0; L < A.nlevels; ++L)
-    launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   h->split[L].max_m, arena, w, s);
-  launch_permute_out<T>(w, h->perm, A.n, g, s);
-  h->launches += 2 + 2 * A.nlevels;
+  return e.addr;
 }
 
 template <typename T>
@@ -1907,7 +1999,7 @@ void block_solve_noalloc_impl(ddps_handle* h, const double* y, double* g, cudaSt
   // Every entry of both scratch vectors is written before it is read (the
   // permutation fills w, each front writes its update vector before its
   // parent reads it), so nothing has to be cleared between calls.
-  block_solve_scratch<T>(h, y, g, s, (T*)base, (T*)(base + wbytes));
+  block_solve_impl<T>(h, y, g, s, DDPS_PROF_BLOCK_SOLVE, (T*)base, (T*)(base + wbytes));
 }
 
 }  // namespace

@@ -694,9 +694,9 @@ void launch_tri_inverse_mc(DevFronts F, const int32_t* tile_front, const int32_t
                            T* inv, const int64_t* inv_off, cudaStream_t s) {
   if (ntiles <= 0) return;
   const size_t sm = sizeof(T) * ((size_t)IB * (NB + 1) + (size_t)NB * (IB + 1) + 2 * (size_t)IB * (IB + 1));
-  cudaFuncSetAttribute(k_tri_inverse_mc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  record_launch_error(cudaFuncSetAttribute(k_tri_inverse_mc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const size_t smd = sizeof(T) * 2 * (size_t)IB * (IB + 1);
-  cudaFuncSetAttribute(k_tri_inverse_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+  record_launch_error(cudaFuncSetAttribute(k_tri_inverse_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
   k_tri_inverse_diag<T><<<dim3(ntiles, 2), kThreads, smd, s>>>(F, tile_front, tile_cb, arena, inv,
                                                                 inv_off);
   k_tri_inverse_mc<T><<<dim3(ntiles, 2), kThreads, sm, s>>>(F, tile_front, tile_cb, arena, inv,
@@ -713,7 +713,7 @@ void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t
   if (nf <= 0) return;
   const size_t sm = ((size_t)max_m * max_m + 2 * (size_t)max_m) * sizeof(T);
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_front_lu_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    record_launch_error(cudaFuncSetAttribute(k_front_lu_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_front_lu_small<T><<<nf, kThreads, sm, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
 }
 

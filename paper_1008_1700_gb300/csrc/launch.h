@@ -12,6 +12,37 @@ namespace ddps {
 
 struct KScal;
 
+// SM count of the current device, cached per device ordinal (a process may
+// switch devices, and devices may differ).
+inline int device_sm_count() {
+  static int cache[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 1;
+  if (cache[dev] <= 0) {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+      nsm = 1;
+    cache[dev] = nsm;
+  }
+  return cache[dev];
+}
+
+// First failed launch-configuration call (attribute setting, extended
+// launch) of the calling thread since the last take_launch_error(); the C
+// ABI layer turns it into DDPS_ERR_CUDA after each sequence of launches.
+inline cudaError_t& launch_error_slot() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+inline void record_launch_error(cudaError_t e) {
+  if (e != cudaSuccess && launch_error_slot() == cudaSuccess) launch_error_slot() = e;
+}
+inline cudaError_t take_launch_error() {
+  const cudaError_t e = launch_error_slot();
+  launch_error_slot() = cudaSuccess;
+  return e;
+}
+
 // Multifrontal structure of all blocks, resident on the device.
 struct DevFronts {
   const int32_t* k;        // pivots per front

@@ -354,31 +354,56 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = lane; i < k; i += 32) w[row0 + i] = warp_row_dot(A + i, m, i, k, t);
 }
 
-// y = A x, CSR, four lanes per row.
-__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                       const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
-                       double* __restrict__ y) {
-  const int sub = threadIdx.x & 3;
-  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2; row < n;
-       row += ((int64_t)gridDim.x * blockDim.x) >> 2) {
-    double s = 0.0;
-    for (int32_t e = rowptr[row] + sub; e < rowptr[row + 1]; e += 4) s += vals[e] * x[colind[e]];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (sub == 0) y[row] = s;
-  }
-}
+// CSR product streamed by row blocks: y = A x (SUB 0) or y = b - A x (SUB 1).
+// A CTA takes kStreamRows consecutive rows; their entries are contiguous,
+// [rowptr[r0], rowptr[r1]), and are read with coalesced loads (thread t the
+// entries t, t + NT, ...; four in flight), the products val * x[col] going
+// to shared memory; then thread t adds its row's products in order.  A row
+// block with more than kStreamCap entries is summed row by row from global
+// memory instead.  Used for the outer products with A (Fig. 2 step 6) and
+// the retrieval's y - R~ z^ (Fig. 3 6.4-6.5), whose R~ columns index z^.
+constexpr int kStreamRows = 256;
+constexpr int kStreamCap = 4096;
 
-// out = y - R~ zhat
-__global__ void k_rt_residual(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const double* __restrict__ val, int64_t n,
-                              const double* __restrict__ y, const double* __restrict__ zhat,
-                              double* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = y[i];
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s -= val[e] * zhat[col[e]];
-    out[i] = s;
+template <int SUB>
+__global__ void __launch_bounds__(kStreamRows)
+    k_csr_stream(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                 const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
+                 const double* __restrict__ b, double* __restrict__ y) {
+  __shared__ double prod[kStreamCap];
+  const int tid = threadIdx.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * kStreamRows; r0 < n;
+       r0 += (int64_t)gridDim.x * kStreamRows) {
+    const int64_t r1 = min(n, r0 + kStreamRows);
+    const int64_t row = r0 + tid;
+    const int32_t e0 = rowptr[r0], ne = rowptr[r1] - e0;
+    int32_t ra = 0, rb = 0;
+    if (row < r1) {
+      ra = rowptr[row];
+      rb = rowptr[row + 1];
+    }
+    double s = 0.0;
+    if (ne <= kStreamCap) {
+      int e = tid;
+      for (; e + 3 * kStreamRows < ne; e += 4 * kStreamRows) {
+        int32_t c[4];
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          c[q] = colind[e0 + e + q * kStreamRows];
+          v[q] = vals[e0 + e + q * kStreamRows];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) prod[e + q * kStreamRows] = v[q] * x[c[q]];
+      }
+      for (; e < ne; e += kStreamRows) prod[e] = vals[e0 + e] * x[colind[e0 + e]];
+      __syncthreads();
+      for (int32_t j = ra - e0; j < rb - e0; ++j) s += prod[j];
+      __syncthreads();
+    } else {
+      for (int32_t j = ra; j < rb; ++j) s += vals[j] * x[colind[j]];
+    }
+    if (row < r1) y[row] = SUB ? b[row] - s : s;
   }
 }
 
@@ -637,16 +662,7 @@ void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, c
   k_permute_out<T><<<grid_for(n, kThreads), kThreads, 0, s>>>(w, perm, n, g);
 }
 
-static int sm_count() {
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
-  return nsm;
-}
+static int sm_count() { return device_sm_count(); }
 
 // One launch per depth of the elimination forest, 256 threads per front.
 // Levels with more fronts than two per SM keep eight loads in flight per
@@ -655,7 +671,9 @@ static int sm_count() {
 // and sixteen loads per lane.
 template <typename K, typename... Args>
 static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t s, Args... args) {
-  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (sm > 48 * 1024)
+    record_launch_error(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nf * c));
   cfg.blockDim = dim3(kThreads);
@@ -670,7 +688,7 @@ static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t 
   at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 2;
-  cudaLaunchKernelEx(&cfg, kern, args...);
+  record_launch_error(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 // Fronts of 1024 rows or more always take a full cluster: one CTA cannot
 // stream their blocks fast enough, however many fronts share the depth.
@@ -732,14 +750,17 @@ void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
 
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
                  const double* x, double* y, cudaStream_t s) {
-  k_spmv<<<grid_for(n * 4, kThreads), kThreads, 0, s>>>(rowptr, colind, vals, n, x, y);
+  if (n <= 0) return;
+  k_csr_stream<0><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(rowptr, colind, vals,
+                                                                             n, x, nullptr, y);
 }
 
 void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
                         int64_t n, const double* y, const double* zhat, double* out,
                         cudaStream_t s) {
-  k_rt_residual<<<grid_for(n, kThreads), kThreads, 0, s>>>(rt_rowptr, rt_col, rt_val, n, y, zhat,
-                                                            out);
+  if (n <= 0) return;
+  k_csr_stream<1><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(
+      rt_rowptr, rt_col, rt_val, n, zhat, y, out);
 }
 
 template <typename TI>
@@ -782,8 +803,8 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
   using AT = typename Acc<TG>::type;
   const size_t sm = (size_t)std::max<int64_t>(max_cols, 1) * sizeof(AT);
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_ghat_matvec_tiled<TG, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+    record_launch_error(cudaFuncSetAttribute(k_ghat_matvec_tiled<TG, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm));
   k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, gq0, gq1,
                                                        gcol_ptr, ghat_off, gld, gcols, v, w, sc,
                                                        block_sys);

@@ -1133,13 +1133,8 @@ void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t
   auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NMMA, C::NPROD>;
   constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
                         (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2;
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  }
+  const int nsm = device_sm_count();
+  record_launch_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const int32_t nct = (NR + TC_BN - 1) / TC_BN;
   const int32_t nitems = nfr * nct;
   const int32_t grid = std::min(nitems, nsm);
@@ -1177,8 +1172,8 @@ void launch_one(DevFronts F, const int32_t* tile_front, const int32_t* tile_m0,
                 long long* err, int inject, cudaStream_t s) {
   constexpr uint32_t stage = 2 * (PASSES == 3 ? 2u : 1u) * TC_TILE_BYTES;
   const size_t sm = 2 * stage;
-  cudaFuncSetAttribute(k_spike_gemm_tc<OP, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sm);
+  record_launch_error(cudaFuncSetAttribute(k_spike_gemm_tc<OP, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm));
   dim3 grid(ntiles, (NR + TC_BN - 1) / TC_BN);
   k_spike_gemm_tc<OP, PASSES><<<grid, TC_THREADS, sm, s>>>(F, tile_front, tile_m0, tile_aoff, atc,
                                                             block_ncols, j0, NR, X, Tb, err, inject);
@@ -1247,7 +1242,7 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
   const size_t sm = (size_t)std::max(max_k, 1) * (TC_BK + 1) * sizeof(float);
   dim3 grid(nfr, max_kb);
 #define DDPS_WPACK(D, P)                                                                        \
-  cudaFuncSetAttribute(k_w_pack<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+  record_launch_error(cudaFuncSetAttribute(k_w_pack<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));   \
   k_w_pack<D, P><<<grid, TC_THREADS, sm, s>>>(F, fronts, woff, arena, wpk);
   if (bwd) {
     if (passes == 3) {
@@ -1293,7 +1288,7 @@ void launch_lu_update_tc(DevFronts F, const int32_t* tile_front, const int32_t* 
                          int32_t ntiles, int32_t j0, float* arena, long long* err, cudaStream_t s) {
   if (ntiles <= 0) return;
   const size_t sm = 2 * 4 * (size_t)TC_TILE_BYTES;  // two stages of L and U, high and low parts
-  cudaFuncSetAttribute(k_lu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  record_launch_error(cudaFuncSetAttribute(k_lu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_lu_update_tc<<<ntiles, TC_THREADS, sm, s>>>(F, tile_front, tile_ij, j0, arena, err);
 }
 int64_t tc_a_block_bytes(int passes) { return (passes == 3 ? 2 : 1) * (int64_t)TC_TILE_BYTES; }

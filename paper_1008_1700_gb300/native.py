@@ -81,8 +81,9 @@ def load():
         "ddps_analyze": (_i32, [_i64, _i64, _p, _p, _i32, _p, _i32, _p, _p,
                                 C.POINTER(ddps_options), C.POINTER(_p)]),
         "ddps_factor": (_i32, [_p, _p, _p]),
-        "ddps_solve": (_i32, [_p, _p, _p, _p, C.POINTER(ddps_solve_info)]),
-        "ddps_solve_host": (_i32, [_p, _p, _p, _p, C.POINTER(ddps_solve_info)]),
+        "ddps_factor_host": (_i32, [_p, _p, _p]),
+        "ddps_solve": (_i32, [_p, _p, _p, _i32, _p, _p, C.POINTER(ddps_solve_info)]),
+        "ddps_solve_host": (_i32, [_p, _p, _p, _i32, _p, _p, C.POINTER(ddps_solve_info)]),
         "ddps_set_reduced_guess": (_i32, [_p, _p, _p]),
         "ddps_get_reduced_solution": (_i32, [_p, _p, _p, _p]),
         "ddps_block_solve": (_i32, [_p, _p, _p, _p]),
@@ -216,17 +217,31 @@ def ddps_factor(h, values, stream=None):
     _check(load().ddps_factor(h, _ptr(values), _stream(stream)), h)
 
 
-def ddps_solve(h, f, x, stream=None, check=True):
+def ddps_factor_host(h, values, stream=None):
+    """ddps_factor with the values in host memory (a NumPy array or a CPU tensor)."""
+    _check(load().ddps_factor_host(h, _ptr(values), _stream(stream)), h)
+
+
+def _nrhs(f):
+    shape = tuple(f.shape)
+    return 1 if len(shape) == 1 else int(shape[0])
+
+
+def ddps_solve(h, f, x, x0=None, stream=None, check=True):
+    """f, x (and x0): device tensors of shape (n,) or (nrhs, n)."""
     info = ddps_solve_info()
-    st = load().ddps_solve(h, _ptr(f), _ptr(x), _stream(stream), C.byref(info))
+    st = load().ddps_solve(h, _ptr(f), _ptr(x), _nrhs(f), _ptr(x0), _stream(stream),
+                           C.byref(info))
     if check and st not in (0, 3):
         _check(st, h)
     return st, info.as_dict()
 
 
-def ddps_solve_host(h, f, x, stream=None):
+def ddps_solve_host(h, f, x, x0=None, stream=None):
+    """f, x (and x0): host arrays of shape (n,) or (nrhs, n)."""
     info = ddps_solve_info()
-    st = load().ddps_solve_host(h, _ptr(f), _ptr(x), _stream(stream), C.byref(info))
+    st = load().ddps_solve_host(h, _ptr(f), _ptr(x), _nrhs(f), _ptr(x0), _stream(stream),
+                                C.byref(info))
     if st not in (0, 3):
         _check(st, h)
     return st, info.as_dict()

@@ -60,20 +60,31 @@ class Solver:
         return s
 
     def factor(self, values):
-        N.ddps_factor(self.h, values)
+        """Fig. 2 steps 1-5 with new values: a CUDA tensor, or host memory (a
+        NumPy array or a CPU tensor), which is copied through the C ABI."""
+        if isinstance(values, np.ndarray) or not getattr(values, "is_cuda", False):
+            N.ddps_factor_host(self.h, np.ascontiguousarray(values, dtype=np.float64)
+                               if isinstance(values, np.ndarray) else values)
+        else:
+            N.ddps_factor(self.h, values)
 
-    def solve(self, f, x=None):
+    def solve(self, f, x=None, x0=None):
+        """f: CUDA tensor (n,) or (nrhs, n); x0: initial guesses of the same
+        shape or None (x0 = 0)."""
         import torch
         if x is None:
             x = torch.empty_like(f)
-        st, info = N.ddps_solve(self.h, f, x)
+        st, info = N.ddps_solve(self.h, f, x, x0)
         info["status"] = N.STATUS[st]
         return x, info
 
-    def solve_host(self, f):
+    def solve_host(self, f, x0=None, x=None):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        x = np.empty_like(f)
-        st, info = N.ddps_solve_host(self.h, f, x)
+        if x is None:
+            x = np.empty_like(f)
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        st, info = N.ddps_solve_host(self.h, f, x, x0)
         info["status"] = N.STATUS[st]
         return x, info
 

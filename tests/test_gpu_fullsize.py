@@ -1,14 +1,20 @@
 """Parity at the full workload sizes, in the configuration bench.py times
-(FP32 factors, bf16x3 tensor-core spike products, FP16 G^, FP64 outer):
-properties that hold at any size (recomputed residual, error against the
-known solution) for every system, and sampled outputs the oracle computes one
-at a time (spike columns G_i(:, k) = A_ii^-1 R~_i(:, k) restricted to the rows
-in c, and whole systems of the batch)."""
+(its ``form_options("mixed")``: FP32 factors, bf16x3 tensor-core spike
+products and LU block updates, FP16 G^, FP64 outer): the oracle's solution
+x = A^-1 f (stored by tests/golden/make_fullsize_reference.py as norms and
+sampled entries), properties that hold at any size (recomputed residual,
+error against the known solution) for every system, and sampled outputs the
+oracle computes one at a time (spike columns G_i(:, k) = A_ii^-1 R~_i(:, k)
+restricted to the rows in c, and whole systems of the batch)."""
+
+import json
+import os
 
 import numpy as np
 import pytest
 import torch
 
+import bench
 import workloads as W
 from gpu_helpers import dev, host, relerr
 from oracle.ddps_oracle import DDPSOracle, csr
@@ -16,8 +22,23 @@ from paper_1008_1700_gb300 import Solver, native as N
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-BENCH_FORM = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
-                  inner_prec=N.DDPS_FP32, tol_out=1e-10, tol_in=1e-4, maxit_in=100)
+# exactly the options bench.py times (tolerances included)
+BENCH_FORM = bench.form_options("mixed")
+
+_REF = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                    "fullsize_reference.json")
+
+
+def _check_against_oracle_x(name, x, bound=1e-8):
+    """x against the oracle's stored solution: relative error of the sampled
+    entries and of the 2-norm."""
+    with open(_REF) as fh:
+        ref = json.load(fh)[name]
+    assert len(x) == ref["n"]
+    idx = np.asarray(ref["idx"])
+    xr = np.asarray(ref["x"])
+    assert relerr(x[idx], xr) <= bound, name
+    assert abs(np.linalg.norm(x) - ref["norm2"]) <= bound * ref["norm2"], name
 
 
 def _check_sampled_spikes(S, P, o, blocks, ncols, rng, tol):
@@ -49,6 +70,7 @@ def test_cd3d_64_slabs16_bench_configuration():
     rr = np.max(np.abs(P.f - A @ x)) / np.max(np.abs(P.f))
     assert info["status"] == "DDPS_OK" and rr <= 1e-10
     assert relerr(x, P.x_true) <= 1e-8
+    _check_against_oracle_x("cd3d_64_slabs16", x)
     o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, spikes=False)
     _check_sampled_spikes(S, P, o, blocks=(0, 7, 15), ncols=4, rng=np.random.default_rng(0),
                           tol=2e-3)  # FP16 storage of G^
@@ -64,6 +86,7 @@ def test_cd3d_64_slabs16_plain_fp64():
     assert info["status"] == "DDPS_OK"
     assert np.max(np.abs(P.f - A @ x)) / np.max(np.abs(P.f)) <= 1e-12
     assert relerr(x, P.x_true) <= 1e-9
+    _check_against_oracle_x("cd3d_64_slabs16", x, bound=1e-9)
     o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, spikes=False)
     _check_sampled_spikes(S, P, o, blocks=(3, 12), ncols=3, rng=np.random.default_rng(1), tol=1e-10)
     S.close()
@@ -97,6 +120,7 @@ def test_cd3d_48_time_steps(t):
     A = csr(P.n, P.rowptr, P.colind, P.values)
     assert info["status"] == "DDPS_OK"
     assert np.max(np.abs(P.f - A @ x)) / np.max(np.abs(P.f)) <= 1e-10
+    _check_against_oracle_x(f"cd3d_48_t{t}", x)
     o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, spikes=False)
     _check_sampled_spikes(S, P, o, blocks=(0, 4, 7), ncols=3, rng=np.random.default_rng(t), tol=2e-3)
     z, g = S.reduced_solution()
@@ -113,7 +137,7 @@ def test_random_band_1m_dropping():
     from oracle.ddps_oracle import drop_entries, factor_blocks, interface_columns, split_block_rows
     P = W.cfg4()
     S = Solver(P.rowptr, P.colind, P.block_ptr, values_host=P.values,
-               drop_mode=N.DDPS_DROP_ABS, drop_tol=1e-4, **BENCH_FORM)
+               **dict(BENCH_FORM, drop_mode=N.DDPS_DROP_ABS, drop_tol=1e-4))
     S.factor(dev(P.values))
     x, info = S.solve(dev(P.f))
     x = host(x)
@@ -121,6 +145,7 @@ def test_random_band_1m_dropping():
     assert info["status"] == "DDPS_OK"
     assert np.max(np.abs(P.f - A @ x)) / np.max(np.abs(P.f)) <= 1e-10
     assert relerr(x, P.x_true) <= 1e-8
+    _check_against_oracle_x("randband_1m", x)
     D, R = split_block_rows(A, P.block_ptr)
     Rt = drop_entries(R, 1e-4)
     c = interface_columns(Rt)

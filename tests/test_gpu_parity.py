@@ -30,7 +30,12 @@ TC1 = dict(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16, ghat_prec=N.DDPS_BF1
 # tile products of each sweep), and with both kinds of fronts in one depth
 TC3_TILES = dict(TC3, fused_rows=-1)
 TC3_MIXED = dict(TC3, fused_rows=24)
-FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mixed": TC3_MIXED}
+# G^ stored in FP16 (FP32 accumulation), and the whole benched form: FP16 G^
+# with tensor-core spike products and tensor-core LU block updates
+TC3_F16 = dict(TC3, ghat_prec=N.DDPS_FP16)
+BENCH = dict(TC3_F16, update_prec=N.DDPS_BF16X3)
+FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mixed": TC3_MIXED,
+         "tc3_f16": TC3_F16, "bench": BENCH}
 # G^ applied without storing it: v + (D~^-1 R~ v)(c) by block solves
 IMPLICIT64 = dict(FP64, ghat_mode=N.DDPS_GHAT_IMPLICIT)
 IMPLICIT = dict(MIXED, ghat_mode=N.DDPS_GHAT_IMPLICIT)
@@ -111,8 +116,11 @@ def test_precond_apply_direct_mode(case):
     assert relerr(z, zo) <= 1e-9
 
 
+# FP16 storage rounds every entry to 11 significant bits (relative 2^-11 =
+# 4.9e-4 of the entry, at most that of the block's largest entry)
 @pytest.mark.parametrize("form,bound", [("mixed", 2e-6), ("tc3", 1e-4), ("tc1", 3e-2),
-                                        ("tc3_tiles", 1e-4), ("tc3_mixed", 1e-4)])
+                                        ("tc3_tiles", 1e-4), ("tc3_mixed", 1e-4),
+                                        ("tc3_f16", 6e-4), ("bench", 6e-4)])
 def test_ghat_precision_forms(case, form, bound):
     """G^ formed with FP32 factors: SIMT FP32 products, bf16x3 and bf16 tensor-core
     products (fused front GEMMs, tile products, or both); each within its
@@ -143,11 +151,12 @@ def test_implicit_reduced_matvec(case, form, bound):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "tc3", "tc1", "implicit64",
-                                  "implicit"])
+                                  "implicit", "tc3_f16", "bench"])
 def test_full_solve_parity(case, prec):
     name, P, drop, o = case
     opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "tc3": TC3, "tc1": TC1,
-            "implicit64": IMPLICIT64, "implicit": IMPLICIT}[prec]
+            "implicit64": IMPLICIT64, "implicit": IMPLICIT, "tc3_f16": TC3_F16,
+            "bench": BENCH}[prec]
     S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **opts)
     x, info = S.solve(dev(P.f))
     assert info["status"] == "DDPS_OK", info
@@ -345,3 +354,44 @@ def test_bounded_wait_reports_timeout_and_context_survives(fused_rows):
     S2 = make_solver(P, tol_out=1e-12, tol_in=1e-8, **TC3)
     x, info = S2.solve(dev(P.f))
     assert info["status"] == "DDPS_OK" and info["relres_inf"] <= 1e-12
+
+
+def test_several_rhs_and_initial_guess():
+    """ddps_solve with nrhs right-hand sides (one after the other with the same
+    factors) and with initial guesses: each column matches the oracle; a guess
+    equal to the solution returns at once; a zero right-hand side gives x = 0
+    whatever the guess."""
+    P = W.small_convdiff_3d(12, [3, 5, 4])
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr)
+    S = make_solver(P, tol_out=1e-12, tol_in=1e-8, **MIXED)
+    rng = np.random.default_rng(21)
+    F = np.stack([P.f, rng.standard_normal(P.n), np.zeros(P.n)])
+    X, info = S.solve(dev(F))
+    assert info["status"] == "DDPS_OK"
+    X = host(X)
+    for j in range(2):
+        xo, _ = o.solve(F[j], tol=1e-12, eps_in=1e-8)
+        assert relerr(X[j], xo) <= 1e-8, j
+    assert np.all(X[2] == 0.0)
+    # the first column's solution as its guess: no iteration; a perturbed guess converges
+    X0 = np.stack([X[0], X[1] + 1e-3 * rng.standard_normal(P.n), rng.standard_normal(P.n)])
+    X2, info2 = S.solve(dev(F), x0=dev(X0))
+    X2 = host(X2)
+    assert info2["status"] == "DDPS_OK"
+    assert np.array_equal(X2[0], X[0])
+    assert relerr(X2[1], X[1]) <= 1e-9
+    assert np.all(X2[2] == 0.0)
+    # host buffers give the same as device buffers
+    Xh, infoh = S.solve_host(F)
+    assert infoh["status"] == "DDPS_OK" and np.array_equal(Xh, X)
+
+
+def test_factor_from_host_values():
+    """ddps_factor_host (values in host memory) factors exactly as ddps_factor."""
+    P = W.small_random_band(3000, 5, 200, seed=2)
+    S1 = make_solver(P, ("abs", 1e-4), **TCLU)
+    S2 = make_solver(P, ("abs", 1e-4), **TCLU)
+    S2.factor(np.asarray(P.values))
+    y = dev(np.random.default_rng(5).standard_normal(P.n))
+    assert np.array_equal(host(S1.block_solve(y)), host(S2.block_solve(y)))
+    assert np.array_equal(S1.ghat_block(2), S2.ghat_block(2))

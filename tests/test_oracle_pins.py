@@ -232,3 +232,23 @@ def test_cfg1_direct_agrees_with_global_lu():
     x_ref = spla.spsolve(o.A.tocsc(), P.f)
     assert info["iterations"] <= 1.0
     assert np.linalg.norm(x - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+
+
+def test_jacobi_reference_against_lapack_and_its_bound():
+    """jacobi_solution (the definition x = A^-1 f for strictly diagonally
+    dominant A): converged, it equals the LAPACK solve; stopped early, its
+    certified bound q/(1-q) ||x_k - x_(k-1)||_inf covers the true error."""
+    from oracle.ddps_oracle import jacobi_solution
+    P = W.small_random_band(400, 4, 30, seed=7)  # diagonal 1.2 x the off-diagonal row sum
+    A = _dense(P)
+    x_ref = np.linalg.solve(A, P.f)
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, spikes=False)
+    x, bound = jacobi_solution(o.A, P.f)
+    assert np.max(np.abs(x - x_ref)) <= 1e-13 * np.max(np.abs(x_ref))
+    for tol in (1e-3, 1e-6):
+        xk, bk = jacobi_solution(o.A, P.f, tol=tol)
+        err = np.max(np.abs(xk - x_ref))
+        assert err <= bk and bk <= tol * np.max(np.abs(xk))
+        assert err > 1e-3 * bk  # the bound is not vacuous
+    with pytest.raises(ValueError):
+        jacobi_solution(o.A - 2.0 * sp.diags(o.A.diagonal()) * 0.8, P.f)

@@ -69,8 +69,11 @@ def test_reference_arm_line_keeps_the_contract(capsys, monkeypatch):
 
     import bench
     monkeypatch.setenv("RANK", "0")
-    args = argparse.Namespace(workload="cd2d_64_p4", steps=1, warmup=0, gpus=1, impl="reference")
+    import time
+    args = argparse.Namespace(workload="cd2d_64_p4", steps=2, warmup=0, gpus=1, impl="reference")
+    t0 = time.perf_counter()
     bench.run_reference(args)
+    wall = time.perf_counter() - t0
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -81,3 +84,6 @@ def test_reference_arm_line_keeps_the_contract(capsys, monkeypatch):
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the steps' reported time is time the run really spent, and one thread ran it
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= wall
+    assert d["cpu_baseline"]["cores"] == 1
