@@ -72,6 +72,16 @@ typedef enum { DDPS_DROP_NONE = 0, DDPS_DROP_COLUMN = 1, DDPS_DROP_ABS = 2 } ddp
  * and G^ v = v + (D~^-1 (R~ v))(c) is computed with one R~ product and one
  * block solve (the kernels of 6.1) per inner product. */
 typedef enum { DDPS_GHAT_EXPLICIT = 0, DDPS_GHAT_IMPLICIT = 1 } ddps_ghat_mode;
+/* How Fig. 3 step 6.3 solves G^ z^ = g^ ("directly or iteratively").
+ * ITERATIVE: unpreconditioned BiCGStab to tol_in (Sec. 4 settings), the
+ * paper's choice in its experiments.
+ * DIRECT: for partitions whose blocks form chains (every coupling column of
+ * a block lies in the block before or after it in the same system, as for
+ * z-slabs or grid-line blocks), G^ is block tridiagonal with identity
+ * diagonal blocks; the factor phase forms its block LU (FP32) and every
+ * application solves with it: no inner iterations (Sec. 3 direct mode when
+ * nothing is dropped). */
+typedef enum { DDPS_REDUCED_ITERATIVE = 0, DDPS_REDUCED_DIRECT = 1 } ddps_reduced_solver;
 
 typedef struct {
   int32_t drop_mode;      /* ddps_drop_mode */
@@ -107,6 +117,8 @@ typedef struct {
                              BF16X3 = with FP32 factors, blocks of 256 pivots whose update of
                              the rest of the front runs on the tensor cores (bf16 high part and
                              remainder, fp32 accumulation, about 16 correct bits per product) */
+  int32_t reduced_solver; /* ddps_reduced_solver; DIRECT needs an explicit G^ (ghat_mode 0) and
+                             a chain partition, else ddps_analyze returns DDPS_ERR_INVALID_ARG */
 } ddps_options;
 
 typedef struct {
@@ -133,6 +145,8 @@ typedef struct {
   int64_t device_bytes;      /* device memory held by the handle */
   double factor_flops;       /* partial-LU flops of all fronts */
   double spike_flops;        /* multi-RHS forward/backward flops for G^ */
+  double direct_flops;       /* reduced_solver DIRECT: flops of the block LU of G^ per factor */
+  int64_t direct_bytes;      /* reduced_solver DIRECT: FP32 matrix bytes one reduced solve reads */
 } ddps_sizes;
 
 /* Fills *opt with the paper's solver settings (Sec. 4: eps_in 1e-4, 100 inner
@@ -242,6 +256,12 @@ ddps_status ddps_reduced_rhs(ddps_handle* h, const double* y, double* ghat, void
  * with ghat_mode IMPLICIT it is computed as v + (D~^-1 (R~ v))(c). */
 ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void* stream);
 
+/* Fig. 3 step 6.3 alone: z^ = G^-1 g^ with the handle's reduced solver
+ * (device float64[m] in/out, c order): DIRECT solves with the block LU of
+ * the factor phase; ITERATIVE runs the inner BiCGStab to tol_in from z^ = 0
+ * (synchronising `stream` between inner iterations). */
+ddps_status ddps_reduced_solve(ddps_handle* h, const double* ghat, double* zhat, void* stream);
+
 /* Fig. 3 in full: z = P^-1 y (device float64[n] in/out).  Runs the inner
  * solve from z^ = 0; synchronises `stream` between inner iterations. */
 ddps_status ddps_precond_apply(ddps_handle* h, const double* y, double* z, void* stream);
@@ -284,7 +304,9 @@ enum {
   DDPS_PROF_BLOCK_SOLVE = 6,   /* g = D~^-1 y (6.1 and the retrieval) */
   DDPS_PROF_GHAT_MATVEC = 7,   /* w = G^ v (6.3) */
   DDPS_PROF_SPMV = 8,          /* y = A x (outer Krylov) */
-  DDPS_PROF_CLASSES = 9
+  DDPS_PROF_DIRECT_FACTOR = 9, /* block LU of G^ (reduced_solver DIRECT) */
+  DDPS_PROF_DIRECT_SOLVE = 10, /* z^ = G^-1 g^ with that LU (reduced_solver DIRECT) */
+  DDPS_PROF_CLASSES = 11
 };
 
 /* Enables CUDA-event timing of the kernel classes whose bit (1 << class) is

@@ -23,7 +23,8 @@ LIB = os.path.join(BUILD, "libddps.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["analyze.cpp", "api.cu", "factor.cu", "spike.cu", "spike_tc.cu", "solve.cu", "krylov.cu", "mlp.cu"]
+SOURCES = ["analyze.cpp", "api.cu", "factor.cu", "spike.cu", "spike_tc.cu", "solve.cu", "krylov.cu",
+           "mlp.cu", "reduced_direct.cu"]
 
 
 def _nvcc() -> str:

@@ -19,6 +19,7 @@
 #include "ddps_internal.h"
 #include "krylov.h"
 #include "launch.h"
+#include "reduced_direct.h"
 
 using namespace ddps;
 
@@ -198,6 +199,9 @@ struct ddps_handle {
   std::vector<ProfRec> prof_recs;
   double prof_ms[DDPS_PROF_CLASSES] = {};
   int64_t prof_cnt[DDPS_PROF_CLASSES] = {};
+  // direct solve of the reduced system (reduced_solver DIRECT)
+  DirectPlan direct;
+  bool use_direct = false;
   // statistics of the current solve
   int64_t stat_inner = 0, stat_precond = 0;
   double stat_first_inner = 0;
@@ -482,6 +486,10 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
       h->launches++;
     }
   }
+  if (h->use_direct) {
+    Prof pr(h, DDPS_PROF_DIRECT_FACTOR, s);
+    h->launches += direct_factor<TG>(h->direct, (const TG*)h->ghat, s);
+  }
   check_launch();
   CK(cudaMemcpyAsync(h->herr, h->derr, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -713,7 +721,13 @@ void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, b
   launch_gather(h->pc_g, h->c, m, h->pc_ghat, s);                        // 6.2
   h->launches++;
   const double* z0 = (first && h->has_guess) ? h->guess : nullptr;
-  const double its = inner_dispatch(h, h->pc_ghat, h->pc_zhat, z0, s);  // 6.3
+  double its = 0;
+  if (h->use_direct) {  // 6.3 by the block LU of G^
+    Prof pr(h, DDPS_PROF_DIRECT_SOLVE, s);
+    h->launches += direct_solve(h->direct, h->pc_ghat, h->pc_zhat, s);
+  } else {
+    its = inner_dispatch(h, h->pc_ghat, h->pc_zhat, z0, s);  // 6.3
+  }
   h->stat_inner += (int64_t)std::ceil(its);
   if (first) {
     h->stat_first_inner = its;
@@ -1379,6 +1393,27 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   CK(cudaMallocHost((void**)&h->hstage, sizeof(KScal) * h->nseg * kStageSlots));
   h->hsc = h->hsc_out;
   h->partial = dalloc<double>(h, 3 * (int64_t)std::max(h->Sn.nchunks, h->Sm.nchunks) + 3);
+  if (h->opt.reduced_solver == DDPS_REDUCED_DIRECT && m > 0) {
+    std::vector<int32_t> gcols_panel(A.gcols.size());
+    for (int32_t b = 0; b < A.p; ++b)
+      for (int64_t pc = A.gcol_ptr[b]; pc < A.gcol_ptr[b + 1]; ++pc)
+        gcols_panel[pc] = A.gcols[A.gcol_ptr[b] + h->gperm[pc]];
+    DirectInput in;
+    in.p = A.p;
+    in.m = m;
+    in.gq0 = A.gq0.data();
+    in.gq1 = A.gq1.data();
+    in.gcol_ptr = A.gcol_ptr.data();
+    in.gcols_panel = gcols_panel.data();
+    in.ghat_off = A.ghat_off.data();
+    in.gld = A.gld.data();
+    in.block_sys = A.block_sys.data();
+    auto alloc = [h](int64_t bytes) { return dalloc_bytes(h, bytes); };
+    const std::string e = plan_direct(in, h->direct, alloc);
+    if (!e.empty()) throw Fail{DDPS_ERR_INVALID_ARG, "ddps_analyze: " + e};
+    upload_direct(h->direct, alloc);
+    h->use_direct = true;
+  }
 }
 
 bool valid_options(const ddps_options& o, std::string& why) {
@@ -1393,6 +1428,14 @@ bool valid_options(const ddps_options& o, std::string& why) {
   }
   if (o.inner_prec != DDPS_FP64 && o.inner_prec != DDPS_FP32) {
     why = "inner_prec must be FP64 or FP32";
+    return false;
+  }
+  if (o.reduced_solver != DDPS_REDUCED_ITERATIVE && o.reduced_solver != DDPS_REDUCED_DIRECT) {
+    why = "reduced_solver must be ITERATIVE or DIRECT";
+    return false;
+  }
+  if (o.reduced_solver == DDPS_REDUCED_DIRECT && o.ghat_mode != DDPS_GHAT_EXPLICIT) {
+    why = "reduced_solver DIRECT needs the stored G^ (ghat_mode EXPLICIT)";
     return false;
   }
   if (o.ghat_prec == DDPS_FP64 && o.inner_prec != DDPS_FP64) {
@@ -1702,6 +1745,26 @@ ddps_status ddps_reduced_matvec(ddps_handle* h, const double* v, double* w, void
   return DDPS_OK;
 }
 
+ddps_status ddps_reduced_solve(ddps_handle* h, const double* ghat, double* zhat, void* stream) {
+  if (!h || (!h->A.c.empty() && (!ghat || !zhat))) return DDPS_ERR_INVALID_ARG;
+  if (!h->factored) return DDPS_ERR_STATE;
+  try {
+    cudaStream_t s = as_stream(stream);
+    if (h->A.c.empty()) return DDPS_OK;
+    if (h->use_direct) {
+      Prof pr(h, DDPS_PROF_DIRECT_SOLVE, s);
+      h->launches += direct_solve(h->direct, ghat, zhat, s);
+    } else {
+      h->stat_inner = 0;
+      inner_dispatch(h, ghat, zhat, nullptr, s);
+    }
+    check_launch();
+  } catch (const Fail& e) {
+    return fail(h, e);
+  }
+  return DDPS_OK;
+}
+
 ddps_status ddps_precond_apply(ddps_handle* h, const double* y, double* z, void* stream) {
   if (!h || !y || !z) return DDPS_ERR_INVALID_ARG;
   if (!h->factored) return DDPS_ERR_STATE;
@@ -1747,6 +1810,8 @@ ddps_status ddps_get_sizes(const ddps_handle* h, ddps_sizes* s) {
   s->device_bytes = h->bytes;
   s->factor_flops = A.factor_flops;
   s->spike_flops = A.spike_flops;
+  s->direct_flops = h->use_direct ? h->direct.factor_flops : 0.0;
+  s->direct_bytes = h->use_direct ? h->direct.solve_bytes : 0;
   return DDPS_OK;
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libddps.so")
 DDPS_FP64, DDPS_FP32, DDPS_BF16, DDPS_BF16X3, DDPS_FP16 = 0, 1, 2, 3, 4
 DDPS_DROP_NONE, DDPS_DROP_COLUMN, DDPS_DROP_ABS = 0, 1, 2
 DDPS_GHAT_EXPLICIT, DDPS_GHAT_IMPLICIT = 0, 1
+DDPS_REDUCED_ITERATIVE, DDPS_REDUCED_DIRECT = 0, 1
 STATUS = {0: "DDPS_OK", 1: "DDPS_ERR_INVALID_ARG", 2: "DDPS_ERR_SINGULAR_BLOCK",
           3: "DDPS_ERR_NOT_CONVERGED", 4: "DDPS_ERR_OUT_OF_MEMORY", 5: "DDPS_ERR_CUDA",
           6: "DDPS_ERR_TIMEOUT", 7: "DDPS_ERR_STATE"}
@@ -33,7 +34,8 @@ class ddps_options(C.Structure):
                 ("pivot_tol", C.c_double), ("leaf_size", C.c_int32),
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
                 ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
-                ("ghat_mode", C.c_int32), ("update_prec", C.c_int32)]
+                ("ghat_mode", C.c_int32), ("update_prec", C.c_int32),
+                ("reduced_solver", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):
@@ -50,7 +52,8 @@ class ddps_sizes(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("n", "nnz", "nsys", "nblocks", "m", "nnz_rt", "nfronts",
                                           "nlevels", "factor_entries", "factor_lu_entries",
                                           "ghat_entries", "max_front", "max_rhs", "device_bytes")] + \
-               [("factor_flops", C.c_double), ("spike_flops", C.c_double)]
+               [("factor_flops", C.c_double), ("spike_flops", C.c_double),
+                ("direct_flops", C.c_double), ("direct_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +93,7 @@ def load():
         "ddps_block_solve_noalloc": (_i32, [_p, _p, _p, _p]),
         "ddps_reduced_matvec": (_i32, [_p, _p, _p, _p]),
         "ddps_reduced_rhs": (_i32, [_p, _p, _p, _p]),
+        "ddps_reduced_solve": (_i32, [_p, _p, _p, _p]),
         "ddps_precond_apply": (_i32, [_p, _p, _p, _p]),
         "ddps_spmv": (_i32, [_p, _p, _p, _p]),
         "ddps_get_sizes": (_i32, [_p, C.POINTER(ddps_sizes)]),
@@ -272,6 +276,10 @@ def ddps_reduced_matvec(h, v, w, stream=None):
     _check(load().ddps_reduced_matvec(h, _ptr(v), _ptr(w), _stream(stream)), h)
 
 
+def ddps_reduced_solve(h, ghat, zhat, stream=None):
+    _check(load().ddps_reduced_solve(h, _ptr(ghat), _ptr(zhat), _stream(stream)), h)
+
+
 def ddps_precond_apply(h, y, z, stream=None):
     _check(load().ddps_precond_apply(h, _ptr(y), _ptr(z), _stream(stream)), h)
 
@@ -313,7 +321,7 @@ def ddps_launch_count(h):
 
 
 PROF_CLASSES = ["assemble", "extend_add", "front_lu", "spike_fwd", "spike_bwd", "ghat_extract",
-                "block_solve", "ghat_matvec", "spmv"]
+                "block_solve", "ghat_matvec", "spmv", "direct_factor", "direct_solve"]
 
 
 def ddps_set_profiling(h, mask):

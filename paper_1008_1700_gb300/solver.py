@@ -106,6 +106,12 @@ class Solver:
         N.ddps_reduced_matvec(self.h, v, w)
         return w
 
+    def reduced_solve(self, ghat):
+        import torch
+        z = torch.empty_like(ghat)
+        N.ddps_reduced_solve(self.h, ghat, z)
+        return z
+
     def precond_apply(self, y):
         import torch
         z = torch.empty_like(y)
