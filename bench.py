@@ -71,7 +71,8 @@ def parse_args():
     ap.add_argument("--workload", default="cd3d_64_slabs16",
                     choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8", "cd2d_batch256",
                              "randband_1m", "cd3d_48_seq"])
-    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64", "implicit"], default="mixed",
+    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64", "implicit", "direct"],
+                    default="mixed",
                     help="mixed: the paper's method with FP32 factors, tensor-core spikes and "
                          "FP16 G^; implicit: the variant that applies G^ by block solves "
                          "instead of forming the spikes")
@@ -131,6 +132,12 @@ def form_options(form):
         # accumulation, FP32 inner vectors, FP64 outer
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
                     inner_prec=N.DDPS_FP32, update_prec=N.DDPS_BF16X3)
+    elif form == "direct":
+        # the mixed form with 6.3 solved directly (block LU of the block-tridiagonal
+        # G^ of a chain of slabs) instead of by the inner BiCGStab
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
+                    inner_prec=N.DDPS_FP32, update_prec=N.DDPS_BF16X3,
+                    reduced_solver=N.DDPS_REDUCED_DIRECT)
     elif form == "implicit":
         # variant (departs from Fig. 2 step 4): no spikes, G^ v = v + (D~^-1 R~ v)(c)
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
@@ -227,7 +234,7 @@ TRAFFIC_RATIO = {"ghat_matvec": (1.012, "ncu --set full, k_ghat_matvec_tiled<__h
 def algorithmic_work(sizes, P, form, steps, prof):
     """Per class: (kind, total algorithmic amount over the timed region)."""
     sf = 8 if form == "fp64" else 4
-    sg = 8 if form == "fp64" else (2 if form == "mixed" else 4)  # G^ storage
+    sg = 8 if form == "fp64" else (2 if form in ("mixed", "direct") else 4)  # G^ storage
     si = sf
     n, nnz, m = sizes["n"], sizes["nnz"], sizes["m"]
     out = {}
@@ -248,6 +255,8 @@ def algorithmic_work(sizes, P, form, steps, prof):
     else:
         out["ghat_matvec"] = ("bytes", (sizes["ghat_entries"] * sg + 2 * m * si) * calls["ghat_matvec"])
     out["spmv"] = ("bytes", (nnz * 12 + (n + 1) * 4 + n * 16) * calls["spmv"])
+    out["direct_factor"] = ("flops", sizes.get("direct_flops", 0.0) * steps)
+    out["direct_solve"] = ("bytes", (sizes.get("direct_bytes", 0) + m * 24) * calls.get("direct_solve", 0))
     return out
 
 
@@ -338,9 +347,10 @@ def oracle_sample(P, nblocks=2, ncols=256, counts=None):
 
 
 # Iteration counts of one whole oracle solve (eps_in 1e-4, tol 1e-10) of the
-# 64^3 slab workload: 1.5 outer iterations = 3 Fig. 3 applications; products
-# with A: 2 per outer iteration plus the true-residual checks.
-DEFAULT_ORACLE_COUNTS = {"spmv": 5, "applies": 3, "inner": 46}
+# 64^3 slab workload, measured once (1.5 outer iterations = 3 Fig. 3
+# applications with 15, 12 and 10.5 inner iterations; products with A: 2 per
+# outer iteration plus the true-residual checks).
+DEFAULT_ORACLE_COUNTS = {"spmv": 5, "applies": 3, "inner": 38}
 
 
 def oracle_batch_sample(systems, count=3):
@@ -365,7 +375,7 @@ def cpu_baseline_entry(P, nsys, workload):
     if nsys > 1:
         est, wall, sample = oracle_batch_sample(P.systems)
     else:
-        nb, nc = (1, 64) if workload == "randband_1m" else (2, 256)
+        nb, nc = (1, 256) if workload == "randband_1m" else (4, 1024)
         est, wall, sample = oracle_sample(P, nblocks=nb, ncols=nc)
     return {"value": nsys / est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
@@ -469,7 +479,7 @@ def kernel_table(prof, work, ms_total, peaks):
     return kern
 
 
-def measure_workload(name, form, steps, warmup, stream, extra_opts=None):
+def measure_workload(name, form, steps, warmup, stream, extra_opts=None, solve_only=False):
     """Factor + solve steps of one workload in one form (profiling off):
     solves/s and accuracy; used for the sub-results of the bench line."""
     import numpy as np
@@ -507,6 +517,22 @@ def measure_workload(name, form, steps, warmup, stream, extra_opts=None):
            "inner_iterations": infos[-1]["inner_iterations"]}
     if P.x_true is not None:
         out["rel_err_vs_xtrue"] = float(np.linalg.norm(xh - P.x_true) / np.linalg.norm(P.x_true))
+    if solve_only:
+        nr = 4
+        F4 = torch.stack([f * (1.0 + 0.25 * j) for j in range(nr)]).contiguous()
+        X4 = torch.empty_like(F4)
+        S.solve(F4, X4)
+        sms, sinf = timed(stream, lambda: S.solve(F4, X4)[1], 2)
+        out["solve_only"] = {"value": 2 * nr * nsys / (sms / 1e3), "unit": UNIT,
+                             "ms_per_solve": sms / (2 * nr), "nrhs_per_call": nr,
+                             "relres_inf": max(i["relres_inf"] for i in sinf)}
+        # per-class split of one factor + solve
+        S.set_profiling((1 << len(N.PROF_CLASSES)) - 1)
+        S.profile(reset=True)
+        step()
+        prof = S.profile(reset=True)
+        S.set_profiling(0)
+        out["classes_ms"] = {k: round(v[0], 3) for k, v in prof.items() if v[1]}
     S.close()
     del vals, f, x
     torch.cuda.empty_cache()
@@ -593,7 +619,7 @@ def run_ours(args):
         peak = peaks["hbm_gbs"]
         bound = "hbm"
         peak_note = f"{peaks['source']} HBM copy bandwidth"
-    elif args.form == "mixed" and dom in ("spike_fwd", "spike_bwd", "front_lu"):
+    elif args.form in ("mixed", "direct") and dom in ("spike_fwd", "spike_bwd", "front_lu"):
         # bf16 tensor-core products (3 passes per algorithmic product): sustained bf16 peak
         peak = peaks["bf16_tflops_sustained"]
         bound = "tensor"
@@ -623,9 +649,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.form == "fp64" else ("bf16x3+f16+f32+f64" if args.form == "mixed" else "f32+f64"),
+        "dtype": "f64" if args.form == "fp64" else ("bf16x3+f16+f32+f64" if args.form in ("mixed", "direct") else "f32+f64"),
         "variant": ("implicit G^: block solves instead of stored spikes (departs from Fig. 2 "
-                    "step 4)" if args.form == "implicit" else None),
+                    "step 4)" if args.form == "implicit" else
+                    "6.3 solved directly: block LU of the block-tridiagonal G^ of the slab chain"
+                    if args.form == "direct" else None),
         "data": "synthetic",
         "config": {"workload": args.workload, "systems_per_step": nsys, "n": P.n, "nnz": P.nnz,
                    "blocks": P.p,
@@ -635,7 +663,8 @@ def run_ours(args):
                           (sizes["factor_entries"] * 4 / 1e9) if args.form == "implicit" else
                           "working set (G^ %.1f GB) larger than L2" %
                           (sizes["ghat_entries"] * (8 if args.form == "fp64" else
-                                                    (2 if args.form == "mixed" else 4)) / 1e9)),
+                                                    (2 if args.form in ("mixed", "direct")
+                                                     else 4)) / 1e9)),
                    "tol_out": opts["tol_out"], "tol_in": opts["tol_in"]},
         "analyze_ms": round(analyze_ms, 1),
         "accuracy": {"relres_inf": relres, "rel_err_vs_xtrue": err_xtrue, "converged": converged,
@@ -712,6 +741,10 @@ def run_ours(args):
         # the benchmark spec's named precision form: FP32 G^ instead of FP16 storage
         line["fp32_ghat"] = measure_workload(args.workload, "mixed", 3, 1, stream,
                                              {"ghat_prec": N.DDPS_FP32})
+        if args.workload in ("cd3d_64_slabs16", "cd3d_48_slabs8"):
+            # variant: 6.3 solved directly (block LU of the block-tridiagonal G^)
+            line["direct_reduced"] = measure_workload(args.workload, "direct", 3, 1, stream,
+                                                      solve_only=True)
     S.close()
     del vals, f, x
     torch.cuda.empty_cache()

@@ -119,6 +119,11 @@ typedef struct {
                              remainder, fp32 accumulation, about 16 correct bits per product) */
   int32_t reduced_solver; /* ddps_reduced_solver; DIRECT needs an explicit G^ (ghat_mode 0) and
                              a chain partition, else ddps_analyze returns DDPS_ERR_INVALID_ARG */
+  int32_t use_graphs;     /* 1 (default): launch sequences that repeat unchanged (the factor
+                             phase, chunks of inner iterations, a direct-mode preconditioner
+                             application) are captured into CUDA graphs on a stream of the
+                             handle at their first use and replayed afterwards; 0: plain
+                             launches.  Graphs are not used while profiling is on. */
 } ddps_options;
 
 typedef struct {

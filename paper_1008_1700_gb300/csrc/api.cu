@@ -202,6 +202,19 @@ struct ddps_handle {
   // direct solve of the reduced system (reduced_solver DIRECT)
   DirectPlan direct;
   bool use_direct = false;
+  // CUDA graphs: launch sequences that repeat unchanged are captured once on
+  // a stream of the handle and replayed (not while profiling is on)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphExec_t g_inner = nullptr, g_factor = nullptr;
+  int64_t g_inner_launches = 0, g_factor_launches = 0;
+  struct PrecGraph {
+    const double* y;
+    double* z;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<PrecGraph> g_prec;
   // statistics of the current solve
   int64_t stat_inner = 0, stat_precond = 0;
   double stat_first_inner = 0;
@@ -318,6 +331,56 @@ void check_launch() {
   if (e != cudaSuccess) throw Fail{DDPS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
+// ---------------------------------------------------------------------------
+// CUDA graphs.  A capture runs on the handle's own stream (the legacy default
+// stream cannot be captured); a replay is ordered after the caller's stream
+// and the caller's stream after it, through two events.
+// ---------------------------------------------------------------------------
+bool graphs_on(const ddps_handle* h) { return h->opt.use_graphs && h->prof_mask == 0; }
+
+void ensure_graph_stream(ddps_handle* h) {
+  if (h->gstream) return;
+  CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
+}
+
+// Captures the launches `body` enqueues on the handle's stream; returns the
+// instantiated graph and adds the launches counted during capture to *count.
+template <typename F>
+cudaGraphExec_t capture_graph(ddps_handle* h, F body, int64_t* count) {
+  ensure_graph_stream(h);
+  const int64_t l0 = h->launches;
+  CK(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed));
+  try {
+    body(h->gstream);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(h->gstream, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamEndCapture(h->gstream, &g));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  *count = h->launches - l0;
+  h->launches = l0;
+  return exec;
+}
+
+void replay_graph(ddps_handle* h, cudaGraphExec_t exec, int64_t count, cudaStream_t s) {
+  CK(cudaEventRecord(h->gev[0], s));
+  CK(cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+  CK(cudaGraphLaunch(exec, h->gstream));
+  CK(cudaEventRecord(h->gev[1], h->gstream));
+  CK(cudaStreamWaitEvent(s, h->gev[1], 0));
+  h->launches += count;
+}
+
 // One spike GEMM op over a tile list: tensor cores for FP32 factors with
 // bf16 spike products, SIMT otherwise.
 template <typename T>
@@ -357,7 +420,7 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
 // Fig. 2 steps 2 and 4 on the device
 // ---------------------------------------------------------------------------
 template <typename T, typename TG>
-void factor_impl(ddps_handle* h, cudaStream_t s) {
+void factor_launches(ddps_handle* h, cudaStream_t s) {
   const Analysis& A = h->A;
   T* arena = (T*)h->arena;
   CK(cudaMemsetAsync(arena, 0, (size_t)A.arena_size * sizeof(T), s));
@@ -491,6 +554,20 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
     h->launches += direct_factor<TG>(h->direct, (const TG*)h->ghat, s);
   }
   check_launch();
+}
+
+// Fig. 2 steps 2-4 (and the block LU of G^ for a direct reduced solve):
+// replayed from a graph after the first call unless profiling is on.
+template <typename T, typename TG>
+void factor_impl(ddps_handle* h, cudaStream_t s) {
+  if (graphs_on(h)) {
+    if (!h->g_factor)
+      h->g_factor = capture_graph(h, [&](cudaStream_t gs) { factor_launches<T, TG>(h, gs); },
+                                  &h->g_factor_launches);
+    replay_graph(h, h->g_factor, h->g_factor_launches, s);
+  } else {
+    factor_launches<T, TG>(h, s);
+  }
   CK(cudaMemcpyAsync(h->herr, h->derr, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h->herr[0] == 2)
@@ -658,31 +735,58 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
   // the host looks at a single "some system still iterating" flag every
   // kCheckEvery iterations.
   constexpr int kCheckEvery = 4;
-  for (int it = 1; it <= h->opt.maxit_in; ++it) {
-    if ((it - 1) % kCheckEvery == 0) {
-      any_active(ns, sc, h->any_flag, s);
-      CK(cudaMemcpyAsync(h->any_host, h->any_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  // one BiCGStab iteration; `it` < 0: the iteration number lives on the device
+  auto iteration = [&](int it, cudaStream_t st) {
+    seg_reduce_post<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, POST_BETA,
+                        sc, tol, it, st);
+    update_p<TI>(S, sc, r, p, v, st);
+    ghat_matvec<TG, TI>(h, p, v, st, sc);
+    seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
+                        POST_ALPHA, sc, tol, it, st);
+    update_s<TI>(S, sc, r, v, sv, st);
+    seg_reduce_post<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
+                        POST_CHECK_HALF, sc, tol, it, st);
+    ghat_matvec<TG, TI>(h, sv, t, st, sc);
+    seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
+                        h->partial, POST_OMEGA, sc, tol, it, st);
+    update_xr_final<TI>(S, sc, z, p, sv, r, t, st);
+    seg_reduce_post<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
+                        POST_CHECK_FULL, sc, tol, it, st);
+    h->launches += 15;
+  };
+  if (graphs_on(h) && h->opt.maxit_in > 0) {
+    // kCheckEvery iterations and the "some system still iterating" flag, one
+    // graph replayed until every system has stopped (the device counter
+    // stops a system after maxit_in iterations)
+    if (!h->g_inner)
+      h->g_inner = capture_graph(
+          h,
+          [&](cudaStream_t gs) {
+            for (int q = 0; q < kCheckEvery; ++q) iteration(-h->opt.maxit_in, gs);
+            any_active(ns, sc, h->any_flag, gs);
+            CK(cudaMemcpyAsync(h->any_host, h->any_flag, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               gs));
+            h->launches++;
+          },
+          &h->g_inner_launches);
+    for (int it = 0; it < h->opt.maxit_in; it += kCheckEvery) {
+      replay_graph(h, h->g_inner, h->g_inner_launches, s);
       CK(cudaStreamSynchronize(s));
       h->stage_next = 0;
-      h->launches++;
       if (!*h->any_host) break;
     }
-    seg_reduce_post<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, POST_BETA,
-                        sc, tol, it, s);
-    update_p<TI>(S, sc, r, p, v, s);
-    ghat_matvec<TG, TI>(h, p, v, s, sc);
-    seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
-                        POST_ALPHA, sc, tol, it, s);
-    update_s<TI>(S, sc, r, v, sv, s);
-    seg_reduce_post<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
-                        POST_CHECK_HALF, sc, tol, it, s);
-    ghat_matvec<TG, TI>(h, sv, t, s, sc);
-    seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
-                        h->partial, POST_OMEGA, sc, tol, it, s);
-    update_xr_final<TI>(S, sc, z, p, sv, r, t, s);
-    seg_reduce_post<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
-                        POST_CHECK_FULL, sc, tol, it, s);
-    h->launches += 15;
+  } else {
+    for (int it = 1; it <= h->opt.maxit_in; ++it) {
+      if ((it - 1) % kCheckEvery == 0) {
+        any_active(ns, sc, h->any_flag, s);
+        CK(cudaMemcpyAsync(h->any_host, h->any_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        h->stage_next = 0;
+        h->launches++;
+        if (!*h->any_host) break;
+      }
+      iteration(it, s);
+    }
   }
   download_sc(h, sc, s);
   for (int q = 0; q < ns; ++q) iters[q] = h->hsc[q].iters;
@@ -709,9 +813,37 @@ double inner_dispatch(ddps_handle* h, const double* ghat64, double* zhat64, cons
                          : inner_solve<__nv_bfloat16, float>(h, ghat64, zhat64, z0, s);
 }
 
+// Fig. 3 with the direct reduced solve: a fixed launch sequence for given
+// y and z, so it is replayed from a graph per (y, z) pair.
+void precond_direct_launches(ddps_handle* h, const double* y, double* z, cudaStream_t s);
+
 // Fig. 3: z = P^-1 y.
 void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, bool first) {
   const int64_t m = (int64_t)h->A.c.size();
+  if (h->use_direct && m > 0) {
+    if (graphs_on(h)) {
+      ddps_handle::PrecGraph* pg = nullptr;
+      for (auto& q : h->g_prec)
+        if (q.y == y && q.z == z) pg = &q;
+      if (!pg) {
+        ddps_handle::PrecGraph q{y, z, nullptr, 0};
+        q.exec = capture_graph(h, [&](cudaStream_t gs) { precond_direct_launches(h, y, z, gs); },
+                               &q.launches);
+        h->g_prec.push_back(q);
+        pg = &h->g_prec.back();
+      }
+      replay_graph(h, pg->exec, pg->launches, s);
+    } else {
+      precond_direct_launches(h, y, z, s);
+    }
+    if (first) {
+      h->stat_first_inner = 0;
+      CK(cudaMemcpyAsync(h->first_zhat, h->pc_zhat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(h->first_ghat, h->pc_ghat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    h->stat_precond++;
+    return;
+  }
   block_solve(h, y, h->pc_g, s);                                        // 6.1
   if (m == 0) {
     CK(cudaMemcpyAsync(z, h->pc_g, h->A.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -721,13 +853,7 @@ void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, b
   launch_gather(h->pc_g, h->c, m, h->pc_ghat, s);                        // 6.2
   h->launches++;
   const double* z0 = (first && h->has_guess) ? h->guess : nullptr;
-  double its = 0;
-  if (h->use_direct) {  // 6.3 by the block LU of G^
-    Prof pr(h, DDPS_PROF_DIRECT_SOLVE, s);
-    h->launches += direct_solve(h->direct, h->pc_ghat, h->pc_zhat, s);
-  } else {
-    its = inner_dispatch(h, h->pc_ghat, h->pc_zhat, z0, s);  // 6.3
-  }
+  const double its = inner_dispatch(h, h->pc_ghat, h->pc_zhat, z0, s);  // 6.3
   h->stat_inner += (int64_t)std::ceil(its);
   if (first) {
     h->stat_first_inner = its;
@@ -739,6 +865,21 @@ void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, b
   h->launches++;
   block_solve(h, h->pc_t, z, s);
   h->stat_precond++;
+}
+
+void precond_direct_launches(ddps_handle* h, const double* y, double* z, cudaStream_t s) {
+  const int64_t m = (int64_t)h->A.c.size();
+  block_solve(h, y, h->pc_g, s);                       // 6.1
+  launch_gather(h->pc_g, h->c, m, h->pc_ghat, s);       // 6.2
+  h->launches++;
+  {
+    Prof pr(h, DDPS_PROF_DIRECT_SOLVE, s);             // 6.3 by the block LU of G^
+    h->launches += direct_solve(h->direct, h->pc_ghat, h->pc_zhat, s);
+  }
+  // 6.4-6.5: z = D~^-1 (y - R~ z^)
+  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s);
+  h->launches++;
+  block_solve(h, h->pc_t, z, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1502,6 +1643,7 @@ void ddps_default_options(ddps_options* o) {
   o->leaf_size = 0;
   o->rhs_chunk = 0;
   o->verbose = 0;
+  o->use_graphs = 1;
 }
 
 ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
@@ -1882,6 +2024,15 @@ ddps_status ddps_get_ghat_block(ddps_handle* h, int32_t b, double* dst, void* st
 
 ddps_status ddps_destroy(ddps_handle* h) {
   if (!h) return DDPS_OK;
+  if (h->g_inner) cudaGraphExecDestroy(h->g_inner);
+  if (h->g_factor) cudaGraphExecDestroy(h->g_factor);
+  for (auto& q : h->g_prec) cudaGraphExecDestroy(q.exec);
+  if (h->gstream) {
+    cudaStreamSynchronize(h->gstream);
+    cudaStreamDestroy(h->gstream);
+  }
+  for (cudaEvent_t e : h->gev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->herr) cudaFreeHost(h->herr);

@@ -47,6 +47,11 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
   KScal& k = sc[sgi];
   if (post == POST_CHECK_FULL) k.half_done = 0;
   if (!k.active) return;
+  const int cap = it < 0 ? -it : 0;
+  if (it < 0) {
+    if (post == POST_BETA) k.it += 1;
+    it = k.it;
+  }
   switch (post) {
     case POST_BETA:
       if (k.rho == 0.0) k.breakdown = 1;
@@ -76,7 +81,8 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
       break;
     case POST_CHECK_FULL:
       k.iters = it;
-      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown) k.active = 0;
+      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown || (cap && it >= cap))
+        k.active = 0;
       break;
   }
 }

@@ -40,6 +40,8 @@ struct KScal {
   int32_t half_done;  // converged at the half step of the current iteration
   int32_t breakdown;
   int32_t flag;       // scratch mask for masked updates
+  int32_t it;         // iteration number on the device (loops that pass it < 0)
+  int32_t pad;
 };
 static_assert(sizeof(KScal) % sizeof(double) == 0, "KScal must be a whole number of doubles");
 constexpr int kScalStride = (int)(sizeof(KScal) / sizeof(double));
@@ -65,7 +67,11 @@ void masked_axpy(const SegView& S, const KScal* sc, T* dst, const T* a, const T*
 // dst = 0 on segments whose flag is set
 template <typename T>
 void masked_zero(const SegView& S, const KScal* sc, T* dst, cudaStream_t s);
-// Reduction whose final pass also updates the segment's scalars:
+// Reduction whose final pass also updates the segment's scalars.  `it` is
+// the iteration number (1-based); it < 0 selects the segment's device
+// counter instead (POST_BETA advances it; -it is the iteration cap: the
+// full-step check stops a segment that has taken -it iterations), so that
+// the same launches serve every iteration of a captured graph.
 enum Post {
   POST_NONE = 0,
   POST_BETA = 1,        // beta = (rho / rho_old)(alpha / omega), 0 at iteration 1

@@ -35,7 +35,7 @@ class ddps_options(C.Structure):
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
                 ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
                 ("ghat_mode", C.c_int32), ("update_prec", C.c_int32),
-                ("reduced_solver", C.c_int32)]
+                ("reduced_solver", C.c_int32), ("use_graphs", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):

@@ -395,3 +395,30 @@ def test_factor_from_host_values():
     y = dev(np.random.default_rng(5).standard_normal(P.n))
     assert np.array_equal(host(S1.block_solve(y)), host(S2.block_solve(y)))
     assert np.array_equal(S1.ghat_block(2), S2.ghat_block(2))
+
+
+@pytest.mark.parametrize("form", ["fp64", "tc3", "implicit", "direct"])
+def test_graph_replay_matches_plain_launches(form):
+    """The factor phase, the inner iterations and (direct mode) the whole
+    preconditioner are replayed from CUDA graphs after their first use; the
+    results are bitwise those of plain launches, over repeated factor + solve
+    calls, and with fewer host-side launches."""
+    opts = {"fp64": FP64, "tc3": dict(TC3, update_prec=N.DDPS_BF16X3), "implicit": IMPLICIT,
+            "direct": dict(TC3, reduced_solver=N.DDPS_REDUCED_DIRECT)}[form]
+    probs = [W.small_convdiff_3d(12, [3, 5, 4]), W.small_convdiff_3d(10, [4, 3, 3], seed=3)]
+    from paper_1008_1700_gb300 import Solver
+    xs = {}
+    for graphs in (0, 1):
+        S = Solver.from_systems([(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs],
+                                tol_out=1e-12, tol_in=1e-6, use_graphs=graphs, **opts)
+        f = dev(np.concatenate([p.f for p in probs]))
+        out = []
+        for rep in range(3):
+            S.factor(dev(S.values_host * (1.0 + 0.01 * rep)))
+            x, info = S.solve(f)
+            assert info["status"] == "DDPS_OK"
+            out.append(host(x).copy())
+        xs[graphs] = out
+        S.close()
+    for rep in range(3):
+        assert np.array_equal(xs[0][rep], xs[1][rep]), rep
