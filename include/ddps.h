@@ -124,6 +124,16 @@ typedef struct {
                              application) are captured into CUDA graphs on a stream of the
                              handle at their first use and replayed afterwards; 0: plain
                              launches.  Graphs are not used while profiling is on. */
+  int32_t persistent_solve; /* 1 (default): the block solves (6.1, 6.5) sweep the deep levels of
+                             small fronts (at most 128 rows) in one persistent launch per sweep,
+                             fronts ordered by per-front completion flags with bounded waits
+                             (a wait that runs out makes ddps_solve return DDPS_ERR_TIMEOUT);
+                             0: one launch per tree depth */
+  int32_t autotune;       /* 1 (default): the first ddps_factor times every candidate launch shape
+                             of each block-solve depth and sweep (warp per front, CTA per front,
+                             clusters of 1-8 CTAs) on the handle's factors and keeps the fastest;
+                             choices are cached per process and, when the environment variable
+                             DDPS_TUNE_CACHE names a file, in that JSON file; 0: fixed rules */
 } ddps_options;
 
 typedef struct {
@@ -277,6 +287,12 @@ ddps_status ddps_spmv(ddps_handle* h, const double* x, double* y, void* stream);
 
 /* Sizes of the analysis (host struct). */
 ddps_status ddps_get_sizes(const ddps_handle* h, ddps_sizes* s);
+
+/* The autotuner's choices as a JSON text (per block-solve depth: fronts,
+ * largest front, chosen shape per sweep and its time): at most cap-1 bytes
+ * and a terminating zero are written to buf (host, may be NULL); *len (host,
+ * may be NULL) receives the full length. */
+ddps_status ddps_get_tuning(const ddps_handle* h, char* buf, int64_t cap, int64_t* len);
 
 /* The interface set c (host int64[m], global row indices, ascending within
  * each system, systems in order). */

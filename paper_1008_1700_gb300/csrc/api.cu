@@ -8,9 +8,13 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <fstream>
+#include <map>
 #include <mutex>
+#include <sstream>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -199,6 +203,14 @@ struct ddps_handle {
   std::vector<ProfRec> prof_recs;
   double prof_ms[DDPS_PROF_CLASSES] = {};
   int64_t prof_cnt[DDPS_PROF_CLASSES] = {};
+  // launch shape of every block-solve depth and sweep (SOLVE_AUTO until tuned)
+  std::vector<int> tune_fwd, tune_bwd;
+  std::vector<float> tune_fwd_ms, tune_bwd_ms;
+  bool tuned = false;
+  // persistent sweeps of the block solve over the levels >= persist_L (fronts of at
+  // most kPersistM rows): orders, waits and flags (2 nfronts done flags, 2 counters)
+  int32_t persist_L = -1, persist_n = 0, persist_max_m = 0;
+  int32_t *p_fwd = nullptr, *p_bwd = nullptr, *p_wait = nullptr, *p_flags = nullptr;
   // direct solve of the reduced system (reduced_solver DIRECT)
   DirectPlan direct;
   bool use_direct = false;
@@ -596,14 +608,152 @@ void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s
   const T* arena = (const T*)h->arena;
   Prof pr(h, prof_cls, s);
   launch_permute_in<T>(y, h->perm, A.n, w, s);
-  for (int L = A.nlevels - 1; L >= 0; --L)
+  // levels >= top: one persistent launch per sweep; the levels above: one launch each
+  const int top = h->persist_L >= 0 ? h->persist_L : A.nlevels;
+  const int64_t nf = (int64_t)A.f_k.size();
+  int32_t* done_f = h->p_flags;
+  int32_t* done_b = h->p_flags + nf;
+  if (h->persist_L >= 0) {
+    CK(cudaMemsetAsync(h->p_flags, 0, (2 * nf + 2) * sizeof(int32_t), s));
+    launch_fwd_persist<T>(h->F, h->p_fwd, h->persist_n, h->persist_max_m, arena, w, u, done_f,
+                          h->p_flags + 2 * nf, h->derr, s);
+    h->launches++;
+  }
+  for (int L = top - 1; L >= 0; --L)
     launch_fwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   h->split[L].max_m, arena, w, u, s);
-  for (int L = 0; L < A.nlevels; ++L)
+                   h->split[L].max_m, arena, w, u, s, h->tune_fwd.empty() ? SOLVE_AUTO : h->tune_fwd[L]);
+  for (int L = 0; L < top; ++L)
     launch_bwd1<T>(h->F, h->level_fronts + A.level_ptr[L], A.level_ptr[L + 1] - A.level_ptr[L],
-                   h->split[L].max_m, arena, w, s);
+                   h->split[L].max_m, arena, w, s, h->tune_bwd.empty() ? SOLVE_AUTO : h->tune_bwd[L]);
+  if (h->persist_L >= 0) {
+    launch_bwd_persist<T>(h->F, h->p_bwd, h->persist_n, h->persist_max_m, h->p_wait, arena, w,
+                          done_b, h->p_flags + 2 * nf + 1, h->derr, s);
+    h->launches++;
+  }
   launch_permute_out<T>(w, h->perm, A.n, g, s);
-  h->launches += 2 + 2 * A.nlevels;
+  h->launches += 2 + 2 * top;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the block-solve launch shapes.  For every depth above the
+// persistent sweeps and both sweeps, each candidate shape (warp per front
+// when the fronts allow, one CTA with eight loads in flight, clusters of 1,
+// 2, 4 and 8 CTAs) is timed with CUDA events on the handle's own factors
+// (one untimed launch, then the mean of three), and the fastest is kept.
+// Choices are cached per process by (device, precision, sweep, front count,
+// largest front, total front entries) and, when the environment variable
+// DDPS_TUNE_CACHE names a file, read from and written to that JSON object.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+bool g_tune_file_read = false;
+
+void tune_cache_read() {
+  const char* path = std::getenv("DDPS_TUNE_CACHE");
+  if (g_tune_file_read || !path) return;
+  g_tune_file_read = true;
+  std::ifstream in(path);
+  if (!in) return;
+  std::stringstream ss;
+  ss << in.rdbuf();
+  const std::string t = ss.str();
+  size_t i = 0;
+  while ((i = t.find('"', i)) != std::string::npos) {
+    const size_t j = t.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string key = t.substr(i + 1, j - i - 1);
+    const size_t c = t.find(':', j);
+    if (c == std::string::npos) break;
+    g_tune_cache[key] = std::atoi(t.c_str() + c + 1);
+    i = t.find_first_of(",}", c);
+    if (i == std::string::npos) break;
+  }
+}
+
+void tune_cache_write() {
+  const char* path = std::getenv("DDPS_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream out(path);
+  out << "{";
+  bool first = true;
+  for (const auto& kv : g_tune_cache) {
+    out << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": " << kv.second;
+    first = false;
+  }
+  out << "\n}\n";
+}
+
+template <typename T>
+void autotune_block_solve(ddps_handle* h, cudaStream_t s) {
+  const Analysis& A = h->A;
+  const int top = h->persist_L >= 0 ? h->persist_L : A.nlevels;
+  h->tune_fwd.assign(A.nlevels, SOLVE_AUTO);
+  h->tune_bwd.assign(A.nlevels, SOLVE_AUTO);
+  h->tune_fwd_ms.assign(A.nlevels, 0.f);
+  h->tune_bwd_ms.assign(A.nlevels, 0.f);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  T* w = (T*)h->w;
+  T* u = (T*)h->updv;
+  const T* arena = (const T*)h->arena;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_cache_read();
+  bool added = false;
+  for (int L = 0; L < top; ++L) {
+    const int32_t nf = A.level_ptr[L + 1] - A.level_ptr[L];
+    const int32_t mm = h->split[L].max_m;
+    int64_t ent = 0;
+    for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q)
+      ent += (int64_t)A.f_m[A.level_fronts[q]] * A.f_m[A.level_fronts[q]];
+    const int32_t* list = h->level_fronts + A.level_ptr[L];
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      const std::string key = std::string(prop.name) + "|" + std::to_string(sizeof(T)) + "|" +
+                              (sweep ? "bwd" : "fwd") + "|" + std::to_string(nf) + "|" +
+                              std::to_string(mm) + "|" + std::to_string(ent);
+      int best = SOLVE_AUTO;
+      float best_ms = 0.f;
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        best = it->second;
+      } else {
+        for (int cfg = SOLVE_WARP; cfg <= SOLVE_CL8; ++cfg) {
+          if (cfg == SOLVE_WARP && mm > kPersistM) continue;
+          auto run = [&]() {
+            if (sweep == 0)
+              launch_fwd1<T>(h->F, list, nf, mm, arena, w, u, s, cfg);
+            else
+              launch_bwd1<T>(h->F, list, nf, mm, arena, w, s, cfg);
+          };
+          run();
+          CK(cudaEventRecord(e0, s));
+          for (int r = 0; r < 3; ++r) run();
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          ms /= 3.f;
+          if (best == SOLVE_AUTO || ms < best_ms) {
+            best = cfg;
+            best_ms = ms;
+          }
+        }
+        check_launch();
+        g_tune_cache[key] = best;
+        added = true;
+      }
+      (sweep ? h->tune_bwd : h->tune_fwd)[L] = best;
+      (sweep ? h->tune_bwd_ms : h->tune_fwd_ms)[L] = best_ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (added) tune_cache_write();
+  h->tuned = true;
 }
 
 void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s,
@@ -1033,13 +1183,16 @@ ddps_status solve_impl(ddps_handle* h, const double* f, double* x, const double*
     }
     upload_sc(h, sc, s);
   }
-  // final true residual of every system
+  // final true residual of every system (and the block solves' wait record)
+  CK(cudaMemcpyAsync(h->herr, h->derr, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   spmv(x, h->o_tmp);
   vec_sub<double>(S, sc, 1, f, h->o_tmp, h->o_tmp, s);
   seg_reduce<double>(S, 1, red(h->o_tmp, nullptr, 2, &sc[0].nrm2), nored(), nored(), h->partial, s);
   h->launches += 2;
   download_sc(h, sc, s);
   check_launch();
+  if (h->herr[0] == 2)
+    throw Fail{DDPS_ERR_TIMEOUT, "a bounded wait of the persistent block-solve sweeps gave up"};
   bool all = true;
   double worst = 0, maxit = 0;
   for (int q = 0; q < ns; ++q) {
@@ -1534,6 +1687,35 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   CK(cudaMallocHost((void**)&h->hstage, sizeof(KScal) * h->nseg * kStageSlots));
   h->hsc = h->hsc_out;
   h->partial = dalloc<double>(h, 3 * (int64_t)std::max(h->Sn.nchunks, h->Sm.nchunks) + 3);
+  {
+    // persistent sweeps: the deepest run of levels whose fronts all have at
+    // most kPersistM rows, if it spans two levels or more
+    int Lc = A.nlevels;
+    while (Lc > 0 && h->split[Lc - 1].max_m <= kPersistM) --Lc;
+    if (A.nlevels - Lc >= 2 && h->opt.persistent_solve != 0) {
+      const int64_t nf = (int64_t)A.f_k.size();
+      std::vector<int32_t> fwd, bwd, wait(nf, -1), level(nf, 0);
+      for (int L = 0; L < A.nlevels; ++L)
+        for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) level[A.level_fronts[q]] = L;
+      for (int L = A.nlevels - 1; L >= Lc; --L)
+        for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+          fwd.push_back(A.level_fronts[q]);
+          h->persist_max_m = std::max(h->persist_max_m, A.f_m[A.level_fronts[q]]);
+        }
+      for (int L = Lc; L < A.nlevels; ++L)
+        for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q) {
+          const int32_t f = A.level_fronts[q];
+          bwd.push_back(f);
+          if (L > Lc) wait[f] = A.f_parent[f];
+        }
+      h->persist_L = Lc;
+      h->persist_n = (int32_t)fwd.size();
+      h->p_fwd = dupload(h, fwd);
+      h->p_bwd = dupload(h, bwd);
+      h->p_wait = dupload(h, wait);
+      h->p_flags = dalloc<int32_t>(h, 2 * nf + 2);
+    }
+  }
   if (h->opt.reduced_solver == DDPS_REDUCED_DIRECT && m > 0) {
     std::vector<int32_t> gcols_panel(A.gcols.size());
     for (int32_t b = 0; b < A.p; ++b)
@@ -1644,6 +1826,8 @@ void ddps_default_options(ddps_options* o) {
   o->rhs_chunk = 0;
   o->verbose = 0;
   o->use_graphs = 1;
+  o->persistent_solve = 1;
+  o->autotune = 1;
 }
 
 ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
@@ -1709,6 +1893,12 @@ static ddps_status factor_values(ddps_handle* h, const double* values, bool host
         factor_impl<float, __half>(h, s);
       else
         factor_impl<float, __nv_bfloat16>(h, s);
+    }
+    if (h->opt.autotune && !h->tuned) {
+      if (fp == DDPS_FP64)
+        autotune_block_solve<double>(h, s);
+      else
+        autotune_block_solve<float>(h, s);
     }
     h->factored = true;
   } catch (const Fail& f) {
@@ -1954,6 +2144,31 @@ ddps_status ddps_get_sizes(const ddps_handle* h, ddps_sizes* s) {
   s->spike_flops = A.spike_flops;
   s->direct_flops = h->use_direct ? h->direct.factor_flops : 0.0;
   s->direct_bytes = h->use_direct ? h->direct.solve_bytes : 0;
+  return DDPS_OK;
+}
+
+ddps_status ddps_get_tuning(const ddps_handle* h, char* buf, int64_t cap, int64_t* len) {
+  if (!h) return DDPS_ERR_INVALID_ARG;
+  static const char* names[] = {"warp", "cta8", "cl1", "cl2", "cl4", "cl8"};
+  std::ostringstream o;
+  o << "{\"tuned\": " << (h->tuned ? "true" : "false") << ", \"persistent_from_level\": "
+    << h->persist_L << ", \"levels\": [";
+  for (size_t L = 0; L < h->tune_fwd.size(); ++L) {
+    const int f = h->tune_fwd[L], b = h->tune_bwd[L];
+    o << (L ? ", " : "") << "{\"level\": " << L
+      << ", \"fronts\": " << (h->A.level_ptr[L + 1] - h->A.level_ptr[L])
+      << ", \"max_m\": " << h->split[L].max_m << ", \"fwd\": \""
+      << (f >= 0 ? names[f] : "auto") << "\", \"bwd\": \"" << (b >= 0 ? names[b] : "auto")
+      << "\", \"fwd_ms\": " << h->tune_fwd_ms[L] << ", \"bwd_ms\": " << h->tune_bwd_ms[L] << "}";
+  }
+  o << "]}";
+  const std::string t = o.str();
+  if (len) *len = (int64_t)t.size();
+  if (buf && cap > 0) {
+    const size_t nc = std::min<size_t>((size_t)cap - 1, t.size());
+    std::memcpy(buf, t.data(), nc);
+    buf[nc] = 0;
+  }
   return DDPS_OK;
 }
 

@@ -66,6 +66,19 @@ struct DevError {
   long long* rec;
 };
 
+// ---- solve.cu: persistent sweeps over the deep levels (fronts of at most
+// kPersistM rows); done: one flag per front, next: the work counter, both zero
+// before the launch ----
+constexpr int32_t kPersistM = 128;
+template <typename T>
+void launch_fwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32_t max_m,
+                        const T* arena, T* w, T* u, int32_t* done, int32_t* next, long long* err,
+                        cudaStream_t s);
+template <typename T>
+void launch_bwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32_t max_m,
+                        const int32_t* wait_on, const T* arena, T* w, int32_t* done,
+                        int32_t* next, long long* err, cudaStream_t s);
+
 // ---- factor.cu --------------------------------------------------------------
 template <typename T>
 void launch_assemble(const double* values, const int64_t* amap, int64_t nnz, T* arena,
@@ -185,12 +198,19 @@ template <typename T>
 void launch_permute_in(const double* y, const int32_t* perm, int64_t n, T* w, cudaStream_t s);
 template <typename T>
 void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, cudaStream_t s);
+// Launch shapes of a block-solve depth (see launch_fwd1): automatic, one warp
+// per front, one CTA per front with eight loads in flight per lane, or a
+// cluster of 1, 2, 4 or 8 CTAs per front with sixteen.
+enum { SOLVE_AUTO = -1, SOLVE_WARP = 0, SOLVE_CTA8 = 1, SOLVE_CL1 = 2, SOLVE_CL2 = 3,
+       SOLVE_CL4 = 4, SOLVE_CL8 = 5 };
+inline int solve_cfg_cluster(int c) { return c >= 8 ? SOLVE_CL8 : c >= 4 ? SOLVE_CL4 : c >= 2 ? SOLVE_CL2 : SOLVE_CL1; }
+inline int solve_cfg_size(int cfg) { return cfg == SOLVE_CL8 ? 8 : cfg == SOLVE_CL4 ? 4 : cfg == SOLVE_CL2 ? 2 : 1; }
 template <typename T>
 void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
-                 T* w, T* u, cudaStream_t s);
+                 T* w, T* u, cudaStream_t s, int cfg = SOLVE_AUTO);
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
-                 T* w, cudaStream_t s);
+                 T* w, cudaStream_t s, int cfg = SOLVE_AUTO);
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
                  const double* x, double* y, cudaStream_t s);
 // y_out = y - R~ zhat (R~ rows over original indices, reduced columns)

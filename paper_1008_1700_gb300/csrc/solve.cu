@@ -354,6 +354,123 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = lane; i < k; i += 32) w[row0 + i] = warp_row_dot(A + i, m, i, k, t);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent sweeps over the deep levels of the elimination forest, where
+// every front has at most kPersistM rows: one launch per sweep instead of
+// one per depth.  Each warp takes the next front of a topological order
+// (children before parents forward, parents before children backward) from
+// an atomic counter, waits until the fronts it depends on have raised their
+// flags, does the front's work as the warp-per-front kernels above do, and
+// raises its own flag.  A front's dependencies were handed out before it,
+// to warps already running, so every wait ends; each wait is still bounded
+// (kPersistSpin polls) and a wait that runs out records code 2 in err,
+// raises the flag anyway and lets the sweep finish.  Data another warp of the
+// same launch wrote is read with ld.global.cg (L2, not a stale L1 line).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPersistSpin = 1u << 22;
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Every lane polls the flag (acquire); false when the bounded wait ran out.
+__device__ __forceinline__ bool wait_flag(const int32_t* flag, long long* err) {
+  uint32_t n = 0;
+  while (ld_acquire(flag) == 0) {
+    if (++n > kPersistSpin) {
+      atomicCAS((unsigned long long*)err, 0ull, 2ull);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd_persist(DevFronts F, const int32_t* __restrict__ order, int32_t nitems, int32_t ldt,
+                  const T* __restrict__ arena, T* __restrict__ w, T* __restrict__ u,
+                  int32_t* __restrict__ done, int32_t* __restrict__ next, long long* err) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* t = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * ldt;  // m entries, then y (k)
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(next, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nitems) return;
+    const int32_t f = order[q];
+    const int32_t k = F.k[f], m = F.m[f];
+    const T* __restrict__ A = arena + F.arena[f];
+    const int64_t row0 = F.row0[f];
+    T* y = t + m;
+    for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) wait_flag(done + F.children[ci], err);
+    for (int i = lane; i < m; i += 32) t[i] = i < k ? ldcg(w + row0 + i) : T(0);
+    __syncwarp();
+    for (int32_t ci = F.cbeg[f]; ci < F.cend[f]; ++ci) {
+      const int32_t c = F.children[ci];
+      const int32_t rc = F.m[c] - F.k[c];
+      const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
+      const T* uc = u + F.upd[c];
+      for (int i = lane; i < rc; i += 32) t[rel[i]] += ldcg(uc + i);
+      __syncwarp();
+    }
+    for (int i = lane; i < k; i += 32) y[i] = t[i] + warp_row_dot(A + i, m, 0, i, t);
+    __syncwarp();
+    T* __restrict__ uf = u + F.upd[f];
+    for (int i = lane; i < m - k; i += 32) uf[i] = t[k + i] - warp_row_dot(A + k + i, m, 0, k, y);
+    for (int i = lane; i < k; i += 32) w[row0 + i] = y[i];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(done + f, 1);
+    __syncwarp();
+  }
+}
+
+// wait_on[f]: the parent whose pivots front f reads, when it is swept by the
+// same launch; -1 when it was done before the launch (or f is a root).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_bwd_persist(DevFronts F, const int32_t* __restrict__ order, int32_t nitems, int32_t ldt,
+                  const int32_t* __restrict__ wait_on, const T* __restrict__ arena,
+                  T* __restrict__ w, int32_t* __restrict__ done, int32_t* __restrict__ next,
+                  long long* err) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* t = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * ldt;  // k entries, then x_upd (r)
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(next, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= nitems) return;
+    const int32_t f = order[q];
+    const int32_t k = F.k[f], m = F.m[f], r = m - k;
+    if (wait_on[f] >= 0) wait_flag(done + wait_on[f], err);
+    const T* __restrict__ A = arena + F.arena[f];
+    const int32_t* __restrict__ idx = F.idx + F.idx_off[f];
+    const int64_t row0 = F.row0[f];
+    T* xu = t + k;
+    for (int j = lane; j < r; j += 32) xu[j] = ldcg(w + idx[k + j]);
+    __syncwarp();
+    for (int i = lane; i < k; i += 32)
+      t[i] = ldcg(w + row0 + i) - warp_row_dot(A + i + (int64_t)k * m, m, 0, r, xu);
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) w[row0 + i] = warp_row_dot(A + i, m, i, k, t);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(done + f, 1);
+    __syncwarp();
+  }
+}
+
 // CSR product streamed by row blocks: y = A x (SUB 0) or y = b - A x (SUB 1).
 // A CTA takes kStreamRows consecutive rows; their entries are contiguous,
 // [rowptr[r0], rowptr[r1]), and are read with coalesced loads (thread t the
@@ -711,11 +828,18 @@ static bool warp_solve_level(int32_t nf, int32_t max_m) {
   return max_m <= kWarpSolveM && nf > 2 * sm_count();
 }
 
+// Launch shape of one depth's sweep: SOLVE_AUTO picks from the front count
+// and size (warp per front for many small fronts, one CTA with eight loads in
+// flight per lane for many fronts, else clusters); the autotuner may fix it.
 template <typename T>
 void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
-                 T* w, T* u, cudaStream_t s) {
+                 T* w, T* u, cudaStream_t s, int cfg) {
   if (nf <= 0) return;
-  if (warp_solve_level(nf, max_m)) {
+  if (cfg == SOLVE_AUTO)
+    cfg = warp_solve_level(nf, max_m) ? SOLVE_WARP
+          : wide_solve_level(nf, max_m) ? SOLVE_CTA8
+                                        : solve_cfg_cluster(solve_cluster(nf, max_m));
+  if (cfg == SOLVE_WARP && max_m <= kWarpSolveM) {
     const int32_t ldt = 2 * max_m;
     const size_t smw = (size_t)(kThreads / 32) * ldt * sizeof(T);
     const int32_t grid = (nf + kThreads / 32 - 1) / (kThreads / 32);
@@ -723,17 +847,21 @@ void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
     return;
   }
   const size_t sm = ((size_t)2 * max_m + kSolveRed) * sizeof(T);
-  if (wide_solve_level(nf, max_m))
+  if (cfg == SOLVE_CTA8)
     launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w, u);
   else
-    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf, max_m), sm, s, F,
-                     list, arena, w, u);
+    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cfg_size(cfg), sm, s, F, list,
+                     arena, w, u);
 }
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
-                 T* w, cudaStream_t s) {
+                 T* w, cudaStream_t s, int cfg) {
   if (nf <= 0) return;
-  if (warp_solve_level(nf, max_m)) {
+  if (cfg == SOLVE_AUTO)
+    cfg = warp_solve_level(nf, max_m) ? SOLVE_WARP
+          : wide_solve_level(nf, max_m) ? SOLVE_CTA8
+                                        : solve_cfg_cluster(solve_cluster(nf, max_m));
+  if (cfg == SOLVE_WARP && max_m <= kWarpSolveM) {
     const int32_t ldt = max_m;
     const size_t smw = (size_t)(kThreads / 32) * ldt * sizeof(T);
     const int32_t grid = (nf + kThreads / 32 - 1) / (kThreads / 32);
@@ -741,11 +869,38 @@ void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
     return;
   }
   const size_t sm = ((size_t)max_m + kSolveRed) * sizeof(T);
-  if (wide_solve_level(nf, max_m))
+  if (cfg == SOLVE_CTA8)
     launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w);
   else
-    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cluster(nf, max_m), sm, s, F,
-                     list, arena, w);
+    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cfg_size(cfg), sm, s, F, list,
+                     arena, w);
+}
+
+// Persistent sweeps: enough warps for every front, at most eight CTAs of
+// eight warps per SM (every warp of a launch that has taken a front is
+// running, so the waits need no co-residency).
+template <typename T>
+void launch_fwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32_t max_m,
+                        const T* arena, T* w, T* u, int32_t* done, int32_t* next, long long* err,
+                        cudaStream_t s) {
+  if (nitems <= 0) return;
+  const int32_t ldt = 2 * max_m;
+  const size_t sm = (size_t)(kThreads / 32) * ldt * sizeof(T);
+  const int32_t grid = std::min<int32_t>((nitems + kThreads / 32 - 1) / (kThreads / 32),
+                                         8 * sm_count());
+  k_fwd_persist<T><<<grid, kThreads, sm, s>>>(F, order, nitems, ldt, arena, w, u, done, next, err);
+}
+template <typename T>
+void launch_bwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32_t max_m,
+                        const int32_t* wait_on, const T* arena, T* w, int32_t* done,
+                        int32_t* next, long long* err, cudaStream_t s) {
+  if (nitems <= 0) return;
+  const int32_t ldt = max_m;
+  const size_t sm = (size_t)(kThreads / 32) * ldt * sizeof(T);
+  const int32_t grid = std::min<int32_t>((nitems + kThreads / 32 - 1) / (kThreads / 32),
+                                         8 * sm_count());
+  k_bwd_persist<T><<<grid, kThreads, sm, s>>>(F, order, nitems, ldt, wait_on, arena, w, done,
+                                              next, err);
 }
 
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
@@ -821,13 +976,22 @@ void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_
   k_gather<<<grid_for(nrt, kThreads), kThreads, 0, s>>>(values, rt_src, nrt, rt_val);
 }
 
+#define DDPS_INST_P(T)                                                                          \
+  template void launch_fwd_persist<T>(DevFronts, const int32_t*, int32_t, int32_t, const T*, T*, \
+                                      T*, int32_t*, int32_t*, long long*, cudaStream_t);         \
+  template void launch_bwd_persist<T>(DevFronts, const int32_t*, int32_t, int32_t,              \
+                                      const int32_t*, const T*, T*, int32_t*, int32_t*,          \
+                                      long long*, cudaStream_t);
+DDPS_INST_P(double)
+DDPS_INST_P(float)
+
 #define DDPS_INST_S(T)                                                                          \
   template void launch_permute_in<T>(const double*, const int32_t*, int64_t, T*, cudaStream_t); \
   template void launch_permute_out<T>(const T*, const int32_t*, int64_t, double*, cudaStream_t);\
   template void launch_fwd1<T>(DevFronts, const int32_t*, int32_t, int32_t, const T*, T*, T*,   \
-                               cudaStream_t);                                                   \
+                               cudaStream_t, int);                                              \
   template void launch_bwd1<T>(DevFronts, const int32_t*, int32_t, int32_t, const T*, T*,       \
-                               cudaStream_t);
+                               cudaStream_t, int);
 DDPS_INST_S(double)
 DDPS_INST_S(float)
 

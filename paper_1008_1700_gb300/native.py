@@ -35,7 +35,8 @@ class ddps_options(C.Structure):
                 ("rhs_chunk", C.c_int32), ("verbose", C.c_int32),
                 ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
                 ("ghat_mode", C.c_int32), ("update_prec", C.c_int32),
-                ("reduced_solver", C.c_int32), ("use_graphs", C.c_int32)]
+                ("reduced_solver", C.c_int32), ("use_graphs", C.c_int32),
+                ("persistent_solve", C.c_int32), ("autotune", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):
@@ -98,6 +99,7 @@ def load():
         "ddps_spmv": (_i32, [_p, _p, _p, _p]),
         "ddps_get_sizes": (_i32, [_p, C.POINTER(ddps_sizes)]),
         "ddps_get_interface": (_i32, [_p, _p]),
+        "ddps_get_tuning": (_i32, [_p, C.c_char_p, _i64, C.POINTER(_i64)]),
         "ddps_get_ghat_layout": (_i32, [_p, _i32, C.POINTER(_i64), C.POINTER(_i64),
                                         C.POINTER(_i64), _p]),
         "ddps_get_ghat_block": (_i32, [_p, _i32, _p, _p]),
@@ -292,6 +294,16 @@ def ddps_get_sizes(h):
     s = ddps_sizes()
     _check(load().ddps_get_sizes(h, C.byref(s)), h)
     return s.as_dict()
+
+
+def ddps_get_tuning(h):
+    """The autotuner's choices (parsed JSON)."""
+    import json
+    n = _i64()
+    _check(load().ddps_get_tuning(h, None, 0, C.byref(n)), h)
+    buf = C.create_string_buffer(n.value + 1)
+    _check(load().ddps_get_tuning(h, buf, n.value + 1, None), h)
+    return json.loads(buf.value.decode())
 
 
 def ddps_get_interface(h):

@@ -134,6 +134,9 @@ class Solver:
         N.ddps_get_reduced_solution(self.h, z, g)
         return z, g
 
+    def tuning(self):
+        return N.ddps_get_tuning(self.h)
+
     def interface(self):
         return N.ddps_get_interface(self.h)
 

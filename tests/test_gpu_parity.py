@@ -422,3 +422,56 @@ def test_graph_replay_matches_plain_launches(form):
         S.close()
     for rep in range(3):
         assert np.array_equal(xs[0][rep], xs[1][rep]), rep
+
+
+@pytest.mark.parametrize("opts", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_persistent_sweeps_match_level_launches(opts):
+    """The deep levels of small fronts swept by one persistent launch per
+    sweep (fronts ordered by completion flags) give the block solves of one
+    launch per depth (whose launch shapes, and so summation orders, the
+    autotuner may choose differently), on a 3-D slab system and on a wide
+    batch; both match the oracle's block solve to the arithmetic's accuracy."""
+    from paper_1008_1700_gb300 import Solver
+    cases = [[W.small_convdiff_3d(16, [5, 6, 5])],
+             [W.small_convdiff_2d(24, 8, seed=60 + k) for k in range(40)]]
+    for probs in cases:
+        gs = []
+        for persist in (0, 1):
+            S = Solver.from_systems([(p.rowptr, p.colind, p.values, p.block_ptr) for p in probs],
+                                    persistent_solve=persist, **opts)
+            S.factor(dev(S.values_host))
+            y = dev(np.random.default_rng(9).standard_normal(S.n))
+            gs.append(host(S.block_solve(y)).copy())
+            x, info = S.solve(dev(np.concatenate([p.f for p in probs])))
+            assert info["status"] == "DDPS_OK"
+            S.close()
+        bound = 1e-12 if opts is FP64 else 1e-5
+        assert relerr(gs[1], gs[0]) <= bound
+        p = probs[0]
+        o = DDPSOracle(p.n, p.rowptr, p.colind, p.values, p.block_ptr, spikes=False)
+        y0 = np.random.default_rng(9).standard_normal(sum(q.n for q in probs))[:p.n]
+        assert relerr(gs[1][:p.n], o.block_solve(y0)) <= (1e-12 if opts is FP64 else 1e-5)
+
+
+def test_autotuned_block_solve_shapes(tmp_path, monkeypatch):
+    """The first factor times every candidate launch shape of each block-solve
+    depth and keeps the fastest; the choices are reported, cached in the JSON
+    file DDPS_TUNE_CACHE names, and the tuned block solve matches the oracle
+    like the fixed rules do."""
+    import json
+    monkeypatch.setenv("DDPS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    P = W.small_random_band(3000, 5, 200, seed=2)  # fronts of up to 428 rows: clusters compete
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=("abs", 1e-4),
+                   spikes=False)
+    y = np.random.default_rng(4).standard_normal(P.n)
+    for tune in (0, 1):
+        S = make_solver(P, ("abs", 1e-4), autotune=tune, persistent_solve=0, **FP64)
+        t = S.tuning()
+        assert t["tuned"] == bool(tune)
+        if tune:
+            names = {"warp", "cta8", "cl1", "cl2", "cl4", "cl8"}
+            assert t["levels"] and all(l["fwd"] in names and l["bwd"] in names for l in t["levels"])
+        assert relerr(host(S.block_solve(dev(y))), o.block_solve(y)) <= 1e-12
+        S.close()
+    cache = json.loads((tmp_path / "tune.json").read_text())
+    assert cache and all(v in range(6) for v in cache.values())
