@@ -12,7 +12,8 @@ without blocking or fusion:
 * Fig. 2 step 1 / Eq. (1)-(2): ``A = D + R`` by block rows   -> ``split_block_rows``
 * Fig. 2 step 2: exact LU of every ``A_ii``                    -> ``factor_blocks``
   (the paper calls a sparse direct solver, Pardiso, for this step; the oracle
-  calls SuperLU through ``scipy.sparse.linalg.splu`` as that library step)
+  calls SuperLU through ``scipy.sparse.linalg.splu`` as that library step),
+  or the approximate variant of Sec. 3, ILU(0) in the block's order -> ``ILU0``
 * Fig. 2 step 3 / Sec. 3 dropping rule: ``R -> R~``           -> ``drop_columns``,
   plus the element-wise absolute rule of the random-band workload -> ``drop_entries``
 * Fig. 2 step 5: ``c`` = nonzero columns of ``G``             -> ``interface_columns``
@@ -38,7 +39,10 @@ Pins (tests in ``tests/test_oracle_pins.py``):
 * p = 1 (no coupling, c empty) reduces to one plain LU solve;
 * the Krylov loop against closed forms (diagonal systems, 1 iteration) and the
   true-residual invariant on every workload family;
-* Fig. 3 retrieval ``z = g - G z`` against the equivalent ``z = D~^-1 (y - R~ z^)``.
+* Fig. 3 retrieval ``z = g - G z`` against the equivalent ``z = D~^-1 (y - R~ z^)``;
+* ILU(0): (L U)_ij = a_ij on the block's pattern (the zero-fill identity),
+  exact on patterns closed under elimination (a band with its full band),
+  and brute-force elimination with the drop rule on tiny dense cases.
 Parity unpinned: none of the functions above; the iteration *counts* of the
 inexact (dropping / eps_in) variants have no independent reference and are
 compared only through the true-residual invariant.
@@ -91,6 +95,52 @@ def factor_blocks(D_blocks, permc_spec="COLAMD"):
     ``permc_spec`` is SuperLU's column ordering; it changes the fill (and so
     the time and memory) and the rounding, not the factored matrix."""
     return [spla.splu(Dii.tocsc(), permc_spec=permc_spec) for Dii in D_blocks]
+
+
+class ILU0:
+    """Incomplete LU with zero fill of one diagonal block, in the block's own
+    row order (Sec. 3: the block factors may be approximate; the paper names
+    incomplete LU as the approximate choice).  L is unit lower triangular and
+    U upper triangular, both on the sparsity pattern of the block; the
+    entries are those of Gaussian elimination (row by row, IKJ form) with
+    every update that would fall outside the pattern left out:
+        for i, for k < i with a_ik in the pattern:
+            a_ik = a_ik / a_kk
+            a_ij = a_ij - a_ik a_kj   for every j > k with a_ij and a_kj in the pattern.
+    ``solve(b)`` returns (L U)^-1 b."""
+
+    def __init__(self, Dii):
+        A = sp.csr_matrix(Dii, dtype=np.float64)
+        A.sort_indices()
+        n = A.shape[0]
+        rp, ci = A.indptr, A.indices
+        a = A.data.copy()
+        for i in range(n):
+            cols = ci[rp[i]:rp[i + 1]]
+            pos = {int(c): rp[i] + t for t, c in enumerate(cols)}
+            for t in range(rp[i], rp[i + 1]):
+                k = int(ci[t])
+                if k >= i:
+                    break
+                dk = rp[k] + int(np.searchsorted(ci[rp[k]:rp[k + 1]], k))
+                a[t] = a[t] / a[dk]
+                for u in range(dk + 1, rp[k + 1]):
+                    j = int(ci[u])
+                    if j in pos:
+                        a[pos[j]] -= a[t] * a[u]
+        F = sp.csr_matrix((a, ci.copy(), rp.copy()), shape=(n, n))
+        self.L = (sp.tril(F, k=-1) + sp.identity(n)).tocsr()
+        self.U = sp.triu(F).tocsr()
+
+    def solve(self, b):
+        b = np.asarray(b, dtype=np.float64)
+        y = spla.spsolve_triangular(self.L, b, lower=True, unit_diagonal=True)
+        return spla.spsolve_triangular(self.U, y, lower=False)
+
+
+def ilu0_blocks(D_blocks):
+    """ILU(0) of each diagonal block (the approximate variant of Fig. 2 step 2)."""
+    return [ILU0(Dii) for Dii in D_blocks]
 
 
 # ----------------------------------------------------------------------------
@@ -259,7 +309,7 @@ class DDPSOracle:
     """
 
     def __init__(self, n, rowptr, colind, values, block_ptr, drop=None, keep_full_G=True,
-                 spikes=True, permc_spec="COLAMD"):
+                 spikes=True, permc_spec="COLAMD", factor="lu"):
         self.n = int(n)
         self.A = csr(n, rowptr, colind, values)
         self.block_ptr = np.asarray(block_ptr, dtype=np.int64)
@@ -267,7 +317,9 @@ class DDPSOracle:
         # step 1
         self.D_blocks, self.R = split_block_rows(self.A, self.block_ptr)
         # step 2
-        self.lu = factor_blocks(self.D_blocks, permc_spec)
+        # step 2: exact LU, or ILU(0) for the approximate variant (Sec. 3)
+        self.lu = (ilu0_blocks(self.D_blocks) if factor == "ilu0"
+                   else factor_blocks(self.D_blocks, permc_spec))
         # step 3
         if drop is None:
             self.Rt = self.R

@@ -252,3 +252,69 @@ def test_jacobi_reference_against_lapack_and_its_bound():
         assert err > 1e-3 * bk  # the bound is not vacuous
     with pytest.raises(ValueError):
         jacobi_solution(o.A - 2.0 * sp.diags(o.A.diagonal()) * 0.8, P.f)
+
+
+def _ilu_brute(Ad):
+    """Dense Gaussian elimination with every update outside the pattern of
+    Ad dropped (the definition of ILU(0)), tiny matrices only."""
+    n = Ad.shape[0]
+    pat = Ad != 0
+    a = Ad.astype(float).copy()
+    for k in range(n):
+        for i in range(k + 1, n):
+            if not pat[i, k]:
+                continue
+            a[i, k] /= a[k, k]
+            for j in range(k + 1, n):
+                if pat[i, j] and pat[k, j]:
+                    a[i, j] -= a[i, k] * a[k, j]
+    return np.tril(a, -1) + np.eye(n), np.triu(a)
+
+
+def test_ilu0_zero_fill_identity_and_brute_force():
+    """ILU(0): L U agrees with A on A's pattern; L and U equal brute-force
+    elimination with the zero-fill rule (KIJ order: a different loop order of
+    the same definition); a solve applies (L U)^-1."""
+    from oracle.ddps_oracle import ILU0
+    for seed in range(4):
+        P = W.small_random_dd(40, 1, k_off=3, dd=1.3, seed=seed)
+        Ad = _dense(P)
+        f = ILU0(sp.csr_matrix(Ad))
+        L, U = f.L.toarray(), f.U.toarray()
+        pat = Ad != 0
+        assert np.max(np.abs((L @ U - Ad)[pat])) <= 1e-12 * np.max(np.abs(Ad))
+        assert np.all(L[~pat & ~np.eye(40, dtype=bool)] == 0) and np.all(U[~pat] == 0)
+        Lb, Ub = _ilu_brute(Ad)
+        assert np.max(np.abs(L - Lb)) <= 1e-12 and np.max(np.abs(U - Ub)) <= 1e-12 * np.max(np.abs(Ad))
+        b = np.random.default_rng(seed).standard_normal(40)
+        assert np.max(np.abs(L @ U @ f.solve(b) - b)) <= 1e-11 * np.max(np.abs(b))
+
+
+def test_ilu0_is_exact_on_a_closed_pattern():
+    """On a matrix with a full band (every fill entry of Gaussian elimination
+    lies inside the band) ILU(0) is the exact LU: L U = A and the solve is
+    A^-1 b (checked against LAPACK)."""
+    from oracle.ddps_oracle import ILU0
+    rng = np.random.default_rng(5)
+    n, bw = 60, 4
+    Ad = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - bw), min(n, i + bw + 1)):
+            Ad[i, j] = rng.standard_normal()
+        Ad[i, i] = 2 * bw + 2.0
+    f = ILU0(sp.csr_matrix(Ad))
+    assert np.max(np.abs(f.L.toarray() @ f.U.toarray() - Ad)) <= 1e-12 * np.max(np.abs(Ad))
+    b = rng.standard_normal(n)
+    assert np.max(np.abs(f.solve(b) - np.linalg.solve(Ad, b))) <= 1e-12 * np.max(np.abs(np.linalg.solve(Ad, b)))
+
+
+def test_ilu_variant_still_converges_to_the_solution():
+    """DDPS with ILU(0) block factors (Sec. 3: approximate LU) is no longer a
+    direct solver, but the outer Krylov iteration still reaches the true
+    residual tolerance and the LAPACK solution."""
+    P = W.small_convdiff_3d(10, [3, 4, 3])
+    o = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, factor="ilu0")
+    x, info = o.solve(P.f, tol=1e-12, eps_in=1e-6, maxit_in=200)
+    assert info["converged"] and info["iterations"] > 1.0
+    x_ref = np.linalg.solve(_dense(P), P.f)
+    assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
