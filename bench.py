@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--workload", default="cd3d_64_slabs16",
                     choices=["cd3d_64_slabs16", "cd2d_64_p4", "cd3d_48_slabs8", "cd2d_batch256",
                              "randband_1m", "cd3d_48_seq"])
-    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64", "implicit", "direct"],
+    ap.add_argument("--form", choices=["mixed", "mixed_simt", "fp64", "implicit", "direct", "ilu"],
                     default="mixed",
                     help="mixed: the paper's method with FP32 factors, tensor-core spikes and "
                          "FP16 G^; implicit: the variant that applies G^ by block solves "
@@ -138,6 +138,11 @@ def form_options(form):
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_BF16X3, ghat_prec=N.DDPS_FP16,
                     inner_prec=N.DDPS_FP32, update_prec=N.DDPS_BF16X3,
                     reduced_solver=N.DDPS_REDUCED_DIRECT)
+    elif form == "ilu":
+        # Sec. 3's approximate block factors: ILU(0) in FP32, SIMT spike solves,
+        # FP16 G^, FP32 inner vectors, FP64 outer
+        base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP16,
+                    inner_prec=N.DDPS_FP32, factor_kind=N.DDPS_FACTOR_ILU0)
     elif form == "implicit":
         # variant (departs from Fig. 2 step 4): no spikes, G^ v = v + (D~^-1 R~ v)(c)
         base.update(factor_prec=N.DDPS_FP32, spike_prec=N.DDPS_FP32, ghat_prec=N.DDPS_FP32,
@@ -234,7 +239,7 @@ TRAFFIC_RATIO = {"ghat_matvec": (1.012, "ncu --set full, k_ghat_matvec_tiled<__h
 def algorithmic_work(sizes, P, form, steps, prof):
     """Per class: (kind, total algorithmic amount over the timed region)."""
     sf = 8 if form == "fp64" else 4
-    sg = 8 if form == "fp64" else (2 if form in ("mixed", "direct") else 4)  # G^ storage
+    sg = 8 if form == "fp64" else (2 if form in ("mixed", "direct", "ilu") else 4)  # G^ storage
     si = sf
     n, nnz, m = sizes["n"], sizes["nnz"], sizes["m"]
     out = {}
@@ -745,6 +750,8 @@ def run_ours(args):
             # variant: 6.3 solved directly (block LU of the block-tridiagonal G^)
             line["direct_reduced"] = measure_workload(args.workload, "direct", 3, 1, stream,
                                                       solve_only=True)
+        # variant: ILU(0) block factors (approximate LU, Sec. 3)
+        line["ilu0_factors"] = measure_workload(args.workload, "ilu", 3, 1, stream)
     S.close()
     del vals, f, x
     torch.cuda.empty_cache()

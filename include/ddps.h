@@ -82,6 +82,13 @@ typedef enum { DDPS_GHAT_EXPLICIT = 0, DDPS_GHAT_IMPLICIT = 1 } ddps_ghat_mode;
  * application solves with it: no inner iterations (Sec. 3 direct mode when
  * nothing is dropped). */
 typedef enum { DDPS_REDUCED_ITERATIVE = 0, DDPS_REDUCED_DIRECT = 1 } ddps_reduced_solver;
+/* Fig. 2 step 2: the block factors "approximate or exact" (Sec. 3).
+ * LU: exact multifrontal LU over a nested-dissection order of every block.
+ * ILU0: incomplete LU with zero fill on the pattern of every block, in the
+ * block's own row order; G = D~^-1 R~ then uses D~ = L~ U~, and the outer
+ * Krylov iteration absorbs the approximation (P = D~ + R~ is no longer A
+ * even without dropping).  Spike products run in factor_prec (SIMT). */
+typedef enum { DDPS_FACTOR_LU = 0, DDPS_FACTOR_ILU0 = 1 } ddps_factor_kind;
 
 typedef struct {
   int32_t drop_mode;      /* ddps_drop_mode */
@@ -129,6 +136,7 @@ typedef struct {
                              fronts ordered by per-front completion flags with bounded waits
                              (a wait that runs out makes ddps_solve return DDPS_ERR_TIMEOUT);
                              0: one launch per tree depth */
+  int32_t factor_kind;    /* a ddps_factor_kind value; 0 = exact LU */
   int32_t autotune;       /* 1 (default): the first ddps_factor times every candidate launch shape
                              of each block-solve depth and sweep (warp per front, CTA per front,
                              clusters of 1-8 CTAs) on the handle's factors and keeps the fastest;

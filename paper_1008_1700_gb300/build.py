@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["analyze.cpp", "api.cu", "factor.cu", "spike.cu", "spike_tc.cu", "solve.cu", "krylov.cu",
-           "mlp.cu", "reduced_direct.cu"]
+           "mlp.cu", "reduced_direct.cu", "ilu.cu"]
 
 
 def _nvcc() -> str:

@@ -357,7 +357,12 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
   };
   std::vector<FrontTmp> F;
   std::vector<int32_t> roots;
-  for (int32_t b = 0; b < p; ++b) {
+  A.ilu = opt.factor_kind == DDPS_FACTOR_ILU0;
+  if (A.ilu) {
+    // ILU(0) keeps every block in its own row order: no dissection, no fronts
+    for (int64_t i = 0; i < n; ++i) A.perm[i] = A.iperm[i] = (int32_t)i;
+  }
+  for (int32_t b = 0; b < (A.ilu ? 0 : p); ++b) {
     int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
     Graph g = block_graph(rowptr, colind, r0, r1);
     NestedDissection nd(g, leaf);
@@ -524,7 +529,63 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
 
   // ---- assembly map: D entries -> front positions; R entries -> -1 ----------
   A.amap.assign(nnz, -1);
-  for (int64_t i = 0; i < n; ++i) {
+  if (A.ilu) {
+    // ILU(0): the D entries of each row, in order, form the factor's CSR; the
+    // map sends entry e to its position there
+    A.il_rp.assign(n + 1, 0);
+    A.il_diag.assign(n, -1);
+    A.il_row_block.assign(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      A.il_row_block[i] = row_block[i];
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        if (!is_d[e]) continue;
+        if (colind[e] == i) A.il_diag[i] = (int32_t)A.il_col.size();
+        A.amap[e] = (int64_t)A.il_col.size();
+        A.il_col.push_back(colind[e]);
+      }
+      A.il_rp[i + 1] = (int32_t)A.il_col.size();
+      if (A.il_diag[i] < 0) {
+        err << "ddps_analyze: ILU(0) needs every diagonal entry stored (row " << i << ")";
+        return err.str();
+      }
+    }
+    // levels: L dependencies (k < i) forward, U dependencies (j > i) backward
+    std::vector<int32_t> lf(n, 0), lb(n, 0);
+    int32_t nlf = 0, nlb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int32_t e = A.il_rp[i]; e < A.il_diag[i]; ++e) lf[i] = std::max(lf[i], lf[A.il_col[e]] + 1);
+      nlf = std::max(nlf, lf[i] + 1);
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      for (int32_t e = A.il_diag[i] + 1; e < A.il_rp[i + 1]; ++e)
+        lb[i] = std::max(lb[i], lb[A.il_col[e]] + 1);
+      nlb = std::max(nlb, lb[i] + 1);
+    }
+    auto bucket = [&](const std::vector<int32_t>& lev, int32_t nl, std::vector<int32_t>& rows,
+                      std::vector<int32_t>& ptr) {
+      ptr.assign(nl + 1, 0);
+      for (int64_t i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+      for (int32_t l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+      rows.resize(n);
+      std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+      for (int64_t i = 0; i < n; ++i) rows[fill[lev[i]]++] = (int32_t)i;
+    };
+    bucket(lf, nlf, A.il_lf, A.il_lf_ptr);
+    bucket(lb, nlb, A.il_lb, A.il_lb_ptr);
+    // flops of the factorisation (1 division and 2 per update) and entries a solve streams
+    for (int64_t i = 0; i < n; ++i)
+      for (int32_t e = A.il_rp[i]; e < A.il_diag[i]; ++e) {
+        const int32_t k = A.il_col[e];
+        int32_t q = e + 1, upd = 0;
+        for (int32_t u = A.il_diag[k] + 1; u < A.il_rp[k + 1]; ++u) {
+          while (q < A.il_rp[i + 1] && A.il_col[q] < A.il_col[u]) ++q;
+          if (q < A.il_rp[i + 1] && A.il_col[q] == A.il_col[u]) ++upd;
+        }
+        A.factor_flops += 1.0 + 2.0 * upd;
+      }
+    A.factor_lu_entries = (int64_t)A.il_col.size();
+  }
+  for (int64_t i = 0; i < (A.ilu ? 0 : n); ++i) {
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
       if (!is_d[e]) continue;
       int32_t a = A.iperm[i], bn = A.iperm[colind[e]];
@@ -569,6 +630,7 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     double blk_lu = 0;
     for (int32_t f = 0; f < nf; ++f)
       if (A.f_block[f] == b) blk_lu += (double)A.f_k[f] * (2.0 * A.f_m[f] - A.f_k[f]);
+    if (A.ilu) blk_lu = (double)(A.il_rp[r1] - A.il_rp[r0]) / 2.0;
     A.spike_flops += 4.0 * blk_lu * (double)cols.size();
   }
   for (int64_t i = 0; i < n; ++i) {

@@ -203,6 +203,10 @@ struct ddps_handle {
   std::vector<ProfRec> prof_recs;
   double prof_ms[DDPS_PROF_CLASSES] = {};
   int64_t prof_cnt[DDPS_PROF_CLASSES] = {};
+  // ILU(0) factors (factor_kind ILU0): CSR structure, levels, values
+  IluDev il{};
+  int32_t *il_lf = nullptr, *il_lb = nullptr;
+  void* il_val = nullptr;
   // launch shape of every block-solve depth and sweep (SOLVE_AUTO until tuned)
   std::vector<int> tune_fwd, tune_bwd;
   std::vector<float> tune_fwd_ms, tune_bwd_ms;
@@ -431,8 +435,75 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
 // ---------------------------------------------------------------------------
 // Fig. 2 steps 2 and 4 on the device
 // ---------------------------------------------------------------------------
+// Fig. 2 steps 2 and 4 with ILU(0) block factors: scatter, level-scheduled
+// factorisation, then the spikes by level-scheduled L and U solves on the
+// panels of coupling columns.
+template <typename T, typename TG>
+void factor_launches_ilu(ddps_handle* h, cudaStream_t s) {
+  const Analysis& A = h->A;
+  T* a = (T*)h->il_val;
+  CK(cudaMemsetAsync(h->derr, 0, 3 * sizeof(long long), s));
+  {
+    Prof pr(h, DDPS_PROF_ASSEMBLE, s);
+    launch_assemble<T>(h->vals, h->amap, A.nnz, a, s);
+    launch_row_absmax(h->rowptr, h->amap, h->vals, h->iperm, A.n, h->rownorm, s);
+    h->launches += 2;
+  }
+  {
+    Prof pr(h, DDPS_PROF_FRONT_LU, s);
+    for (size_t l = 0; l + 1 < A.il_lf_ptr.size(); ++l) {
+      launch_ilu0_level<T>(h->il_lf + A.il_lf_ptr[l], A.il_lf_ptr[l + 1] - A.il_lf_ptr[l], h->il, a,
+                           h->rownorm, h->opt.pivot_tol, h->derr, s);
+      h->launches++;
+    }
+  }
+  launch_gather_rt_values(h->vals, h->rt_src, h->nrt, h->rt_val, s);
+  h->launches++;
+  const int64_t m = (int64_t)A.c.size();
+  if (m > 0 && h->opt.ghat_mode == DDPS_GHAT_EXPLICIT) {
+    T* X = (T*)h->X;
+    const int32_t NR = h->NR;
+    for (int64_t j0 = 0; j0 < A.max_rhs; j0 += NR) {
+      CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
+      launch_spike_rhs<T>(h->rt_rownew, h->rt_rhscol, h->rt_src, h->nrt, h->vals, j0, NR, X, s);
+      h->launches++;
+      {
+        Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
+        for (size_t l = 0; l + 1 < A.il_lf_ptr.size(); ++l) {
+          launch_ilu_panel_level<T>(true, h->il_lf + A.il_lf_ptr[l],
+                                    A.il_lf_ptr[l + 1] - A.il_lf_ptr[l], h->il, a,
+                                    h->block_ncols, j0, NR, X, s);
+          h->launches++;
+        }
+      }
+      {
+        Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
+        for (size_t l = 0; l + 1 < A.il_lb_ptr.size(); ++l) {
+          launch_ilu_panel_level<T>(false, h->il_lb + A.il_lb_ptr[l],
+                                    A.il_lb_ptr[l + 1] - A.il_lb_ptr[l], h->il, a,
+                                    h->block_ncols, j0, NR, X, s);
+          h->launches++;
+        }
+      }
+      Prof pr(h, DDPS_PROF_GHAT_EXTRACT, s);
+      launch_ghat_extract<T, TG>(h->qblock, h->c_rownew, h->gq0, h->gcol_ptr, h->ghat_off, h->gld,
+                                 m, j0, NR, X, (TG*)h->ghat, s);
+      h->launches++;
+    }
+  }
+  if (h->use_direct) {
+    Prof pr(h, DDPS_PROF_DIRECT_FACTOR, s);
+    h->launches += direct_factor<TG>(h->direct, (const TG*)h->ghat, s);
+  }
+  check_launch();
+}
+
 template <typename T, typename TG>
 void factor_launches(ddps_handle* h, cudaStream_t s) {
+  if (h->A.ilu) {
+    factor_launches_ilu<T, TG>(h, s);
+    return;
+  }
   const Analysis& A = h->A;
   T* arena = (T*)h->arena;
   CK(cudaMemsetAsync(arena, 0, (size_t)A.arena_size * sizeof(T), s));
@@ -587,7 +658,10 @@ void factor_impl(ddps_handle* h, cudaStream_t s) {
   if (h->herr[0] != 0) {
     const int64_t row_new = h->herr[2];
     const int64_t row_old = h->A.perm[row_new];
-    const int32_t b = h->A.f_block[h->herr[1]];
+    const int32_t b =
+        h->herr[1] >= 0 ? h->A.f_block[h->herr[1]]
+                        : (int32_t)(std::upper_bound(h->A.block_ptr.begin(), h->A.block_ptr.end(),
+                                                     row_old) - h->A.block_ptr.begin() - 1);
     throw Fail{DDPS_ERR_SINGULAR_BLOCK,
                "pivot below threshold in diagonal block " + std::to_string(b) + " at row " +
                    std::to_string((long long)row_old)};
@@ -608,6 +682,18 @@ void block_solve_impl(ddps_handle* h, const double* y, double* g, cudaStream_t s
   const T* arena = (const T*)h->arena;
   Prof pr(h, prof_cls, s);
   launch_permute_in<T>(y, h->perm, A.n, w, s);
+  if (A.ilu) {  // (L~ U~)^-1 y: level-scheduled triangular solves
+    const T* a = (const T*)h->il_val;
+    for (size_t l = 0; l + 1 < A.il_lf_ptr.size(); ++l)
+      launch_ilu_vec_level<T>(true, h->il_lf + A.il_lf_ptr[l], A.il_lf_ptr[l + 1] - A.il_lf_ptr[l],
+                              h->il, a, w, s);
+    for (size_t l = 0; l + 1 < A.il_lb_ptr.size(); ++l)
+      launch_ilu_vec_level<T>(false, h->il_lb + A.il_lb_ptr[l], A.il_lb_ptr[l + 1] - A.il_lb_ptr[l],
+                              h->il, a, w, s);
+    launch_permute_out<T>(w, h->perm, A.n, g, s);
+    h->launches += 2 + (int64_t)A.il_lf_ptr.size() - 1 + (int64_t)A.il_lb_ptr.size() - 1;
+    return;
+  }
   // levels >= top: one persistent launch per sweep; the levels above: one launch each
   const int top = h->persist_L >= 0 ? h->persist_L : A.nlevels;
   const int64_t nf = (int64_t)A.f_k.size();
@@ -752,7 +838,8 @@ void autotune_block_solve(ddps_handle* h, cudaStream_t s) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (added) tune_cache_write();
+  if (added || (std::getenv("DDPS_TUNE_CACHE") && !std::ifstream(std::getenv("DDPS_TUNE_CACHE"))))
+    tune_cache_write();
   h->tuned = true;
 }
 
@@ -1381,6 +1468,15 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   h->w = dalloc_bytes(h, n * (int64_t)fs);
   h->rownorm = dalloc<double>(h, n);
   h->derr = dalloc<long long>(h, 3);
+  if (A.ilu) {
+    h->il.rp = dupload(h, A.il_rp);
+    h->il.col = dupload(h, A.il_col);
+    h->il.diag = dupload(h, A.il_diag);
+    h->il.row_block = dupload(h, A.il_row_block);
+    h->il_lf = dupload(h, A.il_lf);
+    h->il_lb = dupload(h, A.il_lb);
+    h->il_val = dalloc_bytes(h, std::max<int64_t>((int64_t)A.il_col.size(), 1) * (int64_t)fs);
+  }
   CK(cudaMallocHost((void**)&h->herr, 3 * sizeof(long long)));
   // R~
   h->nrt = (int64_t)A.rt_col.size();
@@ -1661,7 +1757,15 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       h->wpk_nb = (int32_t)pb.size();
       h->wpk_nf = (int32_t)pf.size();
     }
-    build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf);
+    if (!A.ilu) {
+      build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf);
+    } else {
+      // ILU(0): G^ keeps the coupling columns in ascending order
+      h->gperm.resize(A.gcol_ptr[A.p]);
+      for (int32_t b = 0; b < A.p; ++b)
+        for (int64_t pc = A.gcol_ptr[b]; pc < A.gcol_ptr[b + 1]; ++pc)
+          h->gperm[pc] = (int32_t)(pc - A.gcol_ptr[b]);
+    }
   }
   // segments
   h->nseg = A.nsys;
@@ -1751,6 +1855,14 @@ bool valid_options(const ddps_options& o, std::string& why) {
   }
   if (o.inner_prec != DDPS_FP64 && o.inner_prec != DDPS_FP32) {
     why = "inner_prec must be FP64 or FP32";
+    return false;
+  }
+  if (o.factor_kind != DDPS_FACTOR_LU && o.factor_kind != DDPS_FACTOR_ILU0) {
+    why = "factor_kind must be LU or ILU0";
+    return false;
+  }
+  if (o.factor_kind == DDPS_FACTOR_ILU0 && o.spike_prec != o.factor_prec) {
+    why = "ILU0 block factors take spike_prec equal to factor_prec (SIMT spike solves)";
     return false;
   }
   if (o.reduced_solver != DDPS_REDUCED_ITERATIVE && o.reduced_solver != DDPS_REDUCED_DIRECT) {
@@ -1894,7 +2006,7 @@ static ddps_status factor_values(ddps_handle* h, const double* values, bool host
       else
         factor_impl<float, __nv_bfloat16>(h, s);
     }
-    if (h->opt.autotune && !h->tuned) {
+    if (h->opt.autotune && !h->tuned && !h->A.ilu) {
       if (fp == DDPS_FP64)
         autotune_block_solve<double>(h, s);
       else

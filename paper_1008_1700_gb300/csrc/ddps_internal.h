@@ -52,6 +52,14 @@ struct Analysis {
   std::vector<int32_t> gcols;        // reduced indices of the coupling columns (ascending)
   int64_t ghat_entries = 0, max_rhs = 0, max_front = 0, factor_lu_entries = 0;
   double factor_flops = 0, spike_flops = 0;
+
+  // ILU(0) factors (factor_kind ILU0): the blocks keep their own row order
+  // (perm is the identity, no fronts); CSR of the diagonal blocks, diagonal
+  // positions, and the rows grouped in levels for the L and the U solves
+  // (il_lb: level 0 = rows whose U part references no other row).
+  bool ilu = false;
+  std::vector<int32_t> il_rp, il_col, il_diag, il_row_block;
+  std::vector<int32_t> il_lf, il_lf_ptr, il_lb, il_lb_ptr;
 };
 
 // Builds the analysis.  Returns an empty string on success, else the error.

@@ -79,6 +79,26 @@ void launch_bwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32
                         const int32_t* wait_on, const T* arena, T* w, int32_t* done,
                         int32_t* next, long long* err, cudaStream_t s);
 
+// ---- ilu.cu: ILU(0) block factors (factor_kind ILU0) ----
+// CSR of the diagonal blocks (global rows and columns, sorted), position of
+// each row's diagonal, block of each row.
+struct IluDev {
+  const int32_t* rp;
+  const int32_t* col;
+  const int32_t* diag;
+  const int32_t* row_block;
+};
+template <typename T>
+void launch_ilu0_level(const int32_t* rows, int32_t nrows, const IluDev& L, T* a,
+                       const double* rownorm, double pivot_tol, long long* err, cudaStream_t s);
+template <typename T>
+void launch_ilu_vec_level(bool fwd, const int32_t* rows, int32_t nrows, const IluDev& L,
+                          const T* a, T* x, cudaStream_t s);
+template <typename T>
+void launch_ilu_panel_level(bool fwd, const int32_t* rows, int32_t nrows, const IluDev& L,
+                            const T* a, const int64_t* block_ncols, int64_t j0, int32_t NR, T* X,
+                            cudaStream_t s);
+
 // ---- factor.cu --------------------------------------------------------------
 template <typename T>
 void launch_assemble(const double* values, const int64_t* amap, int64_t nnz, T* arena,

@@ -20,6 +20,7 @@ DDPS_FP64, DDPS_FP32, DDPS_BF16, DDPS_BF16X3, DDPS_FP16 = 0, 1, 2, 3, 4
 DDPS_DROP_NONE, DDPS_DROP_COLUMN, DDPS_DROP_ABS = 0, 1, 2
 DDPS_GHAT_EXPLICIT, DDPS_GHAT_IMPLICIT = 0, 1
 DDPS_REDUCED_ITERATIVE, DDPS_REDUCED_DIRECT = 0, 1
+DDPS_FACTOR_LU, DDPS_FACTOR_ILU0 = 0, 1
 STATUS = {0: "DDPS_OK", 1: "DDPS_ERR_INVALID_ARG", 2: "DDPS_ERR_SINGULAR_BLOCK",
           3: "DDPS_ERR_NOT_CONVERGED", 4: "DDPS_ERR_OUT_OF_MEMORY", 5: "DDPS_ERR_CUDA",
           6: "DDPS_ERR_TIMEOUT", 7: "DDPS_ERR_STATE"}
@@ -36,7 +37,8 @@ class ddps_options(C.Structure):
                 ("debug_wait_timeout", C.c_int32), ("fused_rows", C.c_int32),
                 ("ghat_mode", C.c_int32), ("update_prec", C.c_int32),
                 ("reduced_solver", C.c_int32), ("use_graphs", C.c_int32),
-                ("persistent_solve", C.c_int32), ("autotune", C.c_int32)]
+                ("persistent_solve", C.c_int32), ("factor_kind", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):
