@@ -484,7 +484,8 @@ def kernel_table(prof, work, ms_total, peaks):
     return kern
 
 
-def measure_workload(name, form, steps, warmup, stream, extra_opts=None, solve_only=False):
+def measure_workload(name, form, steps, warmup, stream, extra_opts=None, solve_only=False,
+                     profile=False):
     """Factor + solve steps of one workload in one form (profiling off):
     solves/s and accuracy; used for the sub-results of the bench line."""
     import numpy as np
@@ -538,6 +539,15 @@ def measure_workload(name, form, steps, warmup, stream, extra_opts=None, solve_o
         prof = S.profile(reset=True)
         S.set_profiling(0)
         out["classes_ms"] = {k: round(v[0], 3) for k, v in prof.items() if v[1]}
+    if profile:
+        # one profiled factor + solve: per-class time, rate and fraction of the HBM peak
+        S.set_profiling((1 << len(N.PROF_CLASSES)) - 1)
+        S.profile(reset=True)
+        pms, _ = timed(stream, step, 1)
+        prof = S.profile(reset=True)
+        S.set_profiling(0)
+        out["kernels"] = kernel_table(prof, algorithmic_work(S.sizes, P, form, 1, prof), pms,
+                                      load_peaks())
     S.close()
     del vals, f, x
     torch.cuda.empty_cache()
@@ -759,8 +769,8 @@ def run_ours(args):
     if extras and args.workload == "cd3d_64_slabs16":
         # the other workloads, driver-visible: a short timed run of each
         line["workloads"] = {
-            "cd2d_batch256": measure_workload("cd2d_batch256", "mixed", 3, 2, stream),
-            "randband_1m": measure_workload("randband_1m", "mixed", 2, 1, stream),
+            "cd2d_batch256": measure_workload("cd2d_batch256", "mixed", 3, 2, stream, profile=True),
+            "randband_1m": measure_workload("randband_1m", "mixed", 2, 1, stream, profile=True),
         }
         line["workloads"]["cd3d_48_seq"] = sequence_result(args.form, 10, stream)
 
