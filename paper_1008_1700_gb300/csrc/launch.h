@@ -220,7 +220,7 @@ template <typename T>
 void launch_permute_out(const T* w, const int32_t* perm, int64_t n, double* g, cudaStream_t s);
 // Launch shapes of a block-solve depth (see launch_fwd1): automatic, one warp
 // per front, one CTA per front with eight loads in flight per lane, or a
-// cluster of 1, 2, 4 or 8 CTAs per front with sixteen.
+// cluster of 1, 2, 4 or 8 CTAs per front with thirty-two.
 enum { SOLVE_AUTO = -1, SOLVE_WARP = 0, SOLVE_CTA8 = 1, SOLVE_CL1 = 2, SOLVE_CL2 = 3,
        SOLVE_CL4 = 4, SOLVE_CL8 = 5 };
 inline int solve_cfg_cluster(int c) { return c >= 8 ? SOLVE_CL8 : c >= 4 ? SOLVE_CL4 : c >= 2 ? SOLVE_CL2 : SOLVE_CL1; }

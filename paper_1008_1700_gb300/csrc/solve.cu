@@ -72,19 +72,17 @@ __device__ __forceinline__ void cta_matvec(const T* __restrict__ A, int64_t m, i
       if (i < c1) {
         const T* __restrict__ Ai = A + (roff + i) + (int64_t)coff * m;
         for (int j = jb; j < je; j += B) {
-          T a[B], xv[B];
+          // the B column loads go out first; x comes from shared memory as
+          // the products are formed
+          T a[B];
 #pragma unroll
-          for (int q = 0; q < B; ++q) {
-            const bool in = j + q < je;
-            a[q] = in ? Ai[(int64_t)(j + q) * m] : T(0);
-            xv[q] = in ? x[j + q] : T(0);
-          }
+          for (int q = 0; q < B; ++q) a[q] = j + q < je ? Ai[(int64_t)(j + q) * m] : T(0);
 #pragma unroll
           for (int q = 0; q < B; q += 4) {
-            s0 += a[q] * xv[q];
-            s1 += a[q + 1] * xv[q + 1];
-            s2 += a[q + 2] * xv[q + 2];
-            s3 += a[q + 3] * xv[q + 3];
+            s0 += a[q] * (j + q < je ? x[j + q] : T(0));
+            s1 += a[q + 1] * (j + q + 1 < je ? x[j + q + 1] : T(0));
+            s2 += a[q + 2] * (j + q + 2 < je ? x[j + q + 2] : T(0));
+            s3 += a[q + 3] * (j + q + 3 < je ? x[j + q + 3] : T(0));
           }
         }
       }
@@ -107,16 +105,36 @@ __device__ __forceinline__ void cta_rows(int n, int rank, int nct, int* a, int* 
   *b = min(n, *a + per);
 }
 
+// Rows [*a, *b) of a k x k triangle taken by CTA `rank` of `nct`, split so
+// that every CTA reads about the same number of entries (row i of a lower
+// triangle holds i entries, of an upper one k - i): boundaries at
+// k sqrt(r / nct) (lower) or k (1 - sqrt(1 - r / nct)) (upper), in 32-row
+// multiples.
+__device__ __forceinline__ int tri_bound(int k, int r, int nct, bool lower) {
+  if (r <= 0) return 0;
+  if (r >= nct) return k;
+  const float f = (float)r / (float)nct;
+  const float x = lower ? sqrtf(f) : 1.f - sqrtf(1.f - f);
+  return min(k, ((int)(x * (float)k) + 31) / 32 * 32);
+}
+__device__ __forceinline__ void cta_rows_tri(int k, int rank, int nct, bool lower, int* a, int* b) {
+  *a = tri_bound(k, rank, nct, lower);
+  *b = max(*a, tri_bound(k, rank + 1, nct, lower));
+}
+
 // Copies the ranges of v that the cluster's other CTAs computed (cta_rows
 // split of n) from their shared memory into this CTA's copy.
 template <typename T>
-__device__ __forceinline__ void cluster_gather(T* v, int n) {
+__device__ __forceinline__ void cluster_gather(T* v, int n, int tri = 0) {
   cg::cluster_group cl = cg::this_cluster();
   const int nct = (int)cl.num_blocks(), me = (int)cl.block_rank();
   for (int q = 0; q < nct; ++q) {
     if (q == me) continue;
     int a, b;
-    cta_rows(n, q, nct, &a, &b);
+    if (tri)
+      cta_rows_tri(n, q, nct, tri == 1, &a, &b);
+    else
+      cta_rows(n, q, nct, &a, &b);
     const T* rv = cl.map_shared_rank(v, q);
     for (int i = a + (int)threadIdx.x; i < b; i += blockDim.x) v[i] = rv[i];
   }
@@ -158,7 +176,7 @@ constexpr int kMaxChildren = 16;
 // rows over the cluster, goes back to w, and the update entries t(upd) - L21 y
 // go to u for the parent.
 template <typename T, int NT, int CH, int NSEG, int B>
-__global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
+__global__ void __launch_bounds__(NT, B == 8 ? 8 : 2)
     k_fwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
            T* __restrict__ w, T* __restrict__ u) {
   extern __shared__ unsigned char smem_raw[];
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
     ch_upd[tid] = F.upd[c];
   }
   int a, b, a2, b2;
-  cta_rows(k, rank, nct, &a, &b);
+  cta_rows_tri(k, rank, nct, true, &a, &b);
   cta_rows(m - k, rank, nct, &a2, &b2);
   prefetch_rows<T, NT>(A, m, a, b, 0, k);
   prefetch_rows<T, NT>(A, m, k + a2, k + b2, 0, k);
@@ -211,7 +229,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   cta_matvec<T, NT, CH, NSEG, B, 1>(A, m, 0, 0, a, b, k, t, red, [&](int i, T v) { y[i] = t[i] + v; });
   if (nct > 1) {
     cl.sync();  // every CTA has read w and written its rows of y
-    cluster_gather(y, k);
+    cluster_gather(y, k, 1);
   }
   for (int i = a + tid; i < b; i += blockDim.x) w[row0 + i] = y[i];
   __syncthreads();
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
 // x_upd are ancestor pivots of w.  Both products are split by rows over the
 // cluster; the CTAs exchange their parts of the intermediate vector.
 template <typename T, int NT, int CH, int NSEG, int B>
-__global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
+__global__ void __launch_bounds__(NT, B == 8 ? 8 : 2)
     k_bwd1(DevFronts F, const int32_t* __restrict__ list, const T* __restrict__ arena,
            T* __restrict__ w) {
   extern __shared__ unsigned char smem_raw[];
@@ -242,9 +260,12 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
   const int tid = threadIdx.x;
   T* xu = t + k;
   int a, b;
+  int a2, b2;  // rows of the triangular product, split by area
   cta_rows(k, rank, nct, &a, &b);
+  cta_rows_tri(k, rank, nct, false, &a2, &b2);
   const int32_t i0 = tid < r ? idx[k + tid] : 0;
-  prefetch_rows<T, NT>(A, m, a, b, 0, m);
+  prefetch_rows<T, NT>(A, m, a, b, k, m);
+  prefetch_rows<T, NT>(A, m, a2, b2, 0, k);
   pdl_wait();
   if (tid < r) xu[tid] = w[i0];
   for (int j = tid + NT; j < r; j += NT) xu[j] = w[idx[k + j]];
@@ -255,7 +276,7 @@ __global__ void __launch_bounds__(NT, B == 8 ? 8 : 1)
     cluster_gather(t, k);
     __syncthreads();
   }
-  cta_matvec<T, NT, CH, NSEG, B, 2>(A, m, 0, 0, a, b, k, t, red, [&](int i, T v) { w[row0 + i] = v; });
+  cta_matvec<T, NT, CH, NSEG, B, 2>(A, m, 0, 0, a2, b2, k, t, red, [&](int i, T v) { w[row0 + i] = v; });
   if (nct > 1) cl.sync();
 }
 
@@ -785,7 +806,7 @@ static int sm_count() { return device_sm_count(); }
 // Levels with more fronts than two per SM keep eight loads in flight per
 // lane (more CTAs resident); the others take a cluster of up to eight CTAs
 // per front, within two CTAs per SM (always eight for very large fronts),
-// and sixteen loads per lane.
+// and kSolveB loads per lane.
 template <typename K, typename... Args>
 static void launch_clustered(K kern, int32_t nf, int c, size_t sm, cudaStream_t s, Args... args) {
   if (sm > 48 * 1024)
@@ -820,7 +841,12 @@ static int solve_cluster(int32_t nf, int32_t max_m) {
   return c;
 }
 constexpr int kSolveCh = 256;
+// loads in flight per lane in the cluster kernels of the block solve, and
+// the rows they take per block-wide step (fewer barriers than kSolveCh)
+constexpr int kSolveB = 32;
+constexpr int kSolveChW = 512;
 constexpr int kSolveRed = 8 * kSolveCh;
+constexpr int kSolveRedW = 8 * kSolveChW;
 
 // Depths of many fronts of at most kWarpSolveM rows take a warp per front.
 constexpr int kWarpSolveM = 128;
@@ -846,12 +872,12 @@ void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
     launch_clustered(k_fwd1w<T>, grid, 1, smw, s, F, list, nf, ldt, arena, w, u);
     return;
   }
-  const size_t sm = ((size_t)2 * max_m + kSolveRed) * sizeof(T);
   if (cfg == SOLVE_CTA8)
-    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w, u);
+    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1,
+                     ((size_t)2 * max_m + kSolveRed) * sizeof(T), s, F, list, arena, w, u);
   else
-    launch_clustered(k_fwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cfg_size(cfg), sm, s, F, list,
-                     arena, w, u);
+    launch_clustered(k_fwd1<T, kThreads, kSolveChW, 8, kSolveB>, nf, solve_cfg_size(cfg),
+                     ((size_t)2 * max_m + kSolveRedW) * sizeof(T), s, F, list, arena, w, u);
 }
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
@@ -868,12 +894,12 @@ void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
     launch_clustered(k_bwd1w<T>, grid, 1, smw, s, F, list, nf, ldt, arena, w);
     return;
   }
-  const size_t sm = ((size_t)max_m + kSolveRed) * sizeof(T);
   if (cfg == SOLVE_CTA8)
-    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1, sm, s, F, list, arena, w);
+    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 8>, nf, 1,
+                     ((size_t)max_m + kSolveRed) * sizeof(T), s, F, list, arena, w);
   else
-    launch_clustered(k_bwd1<T, kThreads, kSolveCh, 8, 16>, nf, solve_cfg_size(cfg), sm, s, F, list,
-                     arena, w);
+    launch_clustered(k_bwd1<T, kThreads, kSolveChW, 8, kSolveB>, nf, solve_cfg_size(cfg),
+                     ((size_t)max_m + kSolveRedW) * sizeof(T), s, F, list, arena, w);
 }
 
 // Persistent sweeps: enough warps for every front, at most eight CTAs of
