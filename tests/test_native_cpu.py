@@ -94,3 +94,21 @@ def test_analyze_rejects_bad_options_before_any_device_work():
     for kw in bad:
         with pytest.raises(N.DDPSError, match="INVALID_ARG"):
             N.ddps_analyze(P.rowptr, P.colind, P.block_ptr, options=N.default_options(**kw))
+
+
+@pytest.mark.parametrize("make,drop", CASES[:3])
+def test_symbolic_ilu_keeps_the_block_order(make, drop):
+    """With ILU(0) block factors the blocks keep their own row order (the
+    factor is defined on it); c and the G^ layout are those of the oracle."""
+    P = make()
+    o = _opts(drop)
+    o.factor_kind = N.DDPS_FACTOR_ILU0
+    o.factor_prec = o.spike_prec = N.DDPS_FP64
+    sizes, perm, c = N.ddps_symbolic(P.rowptr, P.colind, P.block_ptr, values=P.values, options=o)
+    assert np.array_equal(perm, np.arange(P.n))
+    orc = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, drop=drop, spikes=False)
+    assert np.array_equal(c, orc.c)
+    assert sizes["nfronts"] == 0
+    # a solve streams the stored entries of the diagonal blocks
+    nnz_d = sum(Dii.nnz for Dii in orc.D_blocks)
+    assert sizes["factor_lu_entries"] == nnz_d
