@@ -210,6 +210,8 @@ struct ddps_handle {
   // launch shape of every block-solve depth and sweep (SOLVE_AUTO until tuned)
   std::vector<int> tune_fwd, tune_bwd;
   std::vector<float> tune_fwd_ms, tune_bwd_ms;
+  int tune_spmv = SPMV_STREAM, tune_rt = SPMV_STREAM;  // CSR product kernels for A and R~
+  float tune_spmv_ms = 0.f, tune_rt_ms = 0.f;
   bool tuned = false;
   // persistent sweeps of the block solve over the levels >= persist_L (fronts of at
   // most kPersistM rows): orders, waits and flags (2 nfronts done flags, 2 counters)
@@ -836,6 +838,49 @@ void autotune_block_solve(ddps_handle* h, cudaStream_t s) {
       (sweep ? h->tune_bwd_ms : h->tune_fwd_ms)[L] = best_ms;
     }
   }
+  // CSR product kernels for A (outer iteration) and R~ (retrieval), timed on
+  // the handle's matrices with scratch vectors of the outer workspace
+  for (int which = 0; which < 2; ++which) {
+    const int64_t nn = A.n;
+    const std::string key = std::string(prop.name) + "|csr|" + (which ? "rt" : "a") + "|" +
+                            std::to_string(nn) + "|" +
+                            std::to_string(which ? (int64_t)h->nrt : A.nnz);
+    int best = SPMV_STREAM;
+    float best_ms = 0.f;
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+    } else if (!which || h->nrt > 0) {
+      CK(cudaMemsetAsync(h->o_tmp, 0, nn * sizeof(double), s));
+      CK(cudaMemsetAsync(h->pc_zhat, 0, std::max<int64_t>((int64_t)A.c.size(), 1) * sizeof(double), s));
+      for (int v = SPMV_STREAM; v <= SPMV_VEC8; ++v) {
+        auto run = [&]() {
+          if (which == 0)
+            launch_spmv(h->rowptr, h->colind, h->vals, nn, h->o_tmp, h->o_xt, s, v);
+          else
+            launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, nn, h->o_tmp, h->pc_zhat,
+                               h->o_xt, s, v);
+        };
+        run();
+        CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) run();
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 3.f;
+        if (v == SPMV_STREAM || ms < best_ms) {
+          best = v;
+          best_ms = ms;
+        }
+      }
+      check_launch();
+      g_tune_cache[key] = best;
+      added = true;
+    }
+    (which ? h->tune_rt : h->tune_spmv) = best;
+    (which ? h->tune_rt_ms : h->tune_spmv_ms) = best_ms;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (added || (std::getenv("DDPS_TUNE_CACHE") && !std::ifstream(std::getenv("DDPS_TUNE_CACHE"))))
@@ -1098,7 +1143,7 @@ void precond_apply(ddps_handle* h, const double* y, double* z, cudaStream_t s, b
     CK(cudaMemcpyAsync(h->first_ghat, h->pc_ghat, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   // 6.4-6.5: z = g - G(:,c) z^ = D~^-1 (y - R~ z^)
-  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s);
+  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s, h->tune_rt);
   h->launches++;
   block_solve(h, h->pc_t, z, s);
   h->stat_precond++;
@@ -1114,7 +1159,7 @@ void precond_direct_launches(ddps_handle* h, const double* y, double* z, cudaStr
     h->launches += direct_solve(h->direct, h->pc_ghat, h->pc_zhat, s);
   }
   // 6.4-6.5: z = D~^-1 (y - R~ z^)
-  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s);
+  launch_rt_residual(h->rt_rowptr, h->rt_col, h->rt_val, h->A.n, y, h->pc_zhat, h->pc_t, s, h->tune_rt);
   h->launches++;
   block_solve(h, h->pc_t, z, s);
 }
@@ -1132,7 +1177,7 @@ ddps_status solve_impl(ddps_handle* h, const double* f, double* x, const double*
   KScal* sc = h->sc_out;
   auto spmv = [&](const double* in, double* out) {
     Prof pr(h, DDPS_PROF_SPMV, s);
-    launch_spmv(h->rowptr, h->colind, h->vals, n, in, out, s);
+    launch_spmv(h->rowptr, h->colind, h->vals, n, in, out, s, h->tune_spmv);
     h->launches++;
   };
   h->stat_inner = 0;
@@ -2006,7 +2051,7 @@ static ddps_status factor_values(ddps_handle* h, const double* values, bool host
       else
         factor_impl<float, __nv_bfloat16>(h, s);
     }
-    if (h->opt.autotune && !h->tuned && !h->A.ilu) {
+    if (h->opt.autotune && !h->tuned) {
       if (fp == DDPS_FP64)
         autotune_block_solve<double>(h, s);
       else
@@ -2226,7 +2271,7 @@ ddps_status ddps_spmv(ddps_handle* h, const double* x, double* y, void* stream) 
   if (!h || !x || !y) return DDPS_ERR_INVALID_ARG;
   if (!h->factored) return DDPS_ERR_STATE;
   try {
-    launch_spmv(h->rowptr, h->colind, h->vals, h->A.n, x, y, as_stream(stream));
+    launch_spmv(h->rowptr, h->colind, h->vals, h->A.n, x, y, as_stream(stream), h->tune_spmv);
     h->launches++;
     check_launch();
   } catch (const Fail& e) {
@@ -2263,8 +2308,10 @@ ddps_status ddps_get_tuning(const ddps_handle* h, char* buf, int64_t cap, int64_
   if (!h) return DDPS_ERR_INVALID_ARG;
   static const char* names[] = {"warp", "cta8", "cl1", "cl2", "cl4", "cl8"};
   std::ostringstream o;
+  static const char* csr[] = {"stream", "vec4", "vec8"};
   o << "{\"tuned\": " << (h->tuned ? "true" : "false") << ", \"persistent_from_level\": "
-    << h->persist_L << ", \"levels\": [";
+    << h->persist_L << ", \"spmv\": \"" << csr[h->tune_spmv] << "\", \"spmv_ms\": "
+    << h->tune_spmv_ms << ", \"rt_residual\": \"" << csr[h->tune_rt] << "\", \"levels\": [";
   for (size_t L = 0; L < h->tune_fwd.size(); ++L) {
     const int f = h->tune_fwd[L], b = h->tune_bwd[L];
     o << (L ? ", " : "") << "{\"level\": " << L

@@ -231,12 +231,15 @@ void launch_fwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, co
 template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, cudaStream_t s, int cfg = SOLVE_AUTO);
+// CSR product kernels (the autotuner picks per matrix): row blocks streamed
+// through shared memory, or 4 / 8 lanes per row.
+enum { SPMV_STREAM = 0, SPMV_VEC4 = 1, SPMV_VEC8 = 2 };
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
-                 const double* x, double* y, cudaStream_t s);
+                 const double* x, double* y, cudaStream_t s, int variant = SPMV_STREAM);
 // y_out = y - R~ zhat (R~ rows over original indices, reduced columns)
 void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
                         int64_t n, const double* y, const double* zhat, double* out,
-                        cudaStream_t s);
+                        cudaStream_t s, int variant = SPMV_STREAM);
 // Implicit G^ product: q = R~ v (reduced columns), then w = v + g(c) with
 // g = D~^-1 q from the block solve.
 template <typename TI>

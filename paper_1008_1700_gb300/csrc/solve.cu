@@ -545,6 +545,39 @@ __global__ void __launch_bounds__(kStreamRows)
   }
 }
 
+// The same product with LPR lanes per row (CSR-vector): the lanes of a row
+// take its entries LPR apart, each with all of its (up to 4) loads in flight
+// before the gathers of x, and the row sum is a shuffle reduction in
+// registers (no shared memory).  A warp covers 32 / LPR consecutive rows.
+template <int SUB, int LPR>
+__global__ void __launch_bounds__(256)
+    k_csr_vec(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+              const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
+              const double* __restrict__ b, double* __restrict__ y) {
+  const int sub = threadIdx.x & (LPR - 1);
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR; row < n;
+       row += ((int64_t)gridDim.x * blockDim.x) / LPR) {
+    const int32_t ra = rowptr[row], rb = rowptr[row + 1];
+    double s = 0.0;
+    for (int32_t e = ra + sub; e < rb; e += 4 * LPR) {
+      int32_t c[4];
+      double v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t eq = e + q * LPR;
+        c[q] = eq < rb ? colind[eq] : 0;
+        v[q] = eq < rb ? vals[eq] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (e + q * LPR < rb) s += v[q] * x[c[q]];
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (sub == 0) y[row] = SUB ? b[row] - s : s;
+  }
+}
+
 // q = R~ v for a reduced vector v (the implicit G^ product)
 template <typename TI>
 __global__ void k_rt_apply(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -929,19 +962,31 @@ void launch_bwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32
                                               next, err);
 }
 
-void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
-                 const double* x, double* y, cudaStream_t s) {
+// CSR products: `variant` SPMV_STREAM (row blocks through shared memory) or
+// SPMV_VEC4 / SPMV_VEC8 (4 or 8 lanes per row); chosen by the autotuner.
+template <int SUB>
+static void launch_csr(int variant, const int32_t* rowptr, const int32_t* colind,
+                       const double* vals, int64_t n, const double* x, const double* b, double* y,
+                       cudaStream_t s) {
   if (n <= 0) return;
-  k_csr_stream<0><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(rowptr, colind, vals,
-                                                                             n, x, nullptr, y);
+  if (variant == SPMV_VEC4)
+    k_csr_vec<SUB, 4><<<grid_for(n * 4, 256, 1 << 30), 256, 0, s>>>(rowptr, colind, vals, n, x, b, y);
+  else if (variant == SPMV_VEC8)
+    k_csr_vec<SUB, 8><<<grid_for(n * 8, 256, 1 << 30), 256, 0, s>>>(rowptr, colind, vals, n, x, b, y);
+  else
+    k_csr_stream<SUB><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(rowptr, colind,
+                                                                                 vals, n, x, b, y);
+}
+
+void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
+                 const double* x, double* y, cudaStream_t s, int variant) {
+  launch_csr<0>(variant, rowptr, colind, vals, n, x, nullptr, y, s);
 }
 
 void launch_rt_residual(const int32_t* rt_rowptr, const int32_t* rt_col, const double* rt_val,
                         int64_t n, const double* y, const double* zhat, double* out,
-                        cudaStream_t s) {
-  if (n <= 0) return;
-  k_csr_stream<1><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(
-      rt_rowptr, rt_col, rt_val, n, zhat, y, out);
+                        cudaStream_t s, int variant) {
+  launch_csr<1>(variant, rt_rowptr, rt_col, rt_val, n, zhat, y, out, s);
 }
 
 template <typename TI>
