@@ -36,10 +36,10 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Grouped FP32 GEMM: C = alpha A B + beta C, row-major, one launch over the
-// tiles of many problems.  128 x 128 tiles, K in steps of 8 through a double
+// tiles of many problems.  128 x 128 tiles, K in steps of 16 through a double
 // buffer in shared memory, 256 threads each holding an 8 x 8 block of C.
 // ---------------------------------------------------------------------------
-constexpr int GB_M = 128, GB_N = 128, GB_K = 8, GB_T = 256, GB_PAD = 4;
+constexpr int GB_M = 128, GB_N = 128, GB_K = 16, GB_T = 256, GB_PAD = 4;
 
 __device__ __forceinline__ int find_problem(const int32_t* __restrict__ prefix, int n, int t) {
   int lo = 0, hi = n;  // prefix[lo] <= t < prefix[hi]
@@ -50,7 +50,7 @@ __device__ __forceinline__ int find_problem(const int32_t* __restrict__ prefix, 
   return lo;
 }
 
-__global__ void __launch_bounds__(GB_T)
+__global__ void __launch_bounds__(GB_T, 2)
     k_gemm_grouped(const GemmDesc* __restrict__ D, const int32_t* __restrict__ prefix, int32_t np) {
   __shared__ __align__(16) float As[2][GB_K][GB_M + GB_PAD];
   __shared__ __align__(16) float Bs[2][GB_K][GB_N + GB_PAD];
@@ -60,28 +60,35 @@ __global__ void __launch_bounds__(GB_T)
   const int tiles_n = (d.N + GB_N - 1) / GB_N;
   const int m0 = (t / tiles_n) * GB_M, n0 = (t % tiles_n) * GB_N;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  // loaders: A 128 x 8 (thread: row tid/2, four k from (tid&1)*4), B 8 x 128 (row tid/32, four columns)
-  const int ar = tid >> 1, ak = (tid & 1) * 4;
+  // loaders: A 128 x 16 (thread: row tid/2, eight k from (tid&1)*8), B 16 x 128 (rows tid/32 and
+  // tid/32 + 8, four columns each)
+  const int ar = tid >> 1, ak = (tid & 1) * 8;
   const int bk = tid >> 5, bc = (tid & 31) * 4;
-  float ra[4], rb[4];
+  float ra[8], rb[8];
   auto gload = [&](int k0) {
     const int gr = m0 + ar;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int gk = k0 + ak + q;
       ra[q] = (gr < d.M && gk < d.K) ? d.A[(int64_t)gr * d.lda + gk] : 0.f;
     }
-    const int gk = k0 + bk;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gc = n0 + bc + q;
-      rb[q] = (gk < d.K && gc < d.N) ? d.B[(int64_t)gk * d.ldb + gc] : 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const int gk = k0 + bk + 8 * h;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gc = n0 + bc + q;
+        rb[4 * h + q] = (gk < d.K && gc < d.N) ? d.B[(int64_t)gk * d.ldb + gc] : 0.f;
+      }
     }
   };
   auto sstore = [&](int st) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) As[st][ak + q][ar] = ra[q];
-    *reinterpret_cast<float4*>(&Bs[st][bk][bc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    for (int q = 0; q < 8; ++q) As[st][ak + q][ar] = ra[q];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<float4*>(&Bs[st][bk + 8 * h][bc]) =
+          make_float4(rb[4 * h], rb[4 * h + 1], rb[4 * h + 2], rb[4 * h + 3]);
   };
   float acc[8][8];
 #pragma unroll
