@@ -1025,16 +1025,12 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
     ghat_matvec<TG, TI>(h, p, v, st, sc);
     seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
                         POST_ALPHA, sc, tol, it, st);
-    update_s<TI>(S, sc, r, v, sv, st);
-    seg_reduce_post<TI>(S, 1, red(sv, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
-                        POST_CHECK_HALF, sc, tol, it, st);
+    update_s_norm<TI>(S, sc, r, v, sv, h->partial, tol, it, st);
     ghat_matvec<TG, TI>(h, sv, t, st, sc);
     seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
                         h->partial, POST_OMEGA, sc, tol, it, st);
-    update_xr_final<TI>(S, sc, z, p, sv, r, t, st);
-    seg_reduce_post<TI>(S, 1, red(r, nullptr, 1, &sc[0].nrm), nored(), nored(), h->partial,
-                        POST_CHECK_FULL, sc, tol, it, st);
-    h->launches += 15;
+    update_xr_norm<TI>(S, sc, z, p, sv, r, t, h->partial, tol, it, st);
+    h->launches += 6;  // the two G^ products count their own launches
   };
   if (graphs_on(h) && h->opt.maxit_in > 0) {
     // kCheckEvery iterations and the "some system still iterating" flag, one

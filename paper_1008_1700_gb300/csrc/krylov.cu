@@ -87,33 +87,15 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
   }
 }
 
-// One CTA per chunk: up to three reductions in one pass.
-//   op 0: sum x*y   op 1: sum x*x   op 2: max |x|
-// The last CTA of a segment to finish (counted in S.done) forms the
-// segment's results and its scalar step, then re-arms the counter.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    k_seg_reduce(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
-                 double* __restrict__ partial, int post, KScal* sc, double tol, int it) {
-  const int ch = blockIdx.x;
-  const int64_t b = S.chunk_beg[ch], e = S.chunk_end[ch];
-  RedSpec spec[3] = {r0, r1, r2};
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q >= nred) break;
-      const T* x = (const T*)spec[q].x;
-      const T* y = (const T*)spec[q].y;
-      const double xv = (double)x[i];
-      if (spec[q].op == 0)
-        acc[q] += xv * (double)y[i];
-      else if (spec[q].op == 1)
-        acc[q] += xv * xv;
-      else
-        acc[q] = fmax(acc[q], fabs(xv));
-    }
-  }
+// The end of a chunk reduction, shared by the reduction kernel and the
+// fused update-and-norm kernels: the CTA's per-thread values acc[q] are
+// summed in a fixed tree into the chunk's partial; the last CTA of a segment
+// to finish (counted in S.done) forms the segment's results and its scalar
+// step, then re-arms the counter.
+__device__ __forceinline__ void chunk_reduce_finalize(const SegView& S, int ch, int nred,
+                                                      const RedSpec* spec, double* acc,
+                                                      double* __restrict__ partial, int post,
+                                                      KScal* sc, double tol, int it) {
   __shared__ double red[3][kThreads / 32];
   __shared__ int last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -144,6 +126,88 @@ __global__ void __launch_bounds__(kThreads)
     seg_finalize(S, sgi, lane, nred, spec, partial, post, sc, tol, it);
     if (lane == 0) S.done[sgi] = 0;
   }
+}
+
+// One CTA per chunk: up to three reductions in one pass.
+//   op 0: sum x*y   op 1: sum x*x   op 2: max |x|
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_seg_reduce(SegView S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
+                 double* __restrict__ partial, int post, KScal* sc, double tol, int it) {
+  const int ch = blockIdx.x;
+  const int64_t b = S.chunk_beg[ch], e = S.chunk_end[ch];
+  RedSpec spec[3] = {r0, r1, r2};
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q >= nred) break;
+      const T* x = (const T*)spec[q].x;
+      const T* y = (const T*)spec[q].y;
+      const double xv = (double)x[i];
+      if (spec[q].op == 0)
+        acc[q] += xv * (double)y[i];
+      else if (spec[q].op == 1)
+        acc[q] += xv * xv;
+      else
+        acc[q] = fmax(acc[q], fabs(xv));
+    }
+  }
+  chunk_reduce_finalize(S, ch, nred, spec, acc, partial, post, sc, tol, it);
+}
+
+// s = r - alpha v and ||s||_2 with the half-step check (POST_CHECK_HALF), in
+// one pass: the same values and summation order as update_s followed by the
+// reduction.  Segments that are not iterating are skipped whole.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_update_s_norm(SegView S, KScal* sc, const T* __restrict__ r, const T* __restrict__ v,
+                    T* __restrict__ s_out, double* __restrict__ partial, double tol, int it) {
+  const int ch = blockIdx.x;
+  const int sg = S.chunk_seg[ch];
+  if (!sc[sg].active) return;
+  const double alpha = sc[sg].alpha;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = S.chunk_beg[ch] + threadIdx.x; i < S.chunk_end[ch]; i += blockDim.x) {
+    const T sv = (T)((double)r[i] - alpha * (double)v[i]);
+    s_out[i] = sv;
+    const double xv = (double)sv;
+    acc[0] += xv * xv;
+  }
+  const RedSpec spec[1] = {RedSpec{s_out, nullptr, 1, kScalStride, &sc[0].nrm}};
+  chunk_reduce_finalize(S, ch, 1, spec, acc, partial, POST_CHECK_HALF, sc, tol, it);
+}
+
+// The full step of update_xr_final and ||r||_2 with the full-step check
+// (POST_CHECK_FULL), in one pass.  Segments neither iterating nor stopped at
+// this half step are skipped whole (their check only clears half_done,
+// which is already clear).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_update_xr_norm(SegView S, KScal* sc, T* __restrict__ x, const T* __restrict__ p,
+                     const T* __restrict__ sv, T* __restrict__ r, const T* __restrict__ t,
+                     double* __restrict__ partial, double tol, int it) {
+  const int ch = blockIdx.x;
+  const int sg = S.chunk_seg[ch];
+  const bool act = sc[sg].active != 0, half = sc[sg].half_done != 0;
+  if (!act && !half) return;
+  const double alpha = sc[sg].alpha, omega = sc[sg].omega;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = S.chunk_beg[ch] + threadIdx.x; i < S.chunk_end[ch]; i += blockDim.x) {
+    T ri;
+    if (act) {
+      x[i] = (T)((double)x[i] + alpha * (double)p[i] + omega * (double)sv[i]);
+      ri = (T)((double)sv[i] - omega * (double)t[i]);
+      r[i] = ri;
+    } else {
+      x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+      ri = r[i];
+    }
+    const double xv = (double)ri;
+    acc[0] += xv * xv;
+  }
+  const RedSpec spec[1] = {RedSpec{r, nullptr, 1, kScalStride, &sc[0].nrm}};
+  chunk_reduce_finalize(S, ch, 1, spec, acc, partial, POST_CHECK_FULL, sc, tol, it);
 }
 
 template <typename T>
@@ -307,6 +371,19 @@ void update_xr_final(const SegView& S, const KScal* sc, T* x, const T* p, const 
   if (S.nchunks) k_update_xr_final<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, x, p, sv, r, t);
 }
 
+template <typename T>
+void update_s_norm(const SegView& S, KScal* sc, const T* r, const T* v, T* out, double* partial,
+                   double tol, int it, cudaStream_t s) {
+  if (S.nchunks)
+    k_update_s_norm<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, r, v, out, partial, tol, it);
+}
+template <typename T>
+void update_xr_norm(const SegView& S, KScal* sc, T* x, const T* p, const T* sv, T* r, const T* t,
+                    double* partial, double tol, int it, cudaStream_t s) {
+  if (S.nchunks)
+    k_update_xr_norm<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, x, p, sv, r, t, partial, tol, it);
+}
+
 void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s) {
   k_any_active<<<1, 256, 0, s>>>(nseg, sc, flag);
 }
@@ -369,7 +446,11 @@ void sc_omega(int nseg, KScal* sc, cudaStream_t s) {
   template void seg_reduce_post<T>(const SegView&, int, RedSpec, RedSpec, RedSpec, double*, int, \
                                    KScal*, double, int, cudaStream_t);                           \
   template void update_xr_final<T>(const SegView&, const KScal*, T*, const T*, const T*, T*,     \
-                                   const T*, cudaStream_t);
+                                   const T*, cudaStream_t);                                      \
+  template void update_s_norm<T>(const SegView&, KScal*, const T*, const T*, T*, double*, double, \
+                                 int, cudaStream_t);                                             \
+  template void update_xr_norm<T>(const SegView&, KScal*, T*, const T*, const T*, T*, const T*,  \
+                                  double*, double, int, cudaStream_t);
 DDPS_INST_K(double)
 DDPS_INST_K(float)
 template void convert<float, double>(int64_t, const double*, float*, cudaStream_t);

@@ -88,6 +88,16 @@ void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec
 template <typename T>
 void update_xr_final(const SegView& S, const KScal* sc, T* x, const T* p, const T* sv, T* r,
                      const T* t, cudaStream_t s);
+// Fused forms of the inner loop: s = r - alpha v with ||s||_2 and the
+// half-step check, and the full step of update_xr_final with ||r||_2 and the
+// full-step check (each the values and summation order of the separate
+// update and reduction).
+template <typename T>
+void update_s_norm(const SegView& S, KScal* sc, const T* r, const T* v, T* out, double* partial,
+                   double tol, int it, cudaStream_t s);
+template <typename T>
+void update_xr_norm(const SegView& S, KScal* sc, T* x, const T* p, const T* sv, T* r, const T* t,
+                    double* partial, double tol, int it, cudaStream_t s);
 // *flag = 1 if some segment is still active, else 0.
 void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s);
 void sc_beta(int nseg, KScal* sc, int first, cudaStream_t s);
