@@ -753,7 +753,7 @@ def run_ours(args):
         S64.close()
 
     if extras and args.form == "mixed":
-        # the benchmark spec's named precision form: FP32 G^ instead of FP16 storage
+        # the precision form with FP32 storage of G^ (instead of FP16)
         line["fp32_ghat"] = measure_workload(args.workload, "mixed", 3, 1, stream,
                                              {"ghat_prec": N.DDPS_FP32})
         if args.workload in ("cd3d_64_slabs16", "cd3d_48_slabs8"):
