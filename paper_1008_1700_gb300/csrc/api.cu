@@ -427,8 +427,9 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
       const int32_t n = (int32_t)(ptr[cls + 1] - ptr[cls]);
       if (n <= 0) continue;
       launch_front_gemm_tc(bwd ? 1 : 0, cls, h->tc_passes, h->F, list + ptr[cls], n,
-                           bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X, Tb,
-                           h->derr, h->opt.debug_wait_timeout, s);
+                           bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X,
+                           h->A.n, Tb, (int64_t)h->A.idx.size(), h->derr,
+                           h->opt.debug_wait_timeout, s);
       h->launches++;
     }
   }

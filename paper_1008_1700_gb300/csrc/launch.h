@@ -194,8 +194,9 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
                       unsigned char* wpk, cudaStream_t s);
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
-                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X, float* Tb,
-                          long long* err, int inject_wait, cudaStream_t s);
+                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
+                          int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
+                          int inject_wait, cudaStream_t s);
 void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_front,
                           const int32_t* tile_m0, const int64_t* tile_aoff,
                           const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,

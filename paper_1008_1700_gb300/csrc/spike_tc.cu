@@ -18,6 +18,7 @@
 // accumulator (128 lanes x 128 fp32 columns of tensor memory) is read back
 // with tcgen05.ld for the epilogue.  Every wait is bounded; a wait that runs
 // out records error code 2 in the kernel's error record.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,6 +103,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// Tensor copies (TMA) of panel rows through a tensor map over a row-major
+// fp32 panel (NR columns): a tile of box rows x 128 columns at (x, y), and
+// four single rows y0..y3 (a map with one-row boxes) placed one after another.
+__device__ __forceinline__ void tma_tile_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y0, int32_t y1, int32_t y2, int32_t y3,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(mbar)
       : "memory");
 }
 
@@ -699,6 +721,26 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+// Four consecutive columns of a panel row, of which the first nv are valid
+// (16-byte aligned; nv >= 4: one vector access, nv <= 0: none).
+__device__ __forceinline__ float4 ld_cols4(const float* p, int nv) {
+  if (nv >= 4) return *reinterpret_cast<const float4*>(p);
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (nv > 0) r.x = p[0];
+  if (nv > 1) r.y = p[1];
+  if (nv > 2) r.z = p[2];
+  return r;
+}
+__device__ __forceinline__ void st_cols4(float* p, float4 v, int nv) {
+  if (nv >= 4) {
+    *reinterpret_cast<float4*>(p) = v;
+    return;
+  }
+  if (nv > 0) p[0] = v.x;
+  if (nv > 1) p[1] = v.y;
+  if (nv > 2) p[2] = v.z;
+}
+
 // One work item = (front, 128-column panel tile) of a fused front product.
 // The front's fields are kept between items: consecutive items of a CTA are
 // mostly the tiles of one front, so an item usually costs one cached load.
@@ -741,27 +783,31 @@ __device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_
 // takes a contiguous range of work items (front, 128-column tile); a tile is
 // nkt K-stages of 32 panel rows.  A stage lives in one slot of a ring of SR
 // 16 KB slots from the moment its rows are copied in until its MMAs complete:
-//   warps 16-19 (row producers, stage g by warp 16 + g % NPROD): one 1-D bulk
-//     copy per panel row (fp32, up to 512 bytes, gathered through the front's
-//     row list) into the stage's slot.  One warp streams copies at a bounded
-//     rate, so several issue side by side; every slot belongs to one warp;
+//   warps 16-19 (row producers, stage g by warp 16 + g % NPROD): the stage's
+//     32 panel rows (fp32, 128 columns) into its slot with tensor copies:
+//     forward, the rows are consecutive working rows of the front (one tile
+//     copy); backward, pivot rows and update rows gathered through the front's
+//     row list, four rows per copy.  Every slot belongs to one warp;
 //   warp 20 lane 0 (W producer): the stage's W block into a ring of SW slots;
-//   warps 0-7 (converters): read the slot's fp32 rows, then (after a barrier
-//     of the eight warps) overwrite the slot with the bf16 (high, remainder)
-//     K-major operand;
+//   warps 0-7 (converters, two groups of four on alternate stages): read the
+//     slot's fp32 rows, then (after a barrier of the group's warps) overwrite
+//     the slot with the bf16 (high, remainder) K-major operand;
 //   warps 21 .. 20 + NMMA, lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256
 //     output rows) into one of NACC tensor-memory accumulators, tile t by
 //     thread t % NMMA into accumulator t % NACC; the commits hand the slot and
 //     the W slot back to the producers and, after the tile's last stage, the
 //     accumulator to the epilogue;
 //   warps 8-15 (epilogue, two groups of four): tcgen05.ld of lane quarter
-//     (warp % 4); group q stores the 16-row groups q, q + 2, ...; one 128-byte
-//     row segment per store (forward: the update rows are read one group
-//     ahead and accumulated).
+//     (warp % 4); group q stores the 16-row groups q, q + 2, ...; a 16 x 32
+//     block is turned around in the warp's own shared buffer so that each
+//     lane stores four consecutive columns of a row (forward: the update rows
+//     are read one group ahead and accumulated).
 // Every wait is bounded: a wait that runs out records error code 2 at once
 // (so that the other waits of every CTA give up quickly), the role stops,
 // and before exiting each producer lets its own copies land.
 constexpr int FG_CONV = 256;   // converter threads (warps 0-7)
+constexpr int FG_CGROUPS = 2;  // converter groups (alternate stages)
+constexpr int FG_CGT = FG_CONV / FG_CGROUPS;
 constexpr int FG_EPI0 = 8;     // epilogue warps 8-15 (tensor-memory lane quarter = warp % 4)
 constexpr int FG_NEPI = 8;
 constexpr int FG_PROD0 = 16;   // producer warps 16-19
@@ -777,10 +823,11 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
                     const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
                     const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                     float* __restrict__ X, float* __restrict__ Tb, long long* __restrict__ err,
-                    int inject_wait) {
+                    int inject_wait, const __grid_constant__ CUtensorMap tm_src) {
   // every ring slot is always filled by the same producer warp, so that no
   // producer waits on a slot barrier more than one phase ahead of it
-  static_assert(SR % NPROD == 0 && NPROD <= FG_NPROD && NMMA <= FG_MAXMMA && NACC % NMMA == 0,
+  static_assert(SR % NPROD == 0 && SR % FG_CGROUPS == 0 && NPROD <= FG_NPROD &&
+                    NMMA <= FG_MAXMMA && NACC % NMMA == 0,
                 "ring ownership");
   extern __shared__ __align__(1024) unsigned char smem[];
   // op_full and w_full are split by MMA thread (the owner of the stage's
@@ -798,7 +845,6 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
   const int it0 = (int)blockIdx.x * per, it1 = min(nitems, it0 + per);
-  const float* __restrict__ src = DIR == DIR_BWD ? X : Tb;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -811,7 +857,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[i])));
       for (int a = 0; a < NMMA; ++a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&op_full[a][i])),
-                     "r"(FG_CONV));
+                     "r"(FG_CGT));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&slot_empty[i])));
     }
     for (int i = 0; i < SW; ++i) {
@@ -882,18 +928,33 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       const uint32_t gc = g;
       for (int i = 0; i < NPROD; ++i, ++g) advance();  // this warp's next stage
       if (pos.it < it1) row_next = row_of(pos.w, pos.kt);
-      // panel rows of stage gc into its slot (free once the MMAs of stage gc - SR completed)
+      // panel rows of stage gc into its slot (free once the MMAs of stage gc - SR
+      // completed).  Every copy fills whole 512-byte rows: rows past K and
+      // columns past the block's count are read too (or filled with zeros past
+      // the panel) and masked by the converters.
       const uint32_t sl = gc % SR;
       if (gc >= SR) wait(&slot_empty[sl], ((gc / SR) - 1) & 1);
       bail = __any_sync(0xffffffffu, bail);  // keep the warp together for __syncwarp
       if (bail) break;
-      const int nr = min(TC_BK, cur.w.K - cur.kt * TC_BK);
-      const uint32_t rb = (uint32_t)((cur.w.cv + 3) & ~3) * 4;
-      if (lane == 0) mbar_expect_tx(smem_u32(&raw_full[sl]), (uint32_t)nr * rb);
-      __syncwarp();
-      if (lane < nr)
-        bulk_g2s(sbase + sl * kSlot + (uint32_t)lane * (TC_BN * 4), src + row * NR + cur.w.n0, rb,
-                 smem_u32(&raw_full[sl]));
+      const uint32_t dst = sbase + sl * kSlot;
+      if (DIR == DIR_FWD) {
+        if (lane == 0) {
+          mbar_expect_tx(smem_u32(&raw_full[sl]), kSlot);
+          tma_tile_2d(dst, &tm_src, (int32_t)cur.w.n0, (int32_t)(cur.w.tb0 + cur.kt * TC_BK),
+                      smem_u32(&raw_full[sl]));
+        }
+      } else {
+        const int32_t r = (int32_t)row;
+        const int32_t y0 = __shfl_sync(0xffffffffu, r, (4 * lane) & 31);
+        const int32_t y1 = __shfl_sync(0xffffffffu, r, (4 * lane + 1) & 31);
+        const int32_t y2 = __shfl_sync(0xffffffffu, r, (4 * lane + 2) & 31);
+        const int32_t y3 = __shfl_sync(0xffffffffu, r, (4 * lane + 3) & 31);
+        if (lane == 0) mbar_expect_tx(smem_u32(&raw_full[sl]), kSlot);
+        __syncwarp();
+        if (lane < TC_BK / 4)
+          tma_gather4(dst + (uint32_t)lane * (4 * TC_BN * 4), &tm_src, (int32_t)cur.w.n0, y0, y1,
+                      y2, y3, smem_u32(&raw_full[sl]));
+      }
       issued = gc + 1;
     }
   } else if (warp == FG_WPROD) {
@@ -926,23 +987,26 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     }
   } else if (warp < FG_CONV / 32) {
     // ---------------- converters ----------------
-    const int ct = tid;
+    // two groups of four warps take alternate stages (slot sl always goes to
+    // group sl % 2, SR being even), so that two stages are converted at once
+    const int cg = warp / (FG_CGT / 32), ct = tid - cg * FG_CGT;
     uint32_t g = 0, tc = 0;
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
       if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
       const uint32_t own = tc++ % NMMA;
       for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+        if ((int)(g % FG_CGROUPS) != cg) continue;
         const uint32_t sl = g % SR;
         wait(&raw_full[sl], (g / SR) & 1);
         unsigned char* slot = smem + sl * kSlot;
         const float* raw = reinterpret_cast<const float*>(slot);
         const int nr = min(TC_BK, w.K - kt * TC_BK);
-        constexpr int kQ = (TC_BN * TC_BK / 8) / FG_CONV;
+        constexpr int kQ = (TC_BN * TC_BK / 8) / FG_CGT;
         float v[kQ][8];
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-          const int e = ct + q * FG_CONV;
+          const int e = ct + q * FG_CGT;
           const int col = e % TC_BN, kc = e / TC_BN;
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
@@ -950,20 +1014,20 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
             v[q][u] = (!bail && r < nr && col < w.cv) ? raw[r * TC_BN + col] : 0.f;
           }
         }
-        // the converter warps have read the slot before any overwrites it; the
+        // the group's warps have read the slot before any overwrites it; the
         // barrier also makes a timeout in any of them a decision of all
         uint32_t any_bail;
         asm volatile(
             "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
-            "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            "bar.red.or.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(any_bail)
-            : "r"((uint32_t)bail), "r"(FG_CONV)
+            : "r"((uint32_t)bail), "r"(1 + cg), "r"(FG_CGT)
             : "memory");
         bail = any_bail != 0;
         if (bail) break;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-          const int e = ct + q * FG_CONV;
+          const int e = ct + q * FG_CGT;
           const uint32_t off = chunk_off(e % TC_BN, e / TC_BN);
           store_split_x2(slot + off, slot + TC_TILE_BYTES + off, v[q], PASSES == 3);
         }
@@ -1036,22 +1100,26 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   } else if (warp >= FG_EPI0 && warp < FG_EPI0 + FG_NEPI) {
     // ---------------- epilogue ----------------
     const int quarter = warp & 3, grp = (warp - FG_EPI0) >> 2;
+    // this warp's 16 x 32 buffer (after the rings): lane l holds column l of
+    // 16 rows after tcgen05.ld, and stores columns 4 (l % 8) .. + 3 of rows
+    // 4 r + l / 8 (r = 0..3) after the turn
+    float* tbuf = reinterpret_cast<float*>(smem + SR * kSlot + SW * kWs) + (warp - FG_EPI0) * 512;
+    const int rsub = lane >> 3, c4 = 4 * (lane & 7);
     uint32_t tc = 0;
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
       if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
       const uint32_t a = tc % NACC;
-      const int64_t gj = w.n0 + quarter * 32 + lane;
-      const bool col_ok = quarter * 32 + lane < w.cv;
-      // forward: old values of the update rows of this warp's first row group, read early
-      float old[16];
+      const int64_t gj = w.n0 + quarter * 32 + c4;  // this lane's first column
+      const int nv = w.cv - (quarter * 32 + c4);    // how many of its four columns are valid
+      // forward: old values of the update rows of this lane's rows of the warp's first row group, read early
+      float4 old[4];
       auto load_old = [&](int c16) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int i = c16 + u;
-          old[u] = (DIR == DIR_FWD && col_ok && i >= w.k && i < w.nout)
-                       ? Tb[(w.tb0 + i) * NR + gj]
-                       : 0.f;
+        for (int r4 = 0; r4 < 4; ++r4) {
+          const int i = c16 + 4 * r4 + rsub;
+          old[r4] = (DIR == DIR_FWD && i >= w.k && i < w.nout) ? ld_cols4(Tb + (w.tb0 + i) * NR + gj, nv)
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       };
       if (DIR == DIR_FWD) load_old(grp * 16);
@@ -1070,27 +1138,30 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
               "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
             : "r"(acc + (uint32_t)c16));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 16; ++u) tbuf[u * 32 + lane] = __uint_as_float(rv[u]);
+        __syncwarp();
+        float4 v[4];
+#pragma unroll
+        for (int r4 = 0; r4 < 4; ++r4)
+          v[r4] = *reinterpret_cast<const float4*>(tbuf + (4 * r4 + rsub) * 32 + c4);
+        __syncwarp();  // read before the next group overwrites the buffer
+        float4 cur[4];
         if (DIR == DIR_FWD) {
-          float cur[16];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) cur[u] = old[u];
+          for (int r4 = 0; r4 < 4; ++r4) cur[r4] = old[r4];
           if (c16 + 32 < w.nout) load_old(c16 + 32);  // next group's old values
-          if (col_ok) {
+        }
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const int i = c16 + u;
-              const float val = __uint_as_float(rv[u]);
-              if (i < w.k)
-                X[(w.row0 + i) * NR + gj] = val;
-              else if (i < w.nout)
-                Tb[(w.tb0 + i) * NR + gj] = cur[u] + val;
-            }
-          }
-        } else if (col_ok) {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int i = c16 + u;
-            if (i < w.nout) X[(w.row0 + i) * NR + gj] = __uint_as_float(rv[u]);
+        for (int r4 = 0; r4 < 4; ++r4) {
+          const int i = c16 + 4 * r4 + rsub;
+          if (i >= w.nout || nv <= 0) continue;
+          if (DIR == DIR_FWD && i >= w.k) {
+            const float4 t = make_float4(cur[r4].x + v[r4].x, cur[r4].y + v[r4].y,
+                                         cur[r4].z + v[r4].z, cur[r4].w + v[r4].w);
+            st_cols4(Tb + (w.tb0 + i) * NR + gj, t, nv);
+          } else {
+            st_cols4(X + (w.row0 + i) * NR + gj, v[r4], nv);
           }
         }
       }
@@ -1115,54 +1186,97 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
 }
 
 // Ring depths per tensor-memory width (shared memory: SR x 16 KB stage slots,
-// SW x W blocks; one CTA per SM).
+// SW x W blocks and the epilogue warps' 2 KB buffers; one CTA per SM).
 template <int NT>
 struct FrontCfg {
   static constexpr int SR = NT <= 128 ? 8 : 4;
-  static constexpr int SW = NT <= 128 ? 6 : NT <= 256 ? 4 : 2;
+  static constexpr int SW = NT <= 64 ? 6 : NT <= 128 ? 5 : NT <= 256 ? 4 : 2;
   static constexpr int NACC = NT <= 128 ? 4 : NT <= 256 ? 2 : 1;  // accumulators
   static constexpr int NMMA = NACC >= 2 ? 2 : 1;                   // MMA-issuing threads
   static constexpr int NPROD = 4;  // row producer warps (divides SR)
 };
 
+// Tensor map over a row-major fp32 panel of `rows` rows and NR columns, in
+// boxes of 128 columns x box_rows rows (no swizzle; zeros past the panel).
+using TmapEncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                     const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeTiled tmap_encoder() {
+  static const TmapEncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TmapEncodeTiled f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f = (TmapEncodeTiled)p;
+    cudaGetLastError();
+    return f;
+  }();
+  return fn;
+}
+bool panel_map(CUtensorMap* map, const float* base, int64_t rows, int32_t NR, int box_rows) {
+  const TmapEncodeTiled enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)NR, (cuuint64_t)std::max<int64_t>(rows, 1)};
+  const cuuint64_t stride[1] = {(cuuint64_t)NR * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BN, (cuuint32_t)box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int DIR, int NT, int PASSES>
 void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                   const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
-                  float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
+                  float* X, int64_t x_rows, float* Tb, int64_t tb_rows, long long* err, int inject,
+                  cudaStream_t s) {
   using C = FrontCfg<NT>;
   auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NMMA, C::NPROD>;
   constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
-                        (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2;
+                        (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2 +
+                        (size_t)FG_NEPI * 16 * 32 * sizeof(float);
+  // forward: tiles of 32 working rows; backward: single rows for the gathers
+  CUtensorMap tm;
+  const bool ok = DIR == DIR_FWD ? panel_map(&tm, Tb, tb_rows, NR, TC_BK)
+                                 : panel_map(&tm, X, x_rows, NR, 1);
+  if (!ok) {
+    record_launch_error(cudaErrorInvalidValue);
+    return;
+  }
   const int nsm = device_sm_count();
   record_launch_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const int32_t nct = (NR + TC_BN - 1) / TC_BN;
   const int32_t nitems = nfr * nct;
   const int32_t grid = std::min(nitems, nsm);
   kern<<<grid, FG_THREADS, sm, s>>>(F, fronts, nitems, nct, woff, wpk, block_ncols, j0, NR, X, Tb,
-                                    err, inject);
+                                    err, inject, tm);
 }
 
 template <int DIR, int PASSES>
 void dispatch_front(int cls, DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                     const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
-                    float* X, float* Tb, long long* err, int inject, cudaStream_t s) {
+                    float* X, int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
+                    int inject, cudaStream_t s) {
+#define DDPS_FRONT(NT)                                                                           \
+  launch_front<DIR, NT, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb, \
+                                tb_rows, err, inject, s)
   switch (cls) {
     case 0:
-      launch_front<DIR, 64, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                    inject, s);
+      DDPS_FRONT(64);
       break;
     case 1:
-      launch_front<DIR, 128, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                     inject, s);
+      DDPS_FRONT(128);
       break;
     case 2:
-      launch_front<DIR, 256, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                     inject, s);
+      DDPS_FRONT(256);
       break;
     default:
-      launch_front<DIR, 512, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                     inject, s);
+      DDPS_FRONT(512);
   }
+#undef DDPS_FRONT
 }
 
 template <int OP, int PASSES>
@@ -1262,24 +1376,25 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
 
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
-                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X, float* Tb,
-                          long long* err, int inject_wait, cudaStream_t s) {
+                          const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
+                          int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
+                          int inject_wait, cudaStream_t s) {
   if (nfr <= 0) return;
+#define DDPS_DISP(D, P)                                                                           \
+  dispatch_front<D, P>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb, tb_rows, \
+                       err, inject_wait, s)
   if (bwd) {
     if (passes == 3)
-      dispatch_front<DIR_BWD, 3>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                 inject_wait, s);
+      DDPS_DISP(DIR_BWD, 3);
     else
-      dispatch_front<DIR_BWD, 1>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                 inject_wait, s);
+      DDPS_DISP(DIR_BWD, 1);
   } else {
     if (passes == 3)
-      dispatch_front<DIR_FWD, 3>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                 inject_wait, s);
+      DDPS_DISP(DIR_FWD, 3);
     else
-      dispatch_front<DIR_FWD, 1>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, Tb, err,
-                                 inject_wait, s);
+      DDPS_DISP(DIR_FWD, 1);
   }
+#undef DDPS_DISP
 }
 
 int tc_tile_bk() { return TC_BK; }
