@@ -112,9 +112,13 @@ struct ddps_handle {
   int32_t mv_ntiles = 0;
   int64_t mv_max_cols = 0;
   void* ghat = nullptr;
-  // spike panels: X (n x NR) and the fronts' working rows (sum of m x NR)
+  // spike panels: X (n x NR) and the fronts' working rows (sum of m x NR);
+  // D (rows as U) receives the update rows of the fused forward products,
+  // fz_flag marks those fronts for the parent's gather
   void* X = nullptr;
   void* U = nullptr;
+  void* D = nullptr;
+  uint8_t* fz_flag = nullptr;
   int32_t NR = 0;
   int32_t max_k = 0;
   // LU launch order per depth (see LevelSplit)
@@ -428,7 +432,7 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
       if (n <= 0) continue;
       launch_front_gemm_tc(bwd ? 1 : 0, cls, h->tc_passes, h->F, list + ptr[cls], n,
                            bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X,
-                           h->A.n, Tb, (int64_t)h->A.idx.size(), h->derr,
+                           h->A.n, Tb, (int64_t)h->A.idx.size(), (float*)h->D, h->derr,
                            h->opt.debug_wait_timeout, s);
       h->launches++;
     }
@@ -608,7 +612,7 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
         const int64_t q = c * A.nlevels + L;
         const int32_t ng = (int32_t)(h->fw_g_ptr[q + 1] - h->fw_g_ptr[q]);
         launch_spike_gather<T>(h->F, h->fw_g + h->fw_g_ptr[q], ng, h->block_ncols, j0, NR, X, Tb,
-                               h->fw_active + c * nf, s);
+                               h->fw_active + c * nf, (const T*)h->D, h->fz_flag, s);
         h->launches += ng > 0;
         fused_fronts<T>(h, false, h->fz, h->fz_ptr.data() + 4 * q, j0, X, Tb, s);
         spike_op<T>(h, OP_FWD_LINV, h->fw_kf + h->fw_k_ptr[q], h->fw_km + h->fw_k_ptr[q],
@@ -1792,6 +1796,12 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
         }
       }
       h->wpk = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(wrun, 16));
+      if (!pf.empty()) {  // fused forward fronts: their update rows go to D
+        const size_t db = (size_t)std::max<int64_t>((int64_t)A.idx.size(), 1) * h->NR * sizeof(float);
+        h->D = dalloc_bytes(h, (int64_t)db);
+        CK(cudaMemset(h->D, 0, db));  // columns past a block's count stay zero
+        h->fz_flag = dupload(h, fzf);
+      }
       h->woff_b = dupload(h, wob);
       h->woff_f = dupload(h, wof);
       h->wpk_b = dupload(h, pb);

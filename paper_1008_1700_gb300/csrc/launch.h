@@ -158,9 +158,11 @@ template <typename T>
 int spike_tile_m();
 template <typename T>
 // active (per front, may be null): children with active[c] == 0 are skipped.
+// D (may be null): for children with dflag[c] != 0 the update rows of their
+// forward product are held apart in D (same row indexing as Tb) and added here.
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
-                         cudaStream_t s);
+                         const T* D, const uint8_t* dflag, cudaStream_t s);
 // spike_tc.cu: the same ops on the tensor cores (fp32 factors, bf16 operands,
 // fp32 accumulation); passes = 1 (hi*hi) or 3 (hi*hi + hi*lo + lo*hi).  A wait
 // that runs out writes error code 2 into err[0].
@@ -195,7 +197,7 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
                           const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
-                          int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
+                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
                           int inject_wait, cudaStream_t s);
 void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_front,
                           const int32_t* tile_m0, const int64_t* tile_aoff,

@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kThreads)
     k_spike_gather(DevFronts F, const int32_t* __restrict__ list,
                    const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                    const T* __restrict__ X, T* __restrict__ Tb,
-                   const uint8_t* __restrict__ active) {
+                   const uint8_t* __restrict__ active, const T* __restrict__ D,
+                   const uint8_t* __restrict__ dflag) {
   using V = typename GatherVec<T>::V;
   constexpr int VN = GatherVec<T>::n;
   const int32_t f = list[blockIdx.x];
@@ -87,8 +88,10 @@ __global__ void __launch_bounds__(kThreads)
     const int32_t kc = F.k[c], rc = F.m[c] - kc;
     const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
     const T* __restrict__ Tc = Tb + (F.idx_off[c] + kc) * NR;
+    // the child's own forward update (kept apart by the fused products)
+    const T* __restrict__ Dc = D && dflag[c] ? D + (F.idx_off[c] + kc) * NR : nullptr;
     for (int i0 = warp * 4; i0 < rc; i0 += 32) {
-      V src[4], d[4];
+      V src[4], d[4], e[4];
       int32_t row[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -97,11 +100,23 @@ __global__ void __launch_bounds__(kThreads)
         if (i < rc) {
           src[u] = *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col);
           d[u] = *reinterpret_cast<const V*>(Tf + (int64_t)row[u] * NR + col);
+          if (Dc) e[u] = *reinterpret_cast<const V*>(Dc + (int64_t)i * NR + col);
         }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (i0 + u >= rc) continue;
+        if (Dc) {  // the child's update rows: what its children passed up, plus its own update
+          if constexpr (VN == 4) {
+            src[u].x += e[u].x;
+            src[u].y += e[u].y;
+            src[u].z += e[u].z;
+            src[u].w += e[u].w;
+          } else {
+            src[u].x += e[u].x;
+            src[u].y += e[u].y;
+          }
+        }
         if constexpr (VN == 4) {
           d[u].x += src[u].x;
           d[u].y += src[u].y;
@@ -238,11 +253,12 @@ int spike_tile_m() {
 template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
-                         cudaStream_t s) {
+                         const T* D, const uint8_t* dflag, cudaStream_t s) {
   if (nf <= 0) return;
   const int per = 32 * GatherVec<T>::n;
   dim3 grid(nf, (NR + per - 1) / per);
-  k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb, active);
+  k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb, active, D,
+                                              dflag);
 }
 
 template <typename T>
@@ -274,7 +290,7 @@ void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int
   template int spike_tile_m<T>();                                                               \
   template void launch_spike_gather<T>(DevFronts, const int32_t*, int32_t, const int64_t*,     \
                                        int64_t, int32_t, const T*, T*, const uint8_t*,         \
-                                       cudaStream_t);                                          \
+                                       const T*, const uint8_t*, cudaStream_t);                \
   template void launch_spike_gemm<T>(int, DevFronts, const int32_t*, const int32_t*, int32_t,  \
                                      const T*, const int64_t*, int64_t, int32_t, T*, T*,       \
                                      cudaStream_t);

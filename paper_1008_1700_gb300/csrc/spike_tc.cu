@@ -575,7 +575,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 //   forward:  [X_piv; dT_upd] = W_f T_piv,        W_f = [L11^-1; -L21 L11^-1]   (m x k)
 //   backward: X_piv = W_b [X_piv; X_upd],         W_b = [U11^-1, -U11^-1 U12]    (k x m)
 // (X_upd: the solution on the front's update rows, gathered through its row
-// list; dT_upd is added to the front's update rows for the parent's gather).
+// list; dT_upd is stored apart, in D, and the parent's gather adds it to what
+// the front's own children passed up on those rows).
 // The MMA is transposed with respect to the tile ops above: its M = 128 are
 // panel columns and its N = the front's output rows rounded up to 16, so a
 // small front costs N, not 128, rows of work; the accumulator lives in
@@ -722,15 +723,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 
 // Four consecutive columns of a panel row, of which the first nv are valid
-// (16-byte aligned; nv >= 4: one vector access, nv <= 0: none).
-__device__ __forceinline__ float4 ld_cols4(const float* p, int nv) {
-  if (nv >= 4) return *reinterpret_cast<const float4*>(p);
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (nv > 0) r.x = p[0];
-  if (nv > 1) r.y = p[1];
-  if (nv > 2) r.z = p[2];
-  return r;
-}
+// (16-byte aligned; nv >= 4: one vector store, nv <= 0: none).
 __device__ __forceinline__ void st_cols4(float* p, float4 v, int nv) {
   if (nv >= 4) {
     *reinterpret_cast<float4*>(p) = v;
@@ -742,10 +735,29 @@ __device__ __forceinline__ void st_cols4(float* p, float4 v, int nv) {
 }
 
 // One work item = (front, 128-column panel tile) of a fused front product.
-// The front's fields are kept between items: consecutive items of a CTA are
-// mostly the tiles of one front, so an item usually costs one cached load.
+// The fields of the CTA's first kTab fronts are read once, at the start, into
+// a table in shared memory (FMeta); consecutive items are mostly the tiles of
+// one front, and each role keeps its current front's fields (FItem).
+constexpr int kTab = 32;
+struct FMeta {
+  int32_t f, k, nout, K, row0, tb0, ncols, pad;
+  int64_t wo;
+};
+struct FCtx {
+  DevFronts F;
+  const int32_t* fronts;
+  int32_t nct;
+  const int64_t* woff;
+  const unsigned char* wpk;
+  const int64_t* block_ncols;
+  int64_t j0;
+  int32_t NR;
+  const FMeta* tab;  // fronts p0 .. p0 + ntab - 1 of the list
+  int32_t p0, ntab;
+};
 struct FItem {
-  int32_t f = -1;
+  int32_t p = -1;  // position of the front in the launch's list
+  int32_t f;
   int32_t k, nout, K, nf, nkt, cv;
   int64_t ncols, n0, row0, tb0;
   const int32_t* idx;
@@ -753,27 +765,43 @@ struct FItem {
   uint32_t wpart, wblk;
 };
 
+template <int DIR>
+__device__ __forceinline__ void fmeta_load(const FCtx& c, int32_t f, FMeta& m) {
+  m.f = f;
+  m.k = c.F.k[f];
+  fused_dims<DIR>(m.k, c.F.m[f], m.nout, m.K);
+  m.row0 = (int32_t)c.F.row0[f];
+  m.tb0 = (int32_t)c.F.idx_off[f];
+  m.ncols = (int32_t)min((int64_t)c.NR, c.block_ncols[c.F.block[f]] - c.j0);
+  m.pad = 0;
+  m.wo = c.woff[f];
+}
+
 template <int DIR, int PASSES>
-__device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_t nct,
-                                      const int64_t* woff, const unsigned char* wpk,
-                                      const int64_t* block_ncols, int64_t j0, int32_t NR, int it,
-                                      FItem& w) {
-  const int32_t f = fronts[it / nct];
-  if (f != w.f) {
-    w.f = f;
-    w.ncols = min((int64_t)NR, block_ncols[F.block[f]] - j0);
-    w.k = F.k[f];
-    fused_dims<DIR>(w.k, F.m[f], w.nout, w.K);
+__device__ __forceinline__ bool fitem(const FCtx& c, int it, FItem& w) {
+  const int32_t p = it / c.nct;
+  if (p != w.p) {
+    w.p = p;
+    FMeta m;
+    if (p - c.p0 < c.ntab)
+      m = c.tab[p - c.p0];
+    else
+      fmeta_load<DIR>(c, c.fronts[p], m);
+    w.f = m.f;
+    w.k = m.k;
+    w.nout = m.nout;
+    w.K = m.K;
+    w.ncols = m.ncols;
     w.nf = (w.nout + 15) & ~15;
     w.nkt = (w.K + TC_BK - 1) / TC_BK;
-    w.row0 = F.row0[f];
-    w.tb0 = F.idx_off[f];
-    w.idx = F.idx + F.idx_off[f];
-    w.w = wpk + woff[f];
+    w.row0 = m.row0;
+    w.tb0 = m.tb0;
+    w.idx = c.F.idx + m.tb0;
+    w.w = c.wpk + m.wo;
     w.wpart = (uint32_t)w.nf * TC_BK * 2;
     w.wblk = (PASSES == 3 ? 2u : 1u) * w.wpart;
   }
-  w.n0 = (int64_t)(it % nct) * TC_BN;
+  w.n0 = (int64_t)(it % c.nct) * TC_BN;
   if (w.n0 >= w.ncols) return false;
   w.cv = (int)min((int64_t)TC_BN, w.ncols - w.n0);
   return true;
@@ -792,8 +820,9 @@ __device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_
 //   warps 0-7 (converters, two groups of four on alternate stages): read the
 //     slot's fp32 rows, then (after a barrier of the group's warps) overwrite
 //     the slot with the bf16 (high, remainder) K-major operand;
-//   warps 21 .. 20 + NMMA, lane 0 (MMA): 1 or 3 tcgen05.mma per 16 K (per 256
-//     output rows) into one of NACC tensor-memory accumulators, tile t by
+//   warps 21 .. 20 + NMMA, lane 0 (MMA): 1, 2 (three passes, at most 128
+//     output rows) or 3 tcgen05.mma per 16 K (per 256 output rows) into one of
+//     NACC tensor-memory accumulators, tile t by
 //     thread t % NMMA into accumulator t % NACC; the commits hand the slot and
 //     the W slot back to the producers and, after the tile's last stage, the
 //     accumulator to the epilogue;
@@ -801,7 +830,7 @@ __device__ __forceinline__ bool fitem(DevFronts F, const int32_t* fronts, int32_
 //     (warp % 4); group q stores the 16-row groups q, q + 2, ...; a 16 x 32
 //     block is turned around in the warp's own shared buffer so that each
 //     lane stores four consecutive columns of a row (forward: the update rows
-//     are read one group ahead and accumulated).
+//     go to D).
 // Every wait is bounded: a wait that runs out records error code 2 at once
 // (so that the other waits of every CTA give up quickly), the role stops,
 // and before exiting each producer lets its own copies land.
@@ -822,8 +851,9 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     k_front_gemm_tc(DevFronts F, const int32_t* __restrict__ fronts, int32_t nitems, int32_t nct,
                     const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
                     const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
-                    float* __restrict__ X, float* __restrict__ Tb, long long* __restrict__ err,
-                    int inject_wait, const __grid_constant__ CUtensorMap tm_src) {
+                    float* __restrict__ X, float* __restrict__ Tb, float* __restrict__ D,
+                    long long* __restrict__ err, int inject_wait,
+                    const __grid_constant__ CUtensorMap tm_src) {
   // every ring slot is always filled by the same producer warp, so that no
   // producer waits on a slot barrier more than one phase ahead of it
   static_assert(SR % NPROD == 0 && SR % FG_CGROUPS == 0 && NPROD <= FG_NPROD &&
@@ -837,19 +867,29 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   __shared__ __align__(8) uint64_t never;
   __shared__ uint32_t tmem_slot;
   __shared__ int skip_all;
+  __shared__ FMeta tab[kTab];
   constexpr uint32_t kSlot = TC_BK * TC_BN * 4;                       // 32 fp32 rows x 128
   constexpr uint32_t kWs = (PASSES == 3 ? 2u : 1u) * NT * TC_BK * 2;  // W block
+  // three passes with at most 128 output rows: hi*hi and hi*lo in one MMA over
+  // the stacked [W_hi; W_lo] (N = 2 nf; accumulator columns [0, nf) and
+  // [nf, 2 nf)), lo*hi into the first half; the epilogue adds the halves
+  constexpr bool CAT = PASSES == 3 && NT <= 128;
+  constexpr uint32_t ACW = CAT ? 2 * NT : NT;  // tensor-memory columns per accumulator
   const uint32_t sbase = smem_u32(smem);
   const uint32_t w0 = sbase + SR * kSlot;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
   const int it0 = (int)blockIdx.x * per, it1 = min(nitems, it0 + per);
+  const int32_t p0 = it0 / nct;
+  const int32_t ntab = it1 > it0 ? min(kTab, (it1 - 1) / nct - p0 + 1) : 0;
+  const FCtx ctx{F, fronts, nct, woff, wpk, block_ncols, j0, NR, tab, p0, ntab};
+  if (warp == 1 && lane < ntab) fmeta_load<DIR>(ctx, fronts[p0 + lane], tab[lane]);  // read before the barrier below
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"((uint32_t)(NT * NACC)));
+                 "r"(ACW * NACC));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -905,7 +945,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     Pos pos{it0, 0, {}};
     auto next_valid = [&](int from) {
       int it = from;
-      while (it < it1 && !fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, pos.w)) ++it;
+      while (it < it1 && !fitem<DIR, PASSES>(ctx, it, pos.w)) ++it;
       pos.it = it;
       pos.kt = 0;
     };
@@ -965,7 +1005,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       uint32_t g = 0, tc = 0;
       FItem w;
       for (int it = it0; it < it1 && !bail; ++it, ++tc) {
-        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) {
+        if (!fitem<DIR, PASSES>(ctx, it, w)) {
           --tc;
           continue;
         }
@@ -993,7 +1033,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     uint32_t g = 0, tc = 0;
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
-      if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      if (!fitem<DIR, PASSES>(ctx, it, w)) continue;
       const uint32_t own = tc++ % NMMA;
       for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
         if ((int)(g % FG_CGROUPS) != cg) continue;
@@ -1050,7 +1090,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       uint32_t opar = 0u, wpar_m = 0u;  // phase parity of this thread's barriers, bit per slot
       FItem w;
       for (int it = it0; it < it1 && !bail; ++it) {
-        if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+        if (!fitem<DIR, PASSES>(ctx, it, w)) continue;
         const uint32_t a = tc % NACC;
         if (tc % NMMA != mine) {  // another thread's tile: skip its stages
           g += w.nkt;
@@ -1058,8 +1098,9 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
           continue;
         }
         if (tc >= NACC) wait(&acc_empty[a], ((tc / NACC) - 1) & 1);
-        const uint32_t acc = tmem + a * NT;
+        const uint32_t acc = tmem + a * ACW;
         const uint32_t id0 = idesc_m128(min(256, w.nf));
+        const uint32_t idc = CAT ? idesc_m128(2 * w.nf) : 0u;
         const uint32_t id1 = w.nf > 256 ? idesc_m128(w.nf - 256) : 0u;
         const uint64_t lo_w = w.wpart >> 4;
         for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
@@ -1076,10 +1117,15 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
           for (int kk = 0; kk < TC_BK / 16; ++kk) {
             const uint64_t ko = kk * (256 >> 4);
             const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-            mma_bf16_n(acc, aHi + ko, bHi + ko, id0, acc0);
-            if (PASSES == 3) {
-              mma_bf16_n(acc, aHi + ko, bLo + ko, id0, 1u);
+            if (CAT) {
+              mma_bf16_n(acc, aHi + ko, bHi + ko, idc, acc0);  // [hi*hi | hi*lo]
               mma_bf16_n(acc, aLo + ko, bHi + ko, id0, 1u);
+            } else {
+              mma_bf16_n(acc, aHi + ko, bHi + ko, id0, acc0);
+              if (PASSES == 3) {
+                mma_bf16_n(acc, aHi + ko, bLo + ko, id0, 1u);
+                mma_bf16_n(acc, aLo + ko, bHi + ko, id0, 1u);
+              }
             }
             if (NT > 256 && id1) {  // output rows 256.. : B rows 256.. and accumulator columns 256..
               const uint64_t wo = (256 / 8) * kSBO >> 4;
@@ -1108,26 +1154,15 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     uint32_t tc = 0;
     FItem w;
     for (int it = it0; it < it1 && !bail; ++it) {
-      if (!fitem<DIR, PASSES>(F, fronts, nct, woff, wpk, block_ncols, j0, NR, it, w)) continue;
+      if (!fitem<DIR, PASSES>(ctx, it, w)) continue;
       const uint32_t a = tc % NACC;
       const int64_t gj = w.n0 + quarter * 32 + c4;  // this lane's first column
       const int nv = w.cv - (quarter * 32 + c4);    // how many of its four columns are valid
-      // forward: old values of the update rows of this lane's rows of the warp's first row group, read early
-      float4 old[4];
-      auto load_old = [&](int c16) {
-#pragma unroll
-        for (int r4 = 0; r4 < 4; ++r4) {
-          const int i = c16 + 4 * r4 + rsub;
-          old[r4] = (DIR == DIR_FWD && i >= w.k && i < w.nout) ? ld_cols4(Tb + (w.tb0 + i) * NR + gj, nv)
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      };
-      if (DIR == DIR_FWD) load_old(grp * 16);
       wait(&acc_full[a], (tc / NACC) & 1);
       bail = __any_sync(0xffffffffu, bail);  // tcgen05.ld is warp-collective
       if (bail) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t acc = tmem + a * NT + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t acc = tmem + a * ACW + ((uint32_t)(quarter * 32) << 16);
       for (int c16 = grp * 16; c16 < w.nout; c16 += 32) {
         uint32_t rv[16];
         asm volatile(
@@ -1137,32 +1172,34 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
               "=r"(rv[6]), "=r"(rv[7]), "=r"(rv[8]), "=r"(rv[9]), "=r"(rv[10]), "=r"(rv[11]),
               "=r"(rv[12]), "=r"(rv[13]), "=r"(rv[14]), "=r"(rv[15])
             : "r"(acc + (uint32_t)c16));
+        uint32_t rw[16];
+        if (CAT)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+              "%10, %11, %12, %13, %14, %15}, [%16];"
+              : "=r"(rw[0]), "=r"(rw[1]), "=r"(rw[2]), "=r"(rw[3]), "=r"(rw[4]), "=r"(rw[5]),
+                "=r"(rw[6]), "=r"(rw[7]), "=r"(rw[8]), "=r"(rw[9]), "=r"(rw[10]), "=r"(rw[11]),
+                "=r"(rw[12]), "=r"(rw[13]), "=r"(rw[14]), "=r"(rw[15])
+              : "r"(acc + (uint32_t)(w.nf + c16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int u = 0; u < 16; ++u) tbuf[u * 32 + lane] = __uint_as_float(rv[u]);
+        for (int u = 0; u < 16; ++u)
+          tbuf[u * 32 + lane] =
+              CAT ? __uint_as_float(rv[u]) + __uint_as_float(rw[u]) : __uint_as_float(rv[u]);
         __syncwarp();
         float4 v[4];
 #pragma unroll
         for (int r4 = 0; r4 < 4; ++r4)
           v[r4] = *reinterpret_cast<const float4*>(tbuf + (4 * r4 + rsub) * 32 + c4);
         __syncwarp();  // read before the next group overwrites the buffer
-        float4 cur[4];
-        if (DIR == DIR_FWD) {
-#pragma unroll
-          for (int r4 = 0; r4 < 4; ++r4) cur[r4] = old[r4];
-          if (c16 + 32 < w.nout) load_old(c16 + 32);  // next group's old values
-        }
 #pragma unroll
         for (int r4 = 0; r4 < 4; ++r4) {
           const int i = c16 + 4 * r4 + rsub;
           if (i >= w.nout || nv <= 0) continue;
-          if (DIR == DIR_FWD && i >= w.k) {
-            const float4 t = make_float4(cur[r4].x + v[r4].x, cur[r4].y + v[r4].y,
-                                         cur[r4].z + v[r4].z, cur[r4].w + v[r4].w);
-            st_cols4(Tb + (w.tb0 + i) * NR + gj, t, nv);
-          } else {
+          if (DIR == DIR_FWD && i >= w.k)
+            st_cols4(D + (w.tb0 + i) * NR + gj, v[r4], nv);
+          else
             st_cols4(X + (w.row0 + i) * NR + gj, v[r4], nv);
-          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1182,16 +1219,17 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)(NT * NACC)));
+                 "r"(ACW * NACC));
 }
 
 // Ring depths per tensor-memory width (shared memory: SR x 16 KB stage slots,
 // SW x W blocks and the epilogue warps' 2 KB buffers; one CTA per SM).
-template <int NT>
+template <int NT, int PASSES>
 struct FrontCfg {
   static constexpr int SR = NT <= 128 ? 8 : 4;
   static constexpr int SW = NT <= 64 ? 6 : NT <= 128 ? 5 : NT <= 256 ? 4 : 2;
-  static constexpr int NACC = NT <= 128 ? 4 : NT <= 256 ? 2 : 1;  // accumulators
+  // accumulators (512 tensor-memory columns; twice NT wide for three passes up to 128 rows)
+  static constexpr int NACC = NT <= 64 ? 4 : NT <= 128 ? (PASSES == 3 ? 2 : 4) : NT <= 256 ? 2 : 1;
   static constexpr int NMMA = NACC >= 2 ? 2 : 1;                   // MMA-issuing threads
   static constexpr int NPROD = 4;  // row producer warps (divides SR)
 };
@@ -1231,9 +1269,9 @@ bool panel_map(CUtensorMap* map, const float* base, int64_t rows, int32_t NR, in
 template <int DIR, int NT, int PASSES>
 void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                   const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
-                  float* X, int64_t x_rows, float* Tb, int64_t tb_rows, long long* err, int inject,
-                  cudaStream_t s) {
-  using C = FrontCfg<NT>;
+                  float* X, int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
+                  int inject, cudaStream_t s) {
+  using C = FrontCfg<NT, PASSES>;
   auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NMMA, C::NPROD>;
   constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
                         (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2 +
@@ -1252,17 +1290,17 @@ void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t
   const int32_t nitems = nfr * nct;
   const int32_t grid = std::min(nitems, nsm);
   kern<<<grid, FG_THREADS, sm, s>>>(F, fronts, nitems, nct, woff, wpk, block_ncols, j0, NR, X, Tb,
-                                    err, inject, tm);
+                                    D, err, inject, tm);
 }
 
 template <int DIR, int PASSES>
 void dispatch_front(int cls, DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                     const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
-                    float* X, int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
-                    int inject, cudaStream_t s) {
+                    float* X, int64_t x_rows, float* Tb, int64_t tb_rows, float* D,
+                    long long* err, int inject, cudaStream_t s) {
 #define DDPS_FRONT(NT)                                                                           \
   launch_front<DIR, NT, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb, \
-                                tb_rows, err, inject, s)
+                                tb_rows, D, err, inject, s)
   switch (cls) {
     case 0:
       DDPS_FRONT(64);
@@ -1377,12 +1415,12 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
                           const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
-                          int64_t x_rows, float* Tb, int64_t tb_rows, long long* err,
+                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
                           int inject_wait, cudaStream_t s) {
   if (nfr <= 0) return;
-#define DDPS_DISP(D, P)                                                                           \
-  dispatch_front<D, P>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb, tb_rows, \
-                       err, inject_wait, s)
+#define DDPS_DISP(DD, P)                                                                           \
+  dispatch_front<DD, P>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb,      \
+                        tb_rows, D, err, inject_wait, s)
   if (bwd) {
     if (passes == 3)
       DDPS_DISP(DIR_BWD, 3);
