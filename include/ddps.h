@@ -142,6 +142,12 @@ typedef struct {
                              clusters of 1-8 CTAs) on the handle's factors and keeps the fastest;
                              choices are cached per process and, when the environment variable
                              DDPS_TUNE_CACHE names a file, in that JSON file; 0: fixed rules */
+  int32_t csr_kernel;     /* kernel of the products with A and R~: -1 (default) the autotuner's
+                             choice (row blocks through shared memory when autotune is 0);
+                             0 row blocks, 1 / 2: 4 / 8 lanes per row, 3: row blocks with
+                             all of a block's loads issued at once, 4: 32-row groups per warp
+                             copied asynchronously into shared memory; other values are
+                             rejected */
 } ddps_options;
 
 typedef struct {

@@ -159,6 +159,11 @@ struct ddps_handle {
   // and their tiles (index (c * nlevels + L) into the *_ptr vectors).
   std::vector<int32_t> gperm;  // panel column -> coupling column (G^ column order), per block
   uint8_t* fw_active = nullptr;
+  // per (chunk, front): a fused forward front none of whose children is
+  // active in the chunk; its working rows are its pivot rows of X, read
+  // there by the fused product (no gather), and its parent's gather takes
+  // only its own update rows (D)
+  uint8_t* fw_pleaf = nullptr;
   int32_t *fw_g = nullptr, *fw_kf = nullptr, *fw_km = nullptr, *fw_rf = nullptr, *fw_rm = nullptr;
   int64_t *fw_ka = nullptr, *fw_ra = nullptr;  // packed-A offsets (tensor-core path)
   std::vector<int64_t> fw_g_ptr, fw_k_ptr, fw_r_ptr;
@@ -424,7 +429,7 @@ void spike_op(ddps_handle* h, int op, const int32_t* tf, const int32_t* tm, cons
 // tensor-memory class, lists [ptr[cls], ptr[cls + 1]) of `list`.
 template <typename T>
 void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* ptr, int64_t j0,
-                  T* X, T* Tb, cudaStream_t s) {
+                  T* X, T* Tb, const uint8_t* pleaf, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (!h->tc_passes) return;
     for (int cls = 0; cls < 4; ++cls) {
@@ -432,7 +437,7 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
       if (n <= 0) continue;
       launch_front_gemm_tc(bwd ? 1 : 0, cls, h->tc_passes, h->F, list + ptr[cls], n,
                            bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X,
-                           h->A.n, Tb, (int64_t)h->A.idx.size(), (float*)h->D, h->derr,
+                           h->A.n, Tb, (int64_t)h->A.idx.size(), (float*)h->D, pleaf, h->derr,
                            h->opt.debug_wait_timeout, s);
       h->launches++;
     }
@@ -611,10 +616,11 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
         Prof pr(h, DDPS_PROF_SPIKE_FWD, s);
         const int64_t q = c * A.nlevels + L;
         const int32_t ng = (int32_t)(h->fw_g_ptr[q + 1] - h->fw_g_ptr[q]);
+        const uint8_t* pleaf = h->fw_pleaf ? h->fw_pleaf + c * nf : nullptr;
         launch_spike_gather<T>(h->F, h->fw_g + h->fw_g_ptr[q], ng, h->block_ncols, j0, NR, X, Tb,
-                               h->fw_active + c * nf, (const T*)h->D, h->fz_flag, s);
+                               h->fw_active + c * nf, (const T*)h->D, h->fz_flag, pleaf, s);
         h->launches += ng > 0;
-        fused_fronts<T>(h, false, h->fz, h->fz_ptr.data() + 4 * q, j0, X, Tb, s);
+        fused_fronts<T>(h, false, h->fz, h->fz_ptr.data() + 4 * q, j0, X, Tb, pleaf, s);
         spike_op<T>(h, OP_FWD_LINV, h->fw_kf + h->fw_k_ptr[q], h->fw_km + h->fw_k_ptr[q],
                     h->fw_ka ? h->fw_ka + h->fw_k_ptr[q] : nullptr, (int32_t)(h->fw_k_ptr[q + 1] - h->fw_k_ptr[q]),
                     arena, j0, X, Tb, s);
@@ -624,7 +630,7 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
       }
       for (int L = 0; L < A.nlevels; ++L) {
         Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
-        fused_fronts<T>(h, true, h->bz, h->bz_ptr.data() + 4 * L, j0, X, Tb, s);
+        fused_fronts<T>(h, true, h->bz, h->bz_ptr.data() + 4 * L, j0, X, Tb, nullptr, s);
         const int32_t first = h->tk_ptr[L], nt = h->tk_ptr[L + 1] - h->tk_ptr[L];
         spike_op<T>(h, OP_BWD_U12, h->tk_front + first, h->tk_m0 + first,
                     h->tc_aoff[OP_BWD_U12] ? h->tc_aoff[OP_BWD_U12] + first : nullptr, nt, arena,
@@ -858,7 +864,7 @@ void autotune_block_solve(ddps_handle* h, cudaStream_t s) {
     } else if (!which || h->nrt > 0) {
       CK(cudaMemsetAsync(h->o_tmp, 0, nn * sizeof(double), s));
       CK(cudaMemsetAsync(h->pc_zhat, 0, std::max<int64_t>((int64_t)A.c.size(), 1) * sizeof(double), s));
-      for (int v = SPMV_STREAM; v <= SPMV_VEC8; ++v) {
+      for (int v = SPMV_STREAM; v <= SPMV_WARP; ++v) {
         auto run = [&]() {
           if (which == 0)
             launch_spmv(h->rowptr, h->colind, h->vals, nn, h->o_tmp, h->o_xt, s, v);
@@ -1419,6 +1425,7 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
   const int64_t NR = std::max<int32_t>(h->NR, 1);
   const int64_t nchunks = A.max_rhs > 0 ? (A.max_rhs + NR - 1) / NR : 0;
   std::vector<uint8_t> active((size_t)std::max<int64_t>(nchunks, 1) * nf, 0);
+  std::vector<uint8_t> pleaf((size_t)std::max<int64_t>(nchunks, 1) * nf, 0);
   std::vector<int32_t> g, kfo, kmo, rfo, rmo;
   std::vector<int64_t> kao, rao;
   h->fw_g_ptr.assign(1, 0);
@@ -1435,9 +1442,17 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
         for (int32_t f : col_fronts[c0 + gperm[c0 + pcol]])
           for (int32_t a = f; a >= 0 && !act[a]; a = A.f_parent[a]) act[a] = 1;
     }
+    uint8_t* pl = pleaf.data() + c * nf;
+    if (tc)
+      for (int64_t f = 0; f < nf; ++f) {
+        if (!act[f] || !fused[f]) continue;
+        bool child = false;
+        for (int32_t ci = A.f_cbeg[f]; ci < A.f_cend[f] && !child; ++ci) child = act[A.children[ci]];
+        pl[f] = !child;
+      }
     for (int L = 0; L < A.nlevels; ++L) {
       for (int32_t q = A.level_ptr[L]; q < A.level_ptr[L + 1]; ++q)
-        if (act[A.level_fronts[q]]) g.push_back(A.level_fronts[q]);
+        if (act[A.level_fronts[q]] && !pl[A.level_fronts[q]]) g.push_back(A.level_fronts[q]);
       for (int32_t t = h->fk_ptr[L]; t < h->fk_ptr[L + 1]; ++t)
         if (act[kf[t]]) {
           kfo.push_back(kf[t]);
@@ -1463,6 +1478,7 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
     }
   }
   h->fw_active = dupload(h, active);
+  if (tc) h->fw_pleaf = dupload(h, pleaf);
   h->fw_g = dupload(h, g);
   h->fw_kf = dupload(h, kfo);
   h->fw_km = dupload(h, kmo);
@@ -1913,6 +1929,10 @@ bool valid_options(const ddps_options& o, std::string& why) {
     why = "factor_kind must be LU or ILU0";
     return false;
   }
+  if (o.csr_kernel < -1 || o.csr_kernel > SPMV_WARP) {
+    why = "csr_kernel must be -1 (tuned) or 0-4";
+    return false;
+  }
   if (o.factor_kind == DDPS_FACTOR_ILU0 && o.spike_prec != o.factor_prec) {
     why = "ILU0 block factors take spike_prec equal to factor_prec (SIMT spike solves)";
     return false;
@@ -1992,6 +2012,7 @@ void ddps_default_options(ddps_options* o) {
   o->use_graphs = 1;
   o->persistent_solve = 1;
   o->autotune = 1;
+  o->csr_kernel = -1;
 }
 
 ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
@@ -2064,6 +2085,7 @@ static ddps_status factor_values(ddps_handle* h, const double* values, bool host
       else
         autotune_block_solve<float>(h, s);
     }
+    if (h->opt.csr_kernel >= 0) h->tune_spmv = h->tune_rt = h->opt.csr_kernel;
     h->factored = true;
   } catch (const Fail& f) {
     return fail(h, f);
@@ -2315,7 +2337,7 @@ ddps_status ddps_get_tuning(const ddps_handle* h, char* buf, int64_t cap, int64_
   if (!h) return DDPS_ERR_INVALID_ARG;
   static const char* names[] = {"warp", "cta8", "cl1", "cl2", "cl4", "cl8"};
   std::ostringstream o;
-  static const char* csr[] = {"stream", "vec4", "vec8"};
+  static const char* csr[] = {"stream", "vec4", "vec8", "block", "warp"};
   o << "{\"tuned\": " << (h->tuned ? "true" : "false") << ", \"persistent_from_level\": "
     << h->persist_L << ", \"spmv\": \"" << csr[h->tune_spmv] << "\", \"spmv_ms\": "
     << h->tune_spmv_ms << ", \"rt_residual\": \"" << csr[h->tune_rt] << "\", \"levels\": [";

@@ -159,10 +159,12 @@ int spike_tile_m();
 template <typename T>
 // active (per front, may be null): children with active[c] == 0 are skipped.
 // D (may be null): for children with dflag[c] != 0 the update rows of their
-// forward product are held apart in D (same row indexing as Tb) and added here.
+// forward product are held apart in D (same row indexing as Tb) and added here;
+// children with skipT[c] != 0 (skipT may be null) have no working rows in Tb
+// and contribute D alone.
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
-                         const T* D, const uint8_t* dflag, cudaStream_t s);
+                         const T* D, const uint8_t* dflag, const uint8_t* skipT, cudaStream_t s);
 // spike_tc.cu: the same ops on the tensor cores (fp32 factors, bf16 operands,
 // fp32 accumulation); passes = 1 (hi*hi) or 3 (hi*hi + hi*lo + lo*hi).  A wait
 // that runs out writes error code 2 into err[0].
@@ -197,8 +199,8 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
                           const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
-                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
-                          int inject_wait, cudaStream_t s);
+                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D,
+                          const uint8_t* pleaf, long long* err, int inject_wait, cudaStream_t s);
 void launch_spike_gemm_tc(int op, int passes, DevFronts F, const int32_t* tile_front,
                           const int32_t* tile_m0, const int64_t* tile_aoff,
                           const unsigned char* atc, int32_t ntiles, const int64_t* block_ncols,
@@ -235,8 +237,10 @@ template <typename T>
 void launch_bwd1(DevFronts F, const int32_t* list, int32_t nf, int32_t max_m, const T* arena,
                  T* w, cudaStream_t s, int cfg = SOLVE_AUTO);
 // CSR product kernels (the autotuner picks per matrix): row blocks streamed
-// through shared memory, or 4 / 8 lanes per row.
-enum { SPMV_STREAM = 0, SPMV_VEC4 = 1, SPMV_VEC8 = 2 };
+// through shared memory (SPMV_BLOCK: all of a thread's loads of the block
+// issued at once, 16-byte vectors), 4 / 8 lanes per row, or 32-row groups
+// per warp copied asynchronously into shared memory (SPMV_WARP).
+enum { SPMV_STREAM = 0, SPMV_VEC4 = 1, SPMV_VEC8 = 2, SPMV_BLOCK = 3, SPMV_WARP = 4 };
 void launch_spmv(const int32_t* rowptr, const int32_t* colind, const double* vals, int64_t n,
                  const double* x, double* y, cudaStream_t s, int variant = SPMV_STREAM);
 // y_out = y - R~ zhat (R~ rows over original indices, reduced columns)

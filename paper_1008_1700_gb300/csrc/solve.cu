@@ -545,6 +545,152 @@ __global__ void __launch_bounds__(kStreamRows)
   }
 }
 
+// The same row blocks with every load of the block's entries issued at once:
+// the entries from rowptr[r0] rounded down to a multiple of 4 are read in
+// groups of 4 (one 16-byte load of column indices, two of values), up to
+// kBlockGroups groups per thread, before any x is gathered; the products
+// and the row sums are those of k_csr_stream, in the same order.
+constexpr int kBlockGroups = kStreamCap / 4 / kStreamRows;
+
+template <int SUB>
+__global__ void __launch_bounds__(kStreamRows)
+    k_csr_block(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
+                const double* __restrict__ b, double* __restrict__ y) {
+  __shared__ double prod[kStreamCap];
+  const int tid = threadIdx.x;
+  const int32_t nnz = rowptr[n];
+  for (int64_t r0 = (int64_t)blockIdx.x * kStreamRows; r0 < n;
+       r0 += (int64_t)gridDim.x * kStreamRows) {
+    const int64_t r1 = min(n, r0 + kStreamRows);
+    const int64_t row = r0 + tid;
+    const int32_t e0 = rowptr[r0], e1 = rowptr[r1];
+    const int32_t ea = e0 & ~3;
+    int32_t ra = 0, rb = 0;
+    if (row < r1) {
+      ra = rowptr[row];
+      rb = rowptr[row + 1];
+    }
+    double s = 0.0;
+    if (e1 - ea <= kStreamCap) {
+      int4 c[kBlockGroups];
+      double2 v[kBlockGroups][2];
+#pragma unroll
+      for (int g = 0; g < kBlockGroups; ++g) {
+        const int32_t e = ea + 4 * (tid + g * kStreamRows);
+        if (e < e1) {
+          if (e + 4 <= nnz) {
+            c[g] = *reinterpret_cast<const int4*>(colind + e);
+            v[g][0] = *reinterpret_cast<const double2*>(vals + e);
+            v[g][1] = *reinterpret_cast<const double2*>(vals + e + 2);
+          } else {  // the last entries of the matrix
+            const int32_t l = nnz - 1;
+            c[g] = make_int4(colind[e], colind[min(e + 1, l)], colind[min(e + 2, l)], colind[min(e + 3, l)]);
+            v[g][0] = make_double2(vals[e], vals[min(e + 1, l)]);
+            v[g][1] = make_double2(vals[min(e + 2, l)], vals[min(e + 3, l)]);
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kBlockGroups; ++g) {
+        const int32_t e = ea + 4 * (tid + g * kStreamRows);
+        if (e < e1) {
+          const int32_t cc[4] = {c[g].x, c[g].y, c[g].z, c[g].w};
+          const double vv[4] = {v[g][0].x, v[g][0].y, v[g][1].x, v[g][1].y};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (e + j >= e0 && e + j < e1) prod[e + j - ea] = vv[j] * x[cc[j]];
+        }
+      }
+      __syncthreads();
+      for (int32_t j = ra - ea; j < rb - ea; ++j) s += prod[j];
+      __syncthreads();
+    } else {
+      for (int32_t j = ra; j < rb; ++j) s += vals[j] * x[colind[j]];
+    }
+    if (row < r1) y[row] = SUB ? b[row] - s : s;
+  }
+}
+
+// The same product by warps over 32 consecutive rows: the lanes copy the
+// rows' entries (from rowptr[r0] rounded down to a multiple of 4, at most
+// kWarpCap) into the warp's shared buffers with 16-byte asynchronous copies,
+// which hold no registers, so that many warps keep their copies in flight;
+// the products are formed in place, four entries per lane, and lane r sums
+// row r's in order (the order and the rounding of k_csr_stream).  Longer
+// row groups take the entries from global memory.
+constexpr int kWarpRows = 32, kWarpCap = 512, kWarpWarps = 8;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+template <int SUB>
+__global__ void __launch_bounds__(kWarpRows * kWarpWarps)
+    k_csr_warp(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+               const double* __restrict__ vals, int64_t n, const double* __restrict__ x,
+               const double* __restrict__ b, double* __restrict__ y) {
+  __shared__ __align__(16) double sv_all[kWarpWarps][kWarpCap];
+  __shared__ __align__(16) int32_t sc_all[kWarpWarps][kWarpCap];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* __restrict__ sv = sv_all[wib];
+  int32_t* __restrict__ sc = sc_all[wib];
+  const int32_t nnz = rowptr[n];
+  const int64_t nch = (n + kWarpRows - 1) / kWarpRows;
+  for (int64_t ch = (int64_t)blockIdx.x * kWarpWarps + wib; ch < nch;
+       ch += (int64_t)gridDim.x * kWarpWarps) {
+    const int64_t r0 = ch * kWarpRows, row = r0 + lane, r1 = min(n, r0 + kWarpRows);
+    int32_t ra = 0, rb = 0;
+    if (row < r1) {
+      ra = rowptr[row];
+      rb = rowptr[row + 1];
+    }
+    const int32_t e0 = __shfl_sync(0xffffffffu, ra, 0);
+    const int32_t e1 = __shfl_sync(0xffffffffu, rb, (int)(r1 - r0 - 1));
+    const int32_t ea = e0 & ~3;
+    double s = 0.0;
+    if (e1 - ea <= kWarpCap) {
+      const int ng = (e1 - ea + 3) >> 2;
+      for (int g = lane; g < ng; g += 32) {
+        const int32_t e = ea + 4 * g;
+        const int left = nnz - e;  // >= 1: e < e1 <= nnz
+        cp_async16(sc + 4 * g, colind + e, 4 * min(4, left));
+        cp_async16(sv + 4 * g, vals + e, 8 * min(2, left));
+        if (left > 2) cp_async16(sv + 4 * g + 2, vals + e + 2, 8 * min(2, left - 2));
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+      // products in place, four entries per lane and group, every x gather of
+      // a lane in flight at once
+#pragma unroll
+      for (int q = 0; q < kWarpCap / 128; ++q) {
+        const int g = lane + 32 * q;
+        if (g < ng) {
+          const int4 c = *reinterpret_cast<const int4*>(sc + 4 * g);
+          double2* pv = reinterpret_cast<double2*>(sv + 4 * g);
+          const double2 v01 = pv[0], v23 = pv[1];
+          const int32_t e = ea + 4 * g;
+          const double x0 = e >= e0 ? x[c.x] : 0.0;
+          const double x1 = e + 1 < e1 ? x[c.y] : 0.0;
+          const double x2 = e + 2 < e1 ? x[c.z] : 0.0;
+          const double x3 = e + 3 < e1 ? x[c.w] : 0.0;
+          pv[0] = make_double2(__dmul_rn(v01.x, x0), __dmul_rn(v01.y, x1));
+          pv[1] = make_double2(__dmul_rn(v23.x, x2), __dmul_rn(v23.y, x3));
+        }
+      }
+      __syncwarp();
+      for (int32_t j = ra - ea; j < rb - ea; ++j) s += sv[j];
+      __syncwarp();  // read before the next group overwrites the buffers
+    } else {
+      for (int32_t j = ra; j < rb; ++j) s += __dmul_rn(vals[j], x[colind[j]]);
+    }
+    if (row < r1) y[row] = SUB ? b[row] - s : s;
+  }
+}
+
 // The same product with LPR lanes per row (CSR-vector): the lanes of a row
 // take its entries LPR apart, each with all of its (up to 4) loads in flight
 // before the gathers of x, and the row sum is a shuffle reduction in
@@ -962,14 +1108,21 @@ void launch_bwd_persist(DevFronts F, const int32_t* order, int32_t nitems, int32
                                               next, err);
 }
 
-// CSR products: `variant` SPMV_STREAM (row blocks through shared memory) or
+// CSR products: `variant` SPMV_STREAM / SPMV_BLOCK (row blocks through shared
+// memory), SPMV_WARP (32-row groups per warp, asynchronous copies) or
 // SPMV_VEC4 / SPMV_VEC8 (4 or 8 lanes per row); chosen by the autotuner.
 template <int SUB>
 static void launch_csr(int variant, const int32_t* rowptr, const int32_t* colind,
                        const double* vals, int64_t n, const double* x, const double* b, double* y,
                        cudaStream_t s) {
   if (n <= 0) return;
-  if (variant == SPMV_VEC4)
+  if (variant == SPMV_WARP)
+    k_csr_warp<SUB><<<grid_for((n + kWarpRows - 1) / kWarpRows, kWarpWarps, 1 << 30),
+                      kWarpRows * kWarpWarps, 0, s>>>(rowptr, colind, vals, n, x, b, y);
+  else if (variant == SPMV_BLOCK)
+    k_csr_block<SUB><<<grid_for(n, kStreamRows, 1 << 30), kStreamRows, 0, s>>>(rowptr, colind,
+                                                                                vals, n, x, b, y);
+  else if (variant == SPMV_VEC4)
     k_csr_vec<SUB, 4><<<grid_for(n * 4, 256, 1 << 30), 256, 0, s>>>(rowptr, colind, vals, n, x, b, y);
   else if (variant == SPMV_VEC8)
     k_csr_vec<SUB, 8><<<grid_for(n * 8, 256, 1 << 30), 256, 0, s>>>(rowptr, colind, vals, n, x, b, y);

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads)
                    const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                    const T* __restrict__ X, T* __restrict__ Tb,
                    const uint8_t* __restrict__ active, const T* __restrict__ D,
-                   const uint8_t* __restrict__ dflag) {
+                   const uint8_t* __restrict__ dflag, const uint8_t* __restrict__ skipT) {
   using V = typename GatherVec<T>::V;
   constexpr int VN = GatherVec<T>::n;
   const int32_t f = list[blockIdx.x];
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads)
     if (active && !active[c]) continue;  // a child untouched by this chunk contributes zero
     const int32_t kc = F.k[c], rc = F.m[c] - kc;
     const int32_t* __restrict__ rel = F.rel + F.rel_off[c];
-    const T* __restrict__ Tc = Tb + (F.idx_off[c] + kc) * NR;
+    const T* __restrict__ Tc = skipT && skipT[c] ? nullptr : Tb + (F.idx_off[c] + kc) * NR;
     // the child's own forward update (kept apart by the fused products)
     const T* __restrict__ Dc = D && dflag[c] ? D + (F.idx_off[c] + kc) * NR : nullptr;
     for (int i0 = warp * 4; i0 < rc; i0 += 32) {
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads)
         const int i = i0 + u;
         row[u] = i < rc ? rel[i] : 0;
         if (i < rc) {
-          src[u] = *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col);
+          src[u] = Tc ? *reinterpret_cast<const V*>(Tc + (int64_t)i * NR + col) : zero;
           d[u] = *reinterpret_cast<const V*>(Tf + (int64_t)row[u] * NR + col);
           if (Dc) e[u] = *reinterpret_cast<const V*>(Dc + (int64_t)i * NR + col);
         }
@@ -253,12 +253,12 @@ int spike_tile_m() {
 template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
-                         const T* D, const uint8_t* dflag, cudaStream_t s) {
+                         const T* D, const uint8_t* dflag, const uint8_t* skipT, cudaStream_t s) {
   if (nf <= 0) return;
   const int per = 32 * GatherVec<T>::n;
   dim3 grid(nf, (NR + per - 1) / per);
   k_spike_gather<T><<<grid, kThreads, 0, s>>>(F, list, block_ncols, j0, NR, X, Tb, active, D,
-                                              dflag);
+                                              dflag, skipT);
 }
 
 template <typename T>
@@ -290,7 +290,7 @@ void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int
   template int spike_tile_m<T>();                                                               \
   template void launch_spike_gather<T>(DevFronts, const int32_t*, int32_t, const int64_t*,     \
                                        int64_t, int32_t, const T*, T*, const uint8_t*,         \
-                                       const T*, const uint8_t*, cudaStream_t);                \
+                                       const T*, const uint8_t*, const uint8_t*, cudaStream_t); \
   template void launch_spike_gemm<T>(int, DevFronts, const int32_t*, const int32_t*, int32_t,  \
                                      const T*, const int64_t*, int64_t, int32_t, T*, T*,       \
                                      cudaStream_t);

@@ -740,7 +740,8 @@ __device__ __forceinline__ void st_cols4(float* p, float4 v, int nv) {
 // one front, and each role keeps its current front's fields (FItem).
 constexpr int kTab = 32;
 struct FMeta {
-  int32_t f, k, nout, K, row0, tb0, ncols, pad;
+  int32_t f, k, nout, K, row0, tb0, ncols;
+  int32_t fromx;  // forward: the working rows are the front's pivot rows of X
   int64_t wo;
 };
 struct FCtx {
@@ -754,10 +755,11 @@ struct FCtx {
   int32_t NR;
   const FMeta* tab;  // fronts p0 .. p0 + ntab - 1 of the list
   int32_t p0, ntab;
+  const uint8_t* pleaf;  // forward: fronts without active children (may be null)
 };
 struct FItem {
   int32_t p = -1;  // position of the front in the launch's list
-  int32_t f;
+  int32_t f, fromx;
   int32_t k, nout, K, nf, nkt, cv;
   int64_t ncols, n0, row0, tb0;
   const int32_t* idx;
@@ -773,7 +775,7 @@ __device__ __forceinline__ void fmeta_load(const FCtx& c, int32_t f, FMeta& m) {
   m.row0 = (int32_t)c.F.row0[f];
   m.tb0 = (int32_t)c.F.idx_off[f];
   m.ncols = (int32_t)min((int64_t)c.NR, c.block_ncols[c.F.block[f]] - c.j0);
-  m.pad = 0;
+  m.fromx = DIR == DIR_FWD && c.pleaf && c.pleaf[f] ? 1 : 0;
   m.wo = c.woff[f];
 }
 
@@ -788,6 +790,7 @@ __device__ __forceinline__ bool fitem(const FCtx& c, int it, FItem& w) {
     else
       fmeta_load<DIR>(c, c.fronts[p], m);
     w.f = m.f;
+    w.fromx = m.fromx;
     w.k = m.k;
     w.nout = m.nout;
     w.K = m.K;
@@ -814,8 +817,10 @@ __device__ __forceinline__ bool fitem(const FCtx& c, int it, FItem& w) {
 //   warps 16-19 (row producers, stage g by warp 16 + g % NPROD): the stage's
 //     32 panel rows (fp32, 128 columns) into its slot with tensor copies:
 //     forward, the rows are consecutive working rows of the front (one tile
-//     copy); backward, pivot rows and update rows gathered through the front's
-//     row list, four rows per copy.  Every slot belongs to one warp;
+//     copy; for a front none of whose children is active in the pass they
+//     are its pivot rows of X, which no gather has copied); backward, pivot
+//     rows and update rows gathered through the front's row list, four rows
+//     per copy.  Every slot belongs to one warp;
 //   warp 20 lane 0 (W producer): the stage's W block into a ring of SW slots;
 //   warps 0-7 (converters, two groups of four on alternate stages): read the
 //     slot's fp32 rows, then (after a barrier of the group's warps) overwrite
@@ -852,8 +857,9 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
                     const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
                     const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                     float* __restrict__ X, float* __restrict__ Tb, float* __restrict__ D,
-                    long long* __restrict__ err, int inject_wait,
-                    const __grid_constant__ CUtensorMap tm_src) {
+                    const uint8_t* __restrict__ pleaf, long long* __restrict__ err,
+                    int inject_wait, const __grid_constant__ CUtensorMap tm_src,
+                    const __grid_constant__ CUtensorMap tm_x) {
   // every ring slot is always filled by the same producer warp, so that no
   // producer waits on a slot barrier more than one phase ahead of it
   static_assert(SR % NPROD == 0 && SR % FG_CGROUPS == 0 && NPROD <= FG_NPROD &&
@@ -883,7 +889,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
   const int it0 = (int)blockIdx.x * per, it1 = min(nitems, it0 + per);
   const int32_t p0 = it0 / nct;
   const int32_t ntab = it1 > it0 ? min(kTab, (it1 - 1) / nct - p0 + 1) : 0;
-  const FCtx ctx{F, fronts, nct, woff, wpk, block_ncols, j0, NR, tab, p0, ntab};
+  const FCtx ctx{F, fronts, nct, woff, wpk, block_ncols, j0, NR, tab, p0, ntab, pleaf};
   if (warp == 1 && lane < ntab) fmeta_load<DIR>(ctx, fronts[p0 + lane], tab[lane]);  // read before the barrier below
 
   if (warp == 0) {
@@ -980,8 +986,12 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       if (DIR == DIR_FWD) {
         if (lane == 0) {
           mbar_expect_tx(smem_u32(&raw_full[sl]), kSlot);
-          tma_tile_2d(dst, &tm_src, (int32_t)cur.w.n0, (int32_t)(cur.w.tb0 + cur.kt * TC_BK),
-                      smem_u32(&raw_full[sl]));
+          if (cur.w.fromx)
+            tma_tile_2d(dst, &tm_x, (int32_t)cur.w.n0, (int32_t)(cur.w.row0 + cur.kt * TC_BK),
+                        smem_u32(&raw_full[sl]));
+          else
+            tma_tile_2d(dst, &tm_src, (int32_t)cur.w.n0, (int32_t)(cur.w.tb0 + cur.kt * TC_BK),
+                        smem_u32(&raw_full[sl]));
         }
       } else {
         const int32_t r = (int32_t)row;
@@ -1269,17 +1279,20 @@ bool panel_map(CUtensorMap* map, const float* base, int64_t rows, int32_t NR, in
 template <int DIR, int NT, int PASSES>
 void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                   const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
-                  float* X, int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
-                  int inject, cudaStream_t s) {
+                  float* X, int64_t x_rows, float* Tb, int64_t tb_rows, float* D,
+                  const uint8_t* pleaf, long long* err, int inject, cudaStream_t s) {
   using C = FrontCfg<NT, PASSES>;
   auto kern = k_front_gemm_tc<DIR, NT, PASSES, C::SR, C::SW, C::NACC, C::NMMA, C::NPROD>;
   constexpr size_t sm = (size_t)C::SR * TC_BK * TC_BN * 4 +
                         (size_t)C::SW * (PASSES == 3 ? 2 : 1) * NT * TC_BK * 2 +
                         (size_t)FG_NEPI * 16 * 32 * sizeof(float);
-  // forward: tiles of 32 working rows; backward: single rows for the gathers
-  CUtensorMap tm;
-  const bool ok = DIR == DIR_FWD ? panel_map(&tm, Tb, tb_rows, NR, TC_BK)
-                                 : panel_map(&tm, X, x_rows, NR, 1);
+  // forward: tiles of 32 working rows (of Tb, or of X for fronts without
+  // active children); backward: single rows of X for the gathers
+  CUtensorMap tm, tmx;
+  const bool ok = DIR == DIR_FWD
+                      ? panel_map(&tm, Tb, tb_rows, NR, TC_BK) && panel_map(&tmx, X, x_rows, NR, TC_BK)
+                      : panel_map(&tm, X, x_rows, NR, 1);
+  if (DIR != DIR_FWD) tmx = tm;
   if (!ok) {
     record_launch_error(cudaErrorInvalidValue);
     return;
@@ -1290,17 +1303,17 @@ void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t
   const int32_t nitems = nfr * nct;
   const int32_t grid = std::min(nitems, nsm);
   kern<<<grid, FG_THREADS, sm, s>>>(F, fronts, nitems, nct, woff, wpk, block_ncols, j0, NR, X, Tb,
-                                    D, err, inject, tm);
+                                    D, pleaf, err, inject, tm, tmx);
 }
 
 template <int DIR, int PASSES>
 void dispatch_front(int cls, DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t* woff,
                     const unsigned char* wpk, const int64_t* block_ncols, int64_t j0, int32_t NR,
                     float* X, int64_t x_rows, float* Tb, int64_t tb_rows, float* D,
-                    long long* err, int inject, cudaStream_t s) {
+                    const uint8_t* pleaf, long long* err, int inject, cudaStream_t s) {
 #define DDPS_FRONT(NT)                                                                           \
   launch_front<DIR, NT, PASSES>(F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb, \
-                                tb_rows, D, err, inject, s)
+                                tb_rows, D, pleaf, err, inject, s)
   switch (cls) {
     case 0:
       DDPS_FRONT(64);
@@ -1415,12 +1428,12 @@ void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, i
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,
                           const int64_t* block_ncols, int64_t j0, int32_t NR, float* X,
-                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D, long long* err,
-                          int inject_wait, cudaStream_t s) {
+                          int64_t x_rows, float* Tb, int64_t tb_rows, float* D,
+                          const uint8_t* pleaf, long long* err, int inject_wait, cudaStream_t s) {
   if (nfr <= 0) return;
 #define DDPS_DISP(DD, P)                                                                           \
   dispatch_front<DD, P>(cls, F, fronts, nfr, woff, wpk, block_ncols, j0, NR, X, x_rows, Tb,      \
-                        tb_rows, D, err, inject_wait, s)
+                        tb_rows, D, pleaf, err, inject_wait, s)
   if (bwd) {
     if (passes == 3)
       DDPS_DISP(DIR_BWD, 3);

@@ -38,7 +38,7 @@ class ddps_options(C.Structure):
                 ("ghat_mode", C.c_int32), ("update_prec", C.c_int32),
                 ("reduced_solver", C.c_int32), ("use_graphs", C.c_int32),
                 ("persistent_solve", C.c_int32), ("factor_kind", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("csr_kernel", C.c_int32)]
 
 
 class ddps_solve_info(C.Structure):

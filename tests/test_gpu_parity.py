@@ -475,3 +475,28 @@ def test_autotuned_block_solve_shapes(tmp_path, monkeypatch):
         S.close()
     cache = json.loads((tmp_path / "tune.json").read_text())
     assert cache and all(v in range(6) for v in cache.values())
+
+
+def test_csr_kernels_agree():
+    """Every kernel of the products with A and R~ (row blocks, 4 or 8 lanes per
+    row, row blocks with all loads issued at once, 32-row groups per warp)
+    against A y; the row-block and row-group kernels sum in the same order
+    with the same rounding, so they agree bit for bit, and a whole solve
+    converges with each."""
+    P = W.small_convdiff_2d(151, 5)  # 22,801 rows in ragged blocks, nnz not a multiple of 4
+    A = DDPSOracle(P.n, P.rowptr, P.colind, P.values, P.block_ptr, spikes=False).A
+    y = np.random.default_rng(5).standard_normal(P.n)
+    out = {}
+    for kernel in range(5):
+        S = make_solver(P, csr_kernel=kernel, tol_out=1e-12, **FP64)
+        assert S.tuning()["spmv"] == ["stream", "vec4", "vec8", "block", "warp"][kernel]
+        out[kernel] = host(S.spmv(dev(y)))
+        assert relerr(out[kernel], A @ y) <= 1e-14, kernel
+        x, info = S.solve(dev(P.f))
+        assert info["status"] == "DDPS_OK", (kernel, info)
+        assert np.max(np.abs(P.f - A @ host(x))) / np.max(np.abs(P.f)) <= 1e-12, kernel
+        S.close()
+    assert P.colind.size % 4 != 0
+    assert np.array_equal(out[0], out[3]) and np.array_equal(out[0], out[4])
+    with pytest.raises(N.DDPSError, match="csr_kernel"):
+        make_solver(P, csr_kernel=5, **FP64)
