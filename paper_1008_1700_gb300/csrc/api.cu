@@ -140,12 +140,18 @@ struct ddps_handle {
   int32_t *fk_front = nullptr, *fk_m0 = nullptr;
   std::vector<int32_t> tk_ptr, tr_ptr, fk_ptr;
   // fused front products (tensor-core spikes): packed W per front and direction
-  // (byte offsets, -1 where the front takes the tile ops), the fronts to pack,
-  // and the backward launch lists per (depth, class): [bz_ptr[4L + cls], bz_ptr[4L + cls + 1])
+  // (byte offsets, -1 where the front takes the tile ops) and the backward
+  // launch lists per (depth, class): [bz_ptr[4L + cls], bz_ptr[4L + cls + 1])
   unsigned char* wpk = nullptr;
   int64_t *woff_b = nullptr, *woff_f = nullptr;
-  int32_t *wpk_b = nullptr, *wpk_f = nullptr;
-  int32_t wpk_nb = 0, wpk_nf = 0, wpk_b_kb = 0, wpk_b_k = 0, wpk_f_kb = 0, wpk_f_k = 0;
+  // W forming work: (front, K-block) items per direction (0 forward, 1 backward)
+  // and class of the front's pivot count (shared memory of the launch)
+  struct WpkList {
+    int32_t* front = nullptr;
+    int32_t* kb = nullptr;
+    int32_t n = 0, max_k = 0;
+  };
+  WpkList wpk_items[2][3];
   int32_t* bz = nullptr;
   std::vector<int64_t> bz_ptr;
   // tensor-core spikes: A operands packed as bf16 blocks, byte offsets per op and tile
@@ -591,16 +597,14 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
           h->launches++;
         }
       }
-      if (h->wpk_nb > 0) {
-        launch_tc_w_pack(1, h->tc_passes, h->F, h->wpk_b, h->wpk_nb, h->wpk_b_kb, h->wpk_b_k,
-                         h->woff_b, arena, h->wpk, s);
-        h->launches++;
-      }
-      if (h->wpk_nf > 0) {
-        launch_tc_w_pack(0, h->tc_passes, h->F, h->wpk_f, h->wpk_nf, h->wpk_f_kb, h->wpk_f_k,
-                         h->woff_f, arena, h->wpk, s);
-        h->launches++;
-      }
+      for (int dir = 1; dir >= 0; --dir)
+        for (int cls = 0; cls < 3; ++cls) {
+          const ddps_handle::WpkList& wl = h->wpk_items[dir][cls];
+          if (wl.n <= 0) continue;
+          launch_tc_w_pack(dir, h->tc_passes, h->F, wl.front, wl.kb, wl.n, wl.max_k,
+                           dir ? h->woff_b : h->woff_f, arena, h->wpk, s);
+          h->launches++;
+        }
     }
   }
   if (m > 0 && h->opt.ghat_mode == DDPS_GHAT_EXPLICIT) {
@@ -1792,23 +1796,32 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       h->atc = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(run, 16));
       // packed W of the fused fronts
       std::vector<int64_t> wob(nfr, -1), wof(nfr, -1);
-      std::vector<int32_t> pb, pf;
+      std::vector<int32_t> pf;  // fused forward fronts
+      std::vector<int32_t> wf[2][3], wk[2][3];
+      int32_t wmax[2][3] = {};
       int64_t wrun = 0;
+      auto wclass = [](int32_t kk) { return kk <= 64 ? 0 : kk <= 160 ? 1 : 2; };
       for (int64_t f = 0; f < nfr; ++f) {
         const int32_t kk = A.f_k[f], mm = A.f_m[f];
+        const int wc = wclass(kk);
         if (fzb[f]) {
           wob[f] = wrun;
           wrun += tc_fused_w_bytes(passes, kk, mm);
-          pb.push_back((int32_t)f);
-          h->wpk_b_kb = std::max(h->wpk_b_kb, (mm + BK - 1) / BK);
-          h->wpk_b_k = std::max(h->wpk_b_k, kk);
+          for (int32_t kb = 0; kb < (mm + BK - 1) / BK; ++kb) {
+            wf[1][wc].push_back((int32_t)f);
+            wk[1][wc].push_back(kb);
+          }
+          wmax[1][wc] = std::max(wmax[1][wc], kk);
         }
         if (fzf[f]) {
           wof[f] = wrun;
           wrun += tc_fused_w_bytes(passes, mm, kk);
           pf.push_back((int32_t)f);
-          h->wpk_f_kb = std::max(h->wpk_f_kb, (kk + BK - 1) / BK);
-          h->wpk_f_k = std::max(h->wpk_f_k, kk);
+          for (int32_t kb = 0; kb < (kk + BK - 1) / BK; ++kb) {
+            wf[0][wc].push_back((int32_t)f);
+            wk[0][wc].push_back(kb);
+          }
+          wmax[0][wc] = std::max(wmax[0][wc], kk);
         }
       }
       h->wpk = (unsigned char*)dalloc_bytes(h, std::max<int64_t>(wrun, 16));
@@ -1820,10 +1833,16 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
       }
       h->woff_b = dupload(h, wob);
       h->woff_f = dupload(h, wof);
-      h->wpk_b = dupload(h, pb);
-      h->wpk_f = dupload(h, pf);
-      h->wpk_nb = (int32_t)pb.size();
-      h->wpk_nf = (int32_t)pf.size();
+      for (int dir = 0; dir < 2; ++dir)
+        for (int wc = 0; wc < 3; ++wc) {
+          ddps_handle::WpkList& wl = h->wpk_items[dir][wc];
+          wl.n = (int32_t)wf[dir][wc].size();
+          wl.max_k = wmax[dir][wc];
+          if (wl.n) {
+            wl.front = dupload(h, wf[dir][wc]);
+            wl.kb = dupload(h, wk[dir][wc]);
+          }
+        }
     }
     if (!A.ilu) {
       build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf);

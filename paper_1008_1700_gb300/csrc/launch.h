@@ -193,8 +193,9 @@ void launch_tc_pack_a(int op, int passes, DevFronts F, const int32_t* tile_front
 int tc_fused_max_rows();
 int tc_fused_class(int rows);
 int64_t tc_fused_w_bytes(int passes, int rows, int K);
-void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, int32_t nfr,
-                      int32_t max_kb, int32_t max_k, const int64_t* woff, const float* arena,
+// Items t < nitems: K-block kb[t] of front fronts[t]; max_k bounds their pivots.
+void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, const int32_t* kb,
+                      int32_t nitems, int32_t max_k, const int64_t* woff, const float* arena,
                       unsigned char* wpk, cudaStream_t s);
 void launch_front_gemm_tc(int bwd, int cls, int passes, DevFronts F, const int32_t* fronts,
                           int32_t nfr, const int64_t* woff, const unsigned char* wpk,

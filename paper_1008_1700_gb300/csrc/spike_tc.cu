@@ -613,14 +613,15 @@ __device__ __forceinline__ void fused_dims(int32_t k, int32_t m, int& nout, int&
 // The right factor's 32 columns are staged in shared memory ([k][33]).
 template <int DIR, int PASSES>
 __global__ void __launch_bounds__(TC_THREADS)
-    k_w_pack(DevFronts F, const int32_t* __restrict__ fronts, const int64_t* __restrict__ woff,
-             const float* __restrict__ arena, unsigned char* __restrict__ wpk) {
+    k_w_pack(DevFronts F, const int32_t* __restrict__ fronts, const int32_t* __restrict__ kbs,
+             const int64_t* __restrict__ woff, const float* __restrict__ arena,
+             unsigned char* __restrict__ wpk) {
   extern __shared__ float Rs[];
   const int32_t f = fronts[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
   int nout, K;
   fused_dims<DIR>(k, m, nout, K);
-  const int kb = blockIdx.y;
+  const int kb = kbs[blockIdx.x];
   if (kb * TC_BK >= K) return;
   const int nf = (nout + 15) & ~15;
   const float* __restrict__ A = arena + F.arena[f];
@@ -1400,15 +1401,14 @@ int64_t tc_fused_w_bytes(int passes, int rows, int K) {
   return (passes == 3 ? 2 : 1) * nf * TC_BK * 2 * nkb;
 }
 
-void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, int32_t nfr,
-                      int32_t max_kb, int32_t max_k, const int64_t* woff, const float* arena,
+void launch_tc_w_pack(int bwd, int passes, DevFronts F, const int32_t* fronts, const int32_t* kb,
+                      int32_t nitems, int32_t max_k, const int64_t* woff, const float* arena,
                       unsigned char* wpk, cudaStream_t s) {
-  if (nfr <= 0 || max_kb <= 0) return;
+  if (nitems <= 0) return;
   const size_t sm = (size_t)std::max(max_k, 1) * (TC_BK + 1) * sizeof(float);
-  dim3 grid(nfr, max_kb);
 #define DDPS_WPACK(D, P)                                                                        \
   record_launch_error(cudaFuncSetAttribute(k_w_pack<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));   \
-  k_w_pack<D, P><<<grid, TC_THREADS, sm, s>>>(F, fronts, woff, arena, wpk);
+  k_w_pack<D, P><<<nitems, TC_THREADS, sm, s>>>(F, fronts, kb, woff, arena, wpk);
   if (bwd) {
     if (passes == 3) {
       DDPS_WPACK(DIR_BWD, 3)
