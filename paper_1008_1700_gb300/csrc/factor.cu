@@ -115,37 +115,40 @@ __global__ void __launch_bounds__(kThreads)
   const int tid = threadIdx.x;
   const int jb = min(NB, k - j0);
   __shared__ T D[NB][NB + 1];
+  __shared__ double thr[NB];
   for (int t = tid; t < NB * NB; t += blockDim.x) {
     const int r = t % NB, c = t / NB;
     D[r][c] = (r < jb && c < jb) ? A[(j0 + r) + (int64_t)(j0 + c) * m] : T(r == c ? 1 : 0);
   }
+  if (tid < jb) thr[tid] = pivot_tol * rownorm[row0 + j0 + tid];
   __syncthreads();
-  for (int j = 0; j < jb; ++j) {
-    T piv = D[j][j];
-    const double thr = pivot_tol * rownorm[row0 + j0 + j];
-    const bool small = !(fabs((double)piv) > thr);
-    if (small) {
-      const double rep = thr > 0.0 ? thr : 1e-300;
-      piv = (T)((double)piv < 0.0 ? -rep : rep);
-    }
-    __syncthreads();  // every thread has read the pivot before it is replaced
-    if (small && tid == 0) {
-      if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
-        err[1] = f;
-        err[2] = row0 + j0 + j;
+  if (tid < 32) {
+    // the 32 x 32 LU by one warp: lane r owns row r of the updates
+    for (int j = 0; j < jb; ++j) {
+      T piv = D[j][j];
+      const bool small = !(fabs((double)piv) > thr[j]);
+      if (small) {
+        const double rep = thr[j] > 0.0 ? thr[j] : 1e-300;
+        piv = (T)((double)piv < 0.0 ? -rep : rep);
       }
-      D[j][j] = piv;
+      __syncwarp();  // every lane has read the pivot before it is replaced
+      if (small && tid == 0) {
+        if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+          err[1] = f;
+          err[2] = row0 + j0 + j;
+        }
+        D[j][j] = piv;
+      }
+      const T inv = T(1) / piv;
+      if (tid > j && tid < jb) {
+        const T l = D[tid][j] * inv;
+        D[tid][j] = l;
+        for (int c = j + 1; c < jb; ++c) D[tid][c] -= l * D[j][c];
+      }
+      __syncwarp();
     }
-    const T inv = T(1) / piv;
-    if (tid > j && tid < jb) D[tid][j] *= inv;
-    __syncthreads();
-    const int w = jb - 1 - j;
-    for (int t = tid; t < w * w; t += blockDim.x) {
-      const int r = j + 1 + t % w, c = j + 1 + t / w;
-      D[r][c] -= D[r][j] * D[j][c];
-    }
-    __syncthreads();
   }
+  __syncthreads();
   for (int t = tid; t < jb * jb; t += blockDim.x) {
     const int r = t % jb, c = t / jb;
     A[(j0 + r) + (int64_t)(j0 + c) * m] = D[r][c];
@@ -472,41 +475,78 @@ __global__ void k_tri_inverse_copy(DevFronts F, const int32_t* __restrict__ list
 // inversion of the diagonal triangles done in shared memory by one CTA, then
 // written back once.
 // ---------------------------------------------------------------------------
+constexpr int kLuPanel = 8;  // pivots per panel of the small-front LU
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_front_lu_small(DevFronts F, const int32_t* __restrict__ list, T* __restrict__ arena,
                      const double* __restrict__ rownorm, double pivot_tol,
                      long long* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);
   const int32_t f = list[blockIdx.x];
   const int32_t k = F.k[f], m = F.m[f];
+  double* th = reinterpret_cast<double*>(smem_raw);  // the k pivot thresholds
+  T* A = reinterpret_cast<T*>(smem_raw + (size_t)k * sizeof(double));
   T* __restrict__ G = arena + F.arena[f];
   T* v = A + (int64_t)m * m;  // 2 m scratch entries for the inversions
   const int64_t row0 = F.row0[f];
   const int tid = threadIdx.x;
   for (int t = tid; t < m * m; t += blockDim.x) A[t] = G[t];
+  for (int t = tid; t < k; t += blockDim.x) th[t] = pivot_tol * rownorm[row0 + t];
   __syncthreads();
-  for (int j = 0; j < k; ++j) {
-    T piv = A[j + j * m];
-    const double thr = pivot_tol * rownorm[row0 + j];
-    if (!(fabs((double)piv) > thr)) {
-      const double rep = thr > 0.0 ? thr : 1e-300;
-      piv = (T)((double)piv < 0.0 ? -rep : rep);
-      if (tid == 0 && atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
-        err[1] = f;
-        err[2] = row0 + j;
+  // right-looking LU in panels of kLuPanel pivots: warp 0 factors the panel
+  // columns, the CTA solves the panel rows of U12 and applies the rank-
+  // kLuPanel update to the trailing matrix; every entry sees its updates in
+  // pivot order, so the result is that of the unblocked elimination
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int jp = 0; jp < k; jp += kLuPanel) {
+    const int je = min(k, jp + kLuPanel);
+    if (warp == 0) {
+      for (int j = jp; j < je; ++j) {
+        T piv = A[j + j * m];
+        const double thr = th[j];
+        const bool small = !(fabs((double)piv) > thr);
+        if (small) {
+          const double rep = thr > 0.0 ? thr : 1e-300;
+          piv = (T)((double)piv < 0.0 ? -rep : rep);
+        }
+        __syncwarp();  // every lane has read the pivot before it is replaced
+        if (small && lane == 0) {
+          if (atomicCAS((unsigned long long*)&err[0], 0ull, 1ull) == 0ull) {
+            err[1] = f;
+            err[2] = row0 + j;
+          }
+          A[j + j * m] = piv;
+        }
+        const T inv = T(1) / piv;
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const T l = A[i + j * m] * inv;
+          A[i + j * m] = l;
+          for (int c = j + 1; c < je; ++c) A[i + c * m] -= l * A[j + c * m];
+        }
+        __syncwarp();
       }
     }
-    __syncthreads();  // every thread has read the pivot before it is replaced
-    if (tid == 0) A[j + j * m] = piv;
-    const T inv = T(1) / piv;
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) A[i + j * m] *= inv;
     __syncthreads();
-    // rank-1 update: one warp per column, lanes over rows (no index division)
-    for (int c = j + 1 + (tid >> 5); c < m; c += blockDim.x >> 5) {
-      const T u = A[j + c * m];
-      for (int i = j + 1 + (tid & 31); i < m; i += 32) A[i + c * m] -= A[i + j * m] * u;
+    // U12 rows of the panel: forward substitution with its unit-lower block
+    for (int c = je + tid; c < m; c += blockDim.x)
+      for (int j = jp; j < je; ++j) {
+        const T u = A[j + c * m];
+        for (int i = j + 1; i < je; ++i) A[i + c * m] -= A[i + j * m] * u;
+      }
+    __syncthreads();
+    // trailing update, one warp per column, lanes over rows
+    for (int c = je + warp; c < m; c += blockDim.x >> 5) {
+      T u[kLuPanel];
+#pragma unroll
+      for (int j = 0; j < kLuPanel; ++j) u[j] = jp + j < je ? A[jp + j + c * m] : T(0);
+      for (int i = je + lane; i < m; i += 32) {
+        T a = A[i + c * m];
+#pragma unroll
+        for (int j = 0; j < kLuPanel; ++j)
+          if (jp + j < je) a -= A[i + (jp + j) * m] * u[j];
+        A[i + c * m] = a;
+      }
     }
     __syncthreads();
   }
@@ -711,7 +751,7 @@ void launch_front_lu_small(DevFronts F, const int32_t* list, int32_t nf, int32_t
                            const double* rownorm_new, double pivot_tol, long long* err,
                            cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t sm = ((size_t)max_m * max_m + 2 * (size_t)max_m) * sizeof(T);
+  const size_t sm = ((size_t)max_m * max_m + 2 * (size_t)max_m) * sizeof(T) + (size_t)max_m * sizeof(double);
   if (sm > 48 * 1024)
     record_launch_error(cudaFuncSetAttribute(k_front_lu_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_front_lu_small<T><<<nf, kThreads, sm, s>>>(F, list, arena, rownorm_new, pivot_tol, err);
