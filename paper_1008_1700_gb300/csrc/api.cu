@@ -170,6 +170,13 @@ struct ddps_handle {
   // there by the fused product (no gather), and its parent's gather takes
   // only its own update rows (D)
   uint8_t* fw_pleaf = nullptr;
+  // per chunk (tensor-core spikes): the fronts whose pivot rows of X are
+  // cleared before the chunk (the active fronts, whose rows take the
+  // right-hand side, and the fronts the fused backward products do not take;
+  // the fused backward reads an inactive front's pivot rows as the zero row
+  // n of X instead), [zr_ptr[c], zr_ptr[c + 1]) of zr_front
+  int32_t* zr_front = nullptr;
+  std::vector<int64_t> zr_ptr;
   int32_t *fw_g = nullptr, *fw_kf = nullptr, *fw_km = nullptr, *fw_rf = nullptr, *fw_rm = nullptr;
   int64_t *fw_ka = nullptr, *fw_ra = nullptr;  // packed-A offsets (tensor-core path)
   std::vector<int64_t> fw_g_ptr, fw_k_ptr, fw_r_ptr;
@@ -443,8 +450,8 @@ void fused_fronts(ddps_handle* h, bool bwd, const int32_t* list, const int64_t* 
       if (n <= 0) continue;
       launch_front_gemm_tc(bwd ? 1 : 0, cls, h->tc_passes, h->F, list + ptr[cls], n,
                            bwd ? h->woff_b : h->woff_f, h->wpk, h->block_ncols, j0, h->NR, X,
-                           h->A.n, Tb, (int64_t)h->A.idx.size(), (float*)h->D, pleaf, h->derr,
-                           h->opt.debug_wait_timeout, s);
+                           h->A.n + 1, Tb, (int64_t)h->A.idx.size(), (float*)h->D, pleaf,
+                           h->derr, h->opt.debug_wait_timeout, s);
       h->launches++;
     }
   }
@@ -613,7 +620,13 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
     const int32_t NR = h->NR;
     const int64_t nf = (int64_t)A.f_k.size();
     for (int64_t j0 = 0, c = 0; j0 < A.max_rhs; j0 += NR, ++c) {
-      CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
+      if (h->zr_front) {
+        launch_zero_front_rows<T>(h->F, h->zr_front + h->zr_ptr[c],
+                                  (int32_t)(h->zr_ptr[c + 1] - h->zr_ptr[c]), NR, X, s);
+        h->launches++;
+      } else {
+        CK(cudaMemsetAsync(X, 0, (size_t)A.n * NR * sizeof(T), s));
+      }
       launch_spike_rhs<T>(h->rt_rownew, h->rt_rhscol, h->rt_src, h->nrt, h->vals, j0, NR, X, s);
       h->launches++;
       for (int L = A.nlevels - 1; L >= 0; --L) {
@@ -634,7 +647,8 @@ void factor_launches(ddps_handle* h, cudaStream_t s) {
       }
       for (int L = 0; L < A.nlevels; ++L) {
         Prof pr(h, DDPS_PROF_SPIKE_BWD, s);
-        fused_fronts<T>(h, true, h->bz, h->bz_ptr.data() + 4 * L, j0, X, Tb, nullptr, s);
+        fused_fronts<T>(h, true, h->bz, h->bz_ptr.data() + 4 * L, j0, X, Tb,
+                        h->zr_front ? h->fw_active + c * nf : nullptr, s);
         const int32_t first = h->tk_ptr[L], nt = h->tk_ptr[L + 1] - h->tk_ptr[L];
         spike_op<T>(h, OP_BWD_U12, h->tk_front + first, h->tk_m0 + first,
                     h->tc_aoff[OP_BWD_U12] ? h->tc_aoff[OP_BWD_U12] + first : nullptr, nt, arena,
@@ -1376,7 +1390,7 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
                           const std::vector<int32_t>& km, const std::vector<int32_t>& rf,
                           const std::vector<int32_t>& rm,
                           const std::vector<std::vector<int64_t>>& tc_off,
-                          const std::vector<uint8_t>& fused) {
+                          const std::vector<uint8_t>& fused, const std::vector<uint8_t>& fusedb) {
   const Analysis& A = h->A;
   const int64_t nf = (int64_t)A.f_k.size();
   const int64_t n = A.n;
@@ -1436,7 +1450,8 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
   h->fw_k_ptr.assign(1, 0);
   h->fw_r_ptr.assign(1, 0);
   h->fz_ptr.assign(1, 0);
-  std::vector<int32_t> fz;
+  h->zr_ptr.assign(1, 0);
+  std::vector<int32_t> fz, zr;
   const bool tc = !tc_off.empty();
   for (int64_t c = 0; c < nchunks; ++c) {
     uint8_t* act = active.data() + c * nf;
@@ -1447,6 +1462,11 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
           for (int32_t a = f; a >= 0 && !act[a]; a = A.f_parent[a]) act[a] = 1;
     }
     uint8_t* pl = pleaf.data() + c * nf;
+    if (tc) {
+      for (int64_t f = 0; f < nf; ++f)
+        if (act[f] || !fusedb[f]) zr.push_back((int32_t)f);
+      h->zr_ptr.push_back((int64_t)zr.size());
+    }
     if (tc)
       for (int64_t f = 0; f < nf; ++f) {
         if (!act[f] || !fused[f]) continue;
@@ -1482,7 +1502,10 @@ void build_sparse_forward(ddps_handle* h, const std::vector<int32_t>& kf,
     }
   }
   h->fw_active = dupload(h, active);
-  if (tc) h->fw_pleaf = dupload(h, pleaf);
+  if (tc) {
+    h->fw_pleaf = dupload(h, pleaf);
+    h->zr_front = dupload(h, zr);
+  }
   h->fw_g = dupload(h, g);
   h->fw_kf = dupload(h, kfo);
   h->fw_km = dupload(h, kmo);
@@ -1604,7 +1627,10 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     const int64_t budget = (int64_t)12 << 30;  // bytes for the two panels
     while (nr > 128 && (n + (int64_t)A.idx.size()) * nr * (int64_t)fs > budget) nr = (nr / 2 + 127) / 128 * 128;
     h->NR = (int32_t)nr;
-    h->X = dalloc_bytes(h, n * h->NR * (int64_t)fs);
+    // row n stays zero: the fused backward products read it as the pivot rows
+    // of the fronts the chunk leaves inactive
+    h->X = dalloc_bytes(h, (n + 1) * h->NR * (int64_t)fs);
+    CK(cudaMemset(h->X, 0, (size_t)(n + 1) * h->NR * fs));
     h->U = dalloc_bytes(h, std::max<int64_t>((int64_t)A.idx.size(), 1) * h->NR * (int64_t)fs);
   }
   for (int32_t kf : A.f_k) h->max_k = std::max(h->max_k, kf);
@@ -1845,7 +1871,7 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
         }
     }
     if (!A.ilu) {
-      build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf);
+      build_sparse_forward(h, fkf, fkm, rf, rm, tc_off_host, fzf, fzb);
     } else {
       // ILU(0): G^ keeps the coupling columns in ascending order
       h->gperm.resize(A.gcol_ptr[A.p]);

@@ -156,6 +156,10 @@ void launch_lu_trailing(DevFronts F, const int32_t* tile_front, const int32_t* t
 enum SpikeOp { OP_FWD_LINV = 0, OP_FWD_L21 = 1, OP_BWD_U12 = 2, OP_BWD_UINV = 3 };
 template <typename T>
 int spike_tile_m();
+// Clears the pivot rows of the listed fronts in the panel X (n x NR).
+template <typename T>
+void launch_zero_front_rows(DevFronts F, const int32_t* list, int32_t nf, int32_t NR, T* X,
+                            cudaStream_t s);
 template <typename T>
 // active (per front, may be null): children with active[c] == 0 are skipped.
 // D (may be null): for children with dflag[c] != 0 the update rows of their

@@ -133,6 +133,22 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The pivot rows of front list[blockIdx.x] (k consecutive rows of X, k * NR
+// entries) set to zero, 16 bytes per store.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_zero_front_rows(DevFronts F, const int32_t* __restrict__ list, int32_t NR, T* __restrict__ X) {
+  using V = typename GatherVec<T>::V;
+  constexpr int VN = GatherVec<T>::n;
+  const int32_t f = list[blockIdx.x];
+  V* __restrict__ p = reinterpret_cast<V*>(X + F.row0[f] * NR);
+  const int64_t nv = (int64_t)F.k[f] * NR / VN;  // NR is a multiple of 128
+  const V zero = {};
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < nv;
+       e += (int64_t)gridDim.y * blockDim.x)
+    p[e] = zero;
+}
+
 // C = beta * Cin + alpha * A B for one (front, 128-row) tile and 128 panel
 // columns; A is a block of the front (column-major, leading dimension m,
 // triangular for the two inverse ops), B rows come from the panel or from the
@@ -251,6 +267,13 @@ int spike_tile_m() {
 }
 
 template <typename T>
+void launch_zero_front_rows(DevFronts F, const int32_t* list, int32_t nf, int32_t NR, T* X,
+                            cudaStream_t s) {
+  if (nf <= 0) return;
+  k_zero_front_rows<T><<<dim3(nf, 8), kThreads, 0, s>>>(F, list, NR, X);
+}
+
+template <typename T>
 void launch_spike_gather(DevFronts F, const int32_t* list, int32_t nf, const int64_t* block_ncols,
                          int64_t j0, int32_t NR, const T* X, T* Tb, const uint8_t* active,
                          const T* D, const uint8_t* dflag, const uint8_t* skipT, cudaStream_t s) {
@@ -288,6 +311,8 @@ void launch_spike_gemm(int op, DevFronts F, const int32_t* tile_front, const int
 
 #define DDPS_INST_SP(T)                                                                         \
   template int spike_tile_m<T>();                                                               \
+  template void launch_zero_front_rows<T>(DevFronts, const int32_t*, int32_t, int32_t, T*,     \
+                                          cudaStream_t);                                        \
   template void launch_spike_gather<T>(DevFronts, const int32_t*, int32_t, const int64_t*,     \
                                        int64_t, int32_t, const T*, T*, const uint8_t*,         \
                                        const T*, const uint8_t*, const uint8_t*, cudaStream_t); \

@@ -742,7 +742,9 @@ __device__ __forceinline__ void st_cols4(float* p, float4 v, int nv) {
 constexpr int kTab = 32;
 struct FMeta {
   int32_t f, k, nout, K, row0, tb0, ncols;
-  int32_t fromx;  // forward: the working rows are the front's pivot rows of X
+  // forward: the working rows are the front's pivot rows of X; backward: the
+  // front is inactive in the pass, its pivot rows are read as the zero row
+  int32_t fromx;
   int64_t wo;
 };
 struct FCtx {
@@ -756,7 +758,9 @@ struct FCtx {
   int32_t NR;
   const FMeta* tab;  // fronts p0 .. p0 + ntab - 1 of the list
   int32_t p0, ntab;
-  const uint8_t* pleaf;  // forward: fronts without active children (may be null)
+  // forward: fronts without active children; backward: fronts active in the
+  // pass (may be null)
+  const uint8_t* pleaf;
 };
 struct FItem {
   int32_t p = -1;  // position of the front in the launch's list
@@ -776,7 +780,7 @@ __device__ __forceinline__ void fmeta_load(const FCtx& c, int32_t f, FMeta& m) {
   m.row0 = (int32_t)c.F.row0[f];
   m.tb0 = (int32_t)c.F.idx_off[f];
   m.ncols = (int32_t)min((int64_t)c.NR, c.block_ncols[c.F.block[f]] - c.j0);
-  m.fromx = DIR == DIR_FWD && c.pleaf && c.pleaf[f] ? 1 : 0;
+  m.fromx = c.pleaf && (DIR == DIR_FWD ? c.pleaf[f] != 0 : c.pleaf[f] == 0) ? 1 : 0;
   m.wo = c.woff[f];
 }
 
@@ -820,8 +824,9 @@ __device__ __forceinline__ bool fitem(const FCtx& c, int it, FItem& w) {
 //     forward, the rows are consecutive working rows of the front (one tile
 //     copy; for a front none of whose children is active in the pass they
 //     are its pivot rows of X, which no gather has copied); backward, pivot
-//     rows and update rows gathered through the front's row list, four rows
-//     per copy.  Every slot belongs to one warp;
+//     rows (the zero row of X for a front the pass leaves inactive, whose
+//     forward solution is zero) and update rows gathered through the front's
+//     row list, four rows per copy.  Every slot belongs to one warp;
 //   warp 20 lane 0 (W producer): the stage's W block into a ring of SW slots;
 //   warps 0-7 (converters, two groups of four on alternate stages): read the
 //     slot's fp32 rows, then (after a barrier of the group's warps) overwrite
@@ -858,7 +863,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
                     const int64_t* __restrict__ woff, const unsigned char* __restrict__ wpk,
                     const int64_t* __restrict__ block_ncols, int64_t j0, int32_t NR,
                     float* __restrict__ X, float* __restrict__ Tb, float* __restrict__ D,
-                    const uint8_t* __restrict__ pleaf, long long* __restrict__ err,
+                    const uint8_t* __restrict__ pleaf, int32_t zrow, long long* __restrict__ err,
                     int inject_wait, const __grid_constant__ CUtensorMap tm_src,
                     const __grid_constant__ CUtensorMap tm_x) {
   // every ring slot is always filled by the same producer warp, so that no
@@ -963,7 +968,8 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     auto row_of = [&](const FItem& w, int kk) -> int64_t {
       const int gk = kk * TC_BK + lane;
       if (gk >= w.K) return 0;
-      return DIR == DIR_BWD ? (gk < w.k ? w.row0 + gk : (int64_t)w.idx[gk]) : w.tb0 + gk;
+      return DIR == DIR_BWD ? (gk < w.k ? (w.fromx ? (int64_t)zrow : w.row0 + gk) : (int64_t)w.idx[gk])
+                            : w.tb0 + gk;
     };
     next_valid(it0);
     uint32_t g = 0;
@@ -1304,7 +1310,7 @@ void launch_front(DevFronts F, const int32_t* fronts, int32_t nfr, const int64_t
   const int32_t nitems = nfr * nct;
   const int32_t grid = std::min(nitems, nsm);
   kern<<<grid, FG_THREADS, sm, s>>>(F, fronts, nitems, nct, woff, wpk, block_ncols, j0, NR, X, Tb,
-                                    D, pleaf, err, inject, tm, tmx);
+                                    D, pleaf, (int32_t)(x_rows - 1), err, inject, tm, tmx);
 }
 
 template <int DIR, int PASSES>
