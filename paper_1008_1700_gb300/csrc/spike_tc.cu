@@ -765,7 +765,7 @@ struct FCtx {
 struct FItem {
   int32_t p = -1;  // position of the front in the launch's list
   int32_t f, fromx;
-  int32_t k, nout, K, nf, nkt, cv;
+  int32_t k, nout, K, nf, nkt, kt0, cv;  // stages kt0 .. nkt - 1
   int64_t ncols, n0, row0, tb0;
   const int32_t* idx;
   const unsigned char* w;
@@ -802,6 +802,9 @@ __device__ __forceinline__ bool fitem(const FCtx& c, int it, FItem& w) {
     w.ncols = m.ncols;
     w.nf = (w.nout + 15) & ~15;
     w.nkt = (w.K + TC_BK - 1) / TC_BK;
+    // backward, inactive front: the stages of zero pivot rows are skipped
+    // (at least the last stage runs, so that the product is written)
+    w.kt0 = DIR == DIR_BWD && w.fromx ? min(w.k / TC_BK, w.nkt - 1) : 0;
     w.row0 = m.row0;
     w.tb0 = m.tb0;
     w.idx = c.F.idx + m.tb0;
@@ -959,7 +962,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
       int it = from;
       while (it < it1 && !fitem<DIR, PASSES>(ctx, it, pos.w)) ++it;
       pos.it = it;
-      pos.kt = 0;
+      pos.kt = it < it1 ? pos.w.kt0 : 0;
     };
     auto advance = [&]() {
       if (pos.it >= it1) return;
@@ -1027,7 +1030,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
           continue;
         }
         const uint32_t own = tc % NMMA;
-        for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+        for (int kt = w.kt0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t ws = g % SW;
           if (g >= SW) wait(&w_empty[ws], ((g / SW) - 1) & 1);
           if (bail) break;
@@ -1052,7 +1055,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
     for (int it = it0; it < it1 && !bail; ++it) {
       if (!fitem<DIR, PASSES>(ctx, it, w)) continue;
       const uint32_t own = tc++ % NMMA;
-      for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+      for (int kt = w.kt0; kt < w.nkt && !bail; ++kt, ++g) {
         if ((int)(g % FG_CGROUPS) != cg) continue;
         const uint32_t sl = g % SR;
         wait(&raw_full[sl], (g / SR) & 1);
@@ -1110,7 +1113,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
         if (!fitem<DIR, PASSES>(ctx, it, w)) continue;
         const uint32_t a = tc % NACC;
         if (tc % NMMA != mine) {  // another thread's tile: skip its stages
-          g += w.nkt;
+          g += w.nkt - w.kt0;
           ++tc;
           continue;
         }
@@ -1120,7 +1123,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
         const uint32_t idc = CAT ? idesc_m128(2 * w.nf) : 0u;
         const uint32_t id1 = w.nf > 256 ? idesc_m128(w.nf - 256) : 0u;
         const uint64_t lo_w = w.wpart >> 4;
-        for (int kt = 0; kt < w.nkt && !bail; ++kt, ++g) {
+        for (int kt = w.kt0; kt < w.nkt && !bail; ++kt, ++g) {
           const uint32_t sl = g % SR, ws = g % SW;
           wait(&op_full[mine][sl], (opar >> sl) & 1u);
           wait(&w_full[mine][ws], (wpar_m >> ws) & 1u);
@@ -1133,7 +1136,7 @@ __global__ void __launch_bounds__(FG_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk) {
             const uint64_t ko = kk * (256 >> 4);
-            const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint32_t acc0 = (kt > w.kt0 || kk > 0) ? 1u : 0u;
             if (CAT) {
               mma_bf16_n(acc, aHi + ko, bHi + ko, idc, acc0);  // [hi*hi | hi*lo]
               mma_bf16_n(acc, aLo + ko, bHi + ko, id0, 1u);
