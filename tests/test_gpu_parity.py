@@ -34,8 +34,12 @@ TC3_MIXED = dict(TC3, fused_rows=24)
 # with tensor-core spike products and tensor-core LU block updates
 TC3_F16 = dict(TC3, ghat_prec=N.DDPS_FP16)
 BENCH = dict(TC3_F16, update_prec=N.DDPS_BF16X3)
+# the benched form in passes of 128 coupling columns: passes that leave fronts
+# inactive (cleared rows, zero-row reads, skipped stages in the backward) and
+# fronts without active children (no gather)
+BENCH_PASSES = dict(BENCH, rhs_chunk=128)
 FORMS = {"mixed": MIXED, "tc3": TC3, "tc1": TC1, "tc3_tiles": TC3_TILES, "tc3_mixed": TC3_MIXED,
-         "tc3_f16": TC3_F16, "bench": BENCH}
+         "tc3_f16": TC3_F16, "bench": BENCH, "bench_passes": BENCH_PASSES}
 # G^ applied without storing it: v + (D~^-1 R~ v)(c) by block solves
 IMPLICIT64 = dict(FP64, ghat_mode=N.DDPS_GHAT_IMPLICIT)
 IMPLICIT = dict(MIXED, ghat_mode=N.DDPS_GHAT_IMPLICIT)
@@ -120,7 +124,8 @@ def test_precond_apply_direct_mode(case):
 # 4.9e-4 of the entry, at most that of the block's largest entry)
 @pytest.mark.parametrize("form,bound", [("mixed", 2e-6), ("tc3", 1e-4), ("tc1", 3e-2),
                                         ("tc3_tiles", 1e-4), ("tc3_mixed", 1e-4),
-                                        ("tc3_f16", 6e-4), ("bench", 6e-4)])
+                                        ("tc3_f16", 6e-4), ("bench", 6e-4),
+                                        ("bench_passes", 6e-4)])
 def test_ghat_precision_forms(case, form, bound):
     """G^ formed with FP32 factors: SIMT FP32 products, bf16x3 and bf16 tensor-core
     products (fused front GEMMs, tile products, or both); each within its
@@ -151,12 +156,12 @@ def test_implicit_reduced_matvec(case, form, bound):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "tc3", "tc1", "implicit64",
-                                  "implicit", "tc3_f16", "bench"])
+                                  "implicit", "tc3_f16", "bench", "bench_passes"])
 def test_full_solve_parity(case, prec):
     name, P, drop, o = case
     opts = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "tc3": TC3, "tc1": TC1,
             "implicit64": IMPLICIT64, "implicit": IMPLICIT, "tc3_f16": TC3_F16,
-            "bench": BENCH}[prec]
+            "bench": BENCH, "bench_passes": BENCH_PASSES}[prec]
     S = make_solver(P, drop, tol_out=1e-12, tol_in=1e-6, maxit_in=200, **opts)
     x, info = S.solve(dev(P.f))
     assert info["status"] == "DDPS_OK", info
