@@ -107,8 +107,9 @@ struct ddps_handle {
   int32_t* any_host = nullptr;   // pinned copy
   int64_t *gq0 = nullptr, *gq1 = nullptr, *gcol_ptr = nullptr, *ghat_off = nullptr,
           *gld = nullptr, *block_ncols = nullptr;
-  // tiles of the G^ product: (block, first row) per 64 reduced rows
-  int32_t *mv_block = nullptr, *mv_row = nullptr;
+  // tiles of the G^ product: block, first row and rows (64, or 256 for
+  // blocks of fewer than 1024 coupling columns)
+  int32_t *mv_block = nullptr, *mv_row = nullptr, *mv_h = nullptr;
   int32_t mv_ntiles = 0;
   int64_t mv_max_cols = 0;
   void* ghat = nullptr;
@@ -941,7 +942,7 @@ void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal
   if (h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024) {
     // every block owning reduced rows has tiles (a block without coupling
     // columns gets w = v on its rows)
-    launch_ghat_matvec_tiled<TG, TI>((const TG*)h->ghat, h->mv_block, h->mv_row, h->mv_ntiles,
+    launch_ghat_matvec_tiled<TG, TI>((const TG*)h->ghat, h->mv_block, h->mv_row, h->mv_h, h->mv_ntiles,
                                      h->mv_max_cols, h->gq0, h->gq1, h->gcol_ptr, h->ghat_off,
                                      h->gld, h->gcols, v, w, sc, h->block_sys, s);
   } else {
@@ -1594,18 +1595,23 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
   h->ghat_off = dupload(h, A.ghat_off);
   h->gld = dupload(h, A.gld);
   {
-    std::vector<int32_t> tb, tr;
+    // tiles of 64 rows; blocks of fewer than 1024 coupling columns take tiles
+    // of 256 rows, so that a CTA's fixed cost (staging v) covers enough work
+    std::vector<int32_t> tb, tr, th;
     for (int32_t b = 0; b < A.p; ++b) {
       const int64_t nc = A.gcol_ptr[b + 1] - A.gcol_ptr[b];
       h->mv_max_cols = std::max(h->mv_max_cols, nc);
-      for (int64_t r = 0; r < A.gq1[b] - A.gq0[b]; r += 64) {
+      const int32_t hgt = nc >= 1024 ? 64 : 256;
+      for (int64_t r = 0; r < A.gq1[b] - A.gq0[b]; r += hgt) {
         tb.push_back(b);
         tr.push_back((int32_t)r);
+        th.push_back(hgt);
       }
     }
     h->mv_ntiles = (int32_t)tb.size();
     h->mv_block = dupload(h, tb);
     h->mv_row = dupload(h, tr);
+    h->mv_h = dupload(h, th);
   }
   h->gcols = dupload(h, A.gcols);
   h->block_ncols = dupload(h, ncols);

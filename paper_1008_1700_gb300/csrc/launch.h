@@ -269,7 +269,8 @@ void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq
 // non-null, blocks of systems whose inner solve has stopped are skipped.
 template <typename TG, typename TI>
 void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
-                              int32_t ntiles, int64_t max_cols, const int64_t* gq0,
+                              const int32_t* tile_h, int32_t ntiles, int64_t max_cols,
+                              const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
                               const KScal* sc, const int32_t* block_sys, cudaStream_t s);

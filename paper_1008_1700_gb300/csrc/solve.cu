@@ -892,7 +892,8 @@ __device__ __forceinline__ void load16<__half>(const __half* p, float* out) {
 template <typename TG, typename TI>
 __global__ void __launch_bounds__(256)
     k_ghat_matvec_tiled(const TG* __restrict__ ghat, const int32_t* __restrict__ tile_block,
-                        const int32_t* __restrict__ tile_row, const int64_t* __restrict__ gq0,
+                        const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_h,
+                        const int64_t* __restrict__ gq0,
                         const int64_t* __restrict__ gq1, const int64_t* __restrict__ gcol_ptr,
                         const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
                         const int32_t* __restrict__ gcols,
@@ -917,7 +918,8 @@ __global__ void __launch_bounds__(256)
   const int64_t q0 = gq0[b];
   // each warp streams four rows at once (the last group of a block repeats
   // its last valid row), two 16-byte loads per row and lane in flight
-  for (int rr = warp * 4; rr < 64; rr += 32) {
+  const int th = tile_h[blockIdx.x];
+  for (int rr = warp * 4; rr < th; rr += 32) {
     const int64_t ra = r0 + rr;
     if (ra >= nrows) break;
     const int nv = (int)min((int64_t)4, nrows - ra);
@@ -1174,7 +1176,8 @@ void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq
 
 template <typename TG, typename TI>
 void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
-                              int32_t ntiles, int64_t max_cols, const int64_t* gq0,
+                              const int32_t* tile_h, int32_t ntiles, int64_t max_cols,
+                              const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
                               const KScal* sc, const int32_t* block_sys, cudaStream_t s) {
@@ -1184,7 +1187,7 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
   if (sm > 48 * 1024)
     record_launch_error(cudaFuncSetAttribute(k_ghat_matvec_tiled<TG, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm));
-  k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, gq0, gq1,
+  k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, tile_h, gq0, gq1,
                                                        gcol_ptr, ghat_off, gld, gcols, v, w, sc,
                                                        block_sys);
 }
@@ -1220,7 +1223,8 @@ DDPS_INST_S(double)
 DDPS_INST_S(float)
 
 #define DDPS_INST_MV(TG, TI)                                                                     \
-  template void launch_ghat_matvec_tiled<TG, TI>(const TG*, const int32_t*, const int32_t*, int32_t, \
+  template void launch_ghat_matvec_tiled<TG, TI>(const TG*, const int32_t*, const int32_t*,      \
+                                                 const int32_t*, int32_t,                        \
                                                  int64_t, const int64_t*, const int64_t*,        \
                                                  const int64_t*, const int64_t*, const int64_t*, \
                                                  const int32_t*, const TI*, TI*, const KScal*,   \
