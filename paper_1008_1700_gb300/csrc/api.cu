@@ -1047,10 +1047,14 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
   // the host looks at a single "some system still iterating" flag every
   // kCheckEvery iterations.
   constexpr int kCheckEvery = 4;
+  const bool graphed = graphs_on(h) && h->opt.maxit_in > 0;
+  // rho and beta of the first iteration; every later iteration's come from
+  // the previous one's update of r (POST_CHECK_FULL_BETA)
+  seg_reduce_post<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, POST_BETA,
+                      sc, tol, graphed ? -h->opt.maxit_in : 1, s);
+  h->launches++;
   // one BiCGStab iteration; `it` < 0: the iteration number lives on the device
   auto iteration = [&](int it, cudaStream_t st) {
-    seg_reduce_post<TI>(S, 1, red(rh, r, 0, &sc[0].rho), nored(), nored(), h->partial, POST_BETA,
-                        sc, tol, it, st);
     update_p<TI>(S, sc, r, p, v, st);
     ghat_matvec<TG, TI>(h, p, v, st, sc);
     seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
@@ -1059,10 +1063,10 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
     ghat_matvec<TG, TI>(h, sv, t, st, sc);
     seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
                         h->partial, POST_OMEGA, sc, tol, it, st);
-    update_xr_norm<TI>(S, sc, z, p, sv, r, t, h->partial, tol, it, st);
-    h->launches += 6;  // the two G^ products count their own launches
+    update_xr_norm<TI>(S, sc, z, p, sv, r, t, rh, h->partial, tol, it, st);
+    h->launches += 5;  // the two G^ products count their own launches
   };
-  if (graphs_on(h) && h->opt.maxit_in > 0) {
+  if (graphed) {
     // kCheckEvery iterations and the "some system still iterating" flag, one
     // graph replayed until every system has stopped (the device counter
     // stops a system after maxit_in iterations)

@@ -45,7 +45,7 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
   }
   if (post == POST_NONE || lane != 0) return;
   KScal& k = sc[sgi];
-  if (post == POST_CHECK_FULL) k.half_done = 0;
+  if (post == POST_CHECK_FULL || post == POST_CHECK_FULL_BETA) k.half_done = 0;
   if (!k.active) return;
   const int cap = it < 0 ? -it : 0;
   if (it < 0) {
@@ -80,9 +80,16 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
       k.rho_old = k.rho;
       break;
     case POST_CHECK_FULL:
+    case POST_CHECK_FULL_BETA:
       k.iters = it;
-      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown || (cap && it >= cap))
+      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown || (cap && it >= cap)) {
         k.active = 0;
+      } else if (post == POST_CHECK_FULL_BETA) {
+        // the next iteration (number it + 1 >= 2) starts here: POST_BETA's step
+        if (cap) k.it += 1;
+        if (k.rho == 0.0) k.breakdown = 1;
+        k.beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
+      }
       break;
   }
 }
@@ -186,7 +193,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_update_xr_norm(SegView S, KScal* sc, T* __restrict__ x, const T* __restrict__ p,
                      const T* __restrict__ sv, T* __restrict__ r, const T* __restrict__ t,
-                     double* __restrict__ partial, double tol, int it) {
+                     const T* __restrict__ rh, double* __restrict__ partial, double tol, int it) {
   const int ch = blockIdx.x;
   const int sg = S.chunk_seg[ch];
   const bool act = sc[sg].active != 0, half = sc[sg].half_done != 0;
@@ -205,9 +212,12 @@ __global__ void __launch_bounds__(kThreads)
     }
     const double xv = (double)ri;
     acc[0] += xv * xv;
+    if (rh) acc[1] += (double)rh[i] * xv;
   }
-  const RedSpec spec[1] = {RedSpec{r, nullptr, 1, kScalStride, &sc[0].nrm}};
-  chunk_reduce_finalize(S, ch, 1, spec, acc, partial, POST_CHECK_FULL, sc, tol, it);
+  const RedSpec spec[2] = {RedSpec{r, nullptr, 1, kScalStride, &sc[0].nrm},
+                           RedSpec{rh, r, 0, kScalStride, &sc[0].rho}};
+  chunk_reduce_finalize(S, ch, rh ? 2 : 1, spec, acc, partial,
+                        rh ? POST_CHECK_FULL_BETA : POST_CHECK_FULL, sc, tol, it);
 }
 
 template <typename T>
@@ -379,9 +389,9 @@ void update_s_norm(const SegView& S, KScal* sc, const T* r, const T* v, T* out, 
 }
 template <typename T>
 void update_xr_norm(const SegView& S, KScal* sc, T* x, const T* p, const T* sv, T* r, const T* t,
-                    double* partial, double tol, int it, cudaStream_t s) {
+                    const T* rh, double* partial, double tol, int it, cudaStream_t s) {
   if (S.nchunks)
-    k_update_xr_norm<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, x, p, sv, r, t, partial, tol, it);
+    k_update_xr_norm<T><<<S.nchunks, kThreads, 0, s>>>(S, sc, x, p, sv, r, t, rh, partial, tol, it);
 }
 
 void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s) {
@@ -450,7 +460,7 @@ void sc_omega(int nseg, KScal* sc, cudaStream_t s) {
   template void update_s_norm<T>(const SegView&, KScal*, const T*, const T*, T*, double*, double, \
                                  int, cudaStream_t);                                             \
   template void update_xr_norm<T>(const SegView&, KScal*, T*, const T*, const T*, T*, const T*,  \
-                                  double*, double, int, cudaStream_t);
+                                  const T*, double*, double, int, cudaStream_t);
 DDPS_INST_K(double)
 DDPS_INST_K(float)
 template void convert<float, double>(int64_t, const double*, float*, cudaStream_t);

@@ -78,7 +78,9 @@ enum Post {
   POST_ALPHA = 2,       // alpha = rho / sigma
   POST_CHECK_HALF = 3,  // ||s|| <= tol ref: stop at the half step (x += alpha p pending)
   POST_OMEGA = 4,       // omega = (t, s) / (t, t); rho_old = rho
-  POST_CHECK_FULL = 5   // ||r|| <= tol ref, omega = 0 or breakdown: stop; clears half_done
+  POST_CHECK_FULL = 5,  // ||r|| <= tol ref, omega = 0 or breakdown: stop; clears half_done
+  POST_CHECK_FULL_BETA = 6  // the full-step check, then (still iterating) the next
+                            // iteration's beta from the rho reduced with ||r||
 };
 template <typename T>
 void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
@@ -96,8 +98,10 @@ template <typename T>
 void update_s_norm(const SegView& S, KScal* sc, const T* r, const T* v, T* out, double* partial,
                    double tol, int it, cudaStream_t s);
 template <typename T>
+// rh (may be null): also rho = (rh, r) for the next iteration, with
+// POST_CHECK_FULL_BETA instead of POST_CHECK_FULL.
 void update_xr_norm(const SegView& S, KScal* sc, T* x, const T* p, const T* sv, T* r, const T* t,
-                    double* partial, double tol, int it, cudaStream_t s);
+                    const T* rh, double* partial, double tol, int it, cudaStream_t s);
 // *flag = 1 if some segment is still active, else 0.
 void any_active(int nseg, const KScal* sc, int32_t* flag, cudaStream_t s);
 void sc_beta(int nseg, KScal* sc, int first, cudaStream_t s);
