@@ -111,6 +111,10 @@ struct ddps_handle {
   // blocks of fewer than 1024 coupling columns)
   int32_t *mv_block = nullptr, *mv_row = nullptr, *mv_h = nullptr;
   int32_t mv_ntiles = 0;
+  // reductions folded into the tiled product: tiles per system, partial sums
+  // (2 per tile) and per-system counters
+  int32_t *mv_sys_tptr = nullptr, *mv_done = nullptr;
+  double* mv_partial = nullptr;
   int64_t mv_max_cols = 0;
   void* ghat = nullptr;
   // spike panels: X (n x NR) and the fronts' working rows (sum of m x NR);
@@ -926,8 +930,17 @@ void block_solve(ddps_handle* h, const double* y, double* g, cudaStream_t s,
     block_solve_impl<float>(h, y, g, s, prof_cls);
 }
 
+// Whether the G^ product runs the tiled kernel (which can take the inner
+// iteration's reductions).
+template <typename TG>
+bool ghat_tiled(const ddps_handle* h) {
+  using AT = typename std::conditional<std::is_same<TG, double>::value, double, float>::type;
+  return h->opt.ghat_mode != DDPS_GHAT_IMPLICIT && h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024;
+}
+
 template <typename TG, typename TI>
-void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal* sc = nullptr) {
+void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal* sc = nullptr,
+                 const MvRed* red = nullptr) {
   Prof pr(h, DDPS_PROF_GHAT_MATVEC, s);
   if (h->opt.ghat_mode == DDPS_GHAT_IMPLICIT) {
     // G^ v = v + (D~^-1 R~ v)(c): every system is computed (a stopped
@@ -938,13 +951,12 @@ void ghat_matvec(ddps_handle* h, const TI* v, TI* w, cudaStream_t s, const KScal
     h->launches += 2;
     return;
   }
-  using AT = typename std::conditional<std::is_same<TG, double>::value, double, float>::type;
-  if (h->mv_max_cols * (int64_t)sizeof(AT) <= 200 * 1024) {
+  if (ghat_tiled<TG>(h)) {
     // every block owning reduced rows has tiles (a block without coupling
     // columns gets w = v on its rows)
     launch_ghat_matvec_tiled<TG, TI>((const TG*)h->ghat, h->mv_block, h->mv_row, h->mv_h, h->mv_ntiles,
                                      h->mv_max_cols, h->gq0, h->gq1, h->gcol_ptr, h->ghat_off,
-                                     h->gld, h->gcols, v, w, sc, h->block_sys, s);
+                                     h->gld, h->gcols, v, w, sc, h->block_sys, red, s);
   } else {
     launch_ghat_matvec<TG, TI>((const TG*)h->ghat, h->qblock, h->gq0, h->gcol_ptr, h->ghat_off,
                                h->gld, h->gcols, (int64_t)h->A.c.size(), v, w, s);
@@ -1054,17 +1066,49 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
                       sc, tol, graphed ? -h->opt.maxit_in : 1, s);
   h->launches++;
   // one BiCGStab iteration; `it` < 0: the iteration number lives on the device
+  // with the tiled G^ product, sigma and (t, s), (t, t) are reduced by the
+  // products themselves, which also take the alpha and omega steps
+  const bool fold = ghat_tiled<TG>(h);
   auto iteration = [&](int it, cudaStream_t st) {
     update_p<TI>(S, sc, r, p, v, st);
-    ghat_matvec<TG, TI>(h, p, v, st, sc);
-    seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
-                        POST_ALPHA, sc, tol, it, st);
+    if (fold) {
+      MvRed ra;
+      ra.nred = 1;
+      ra.x = rh;
+      ra.partial = h->mv_partial;
+      ra.done = h->mv_done;
+      ra.sys_tptr = h->mv_sys_tptr;
+      ra.sc = sc;
+      ra.post = POST_ALPHA;
+      ra.tol = tol;
+      ra.it = it;
+      ghat_matvec<TG, TI>(h, p, v, st, sc, &ra);
+    } else {
+      ghat_matvec<TG, TI>(h, p, v, st, sc);
+      seg_reduce_post<TI>(S, 1, red(rh, v, 0, &sc[0].sigma), nored(), nored(), h->partial,
+                          POST_ALPHA, sc, tol, it, st);
+      h->launches++;
+    }
     update_s_norm<TI>(S, sc, r, v, sv, h->partial, tol, it, st);
-    ghat_matvec<TG, TI>(h, sv, t, st, sc);
-    seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
-                        h->partial, POST_OMEGA, sc, tol, it, st);
+    if (fold) {
+      MvRed ro;
+      ro.nred = 2;
+      ro.partial = h->mv_partial;
+      ro.done = h->mv_done;
+      ro.sys_tptr = h->mv_sys_tptr;
+      ro.sc = sc;
+      ro.post = POST_OMEGA;
+      ro.tol = tol;
+      ro.it = it;
+      ghat_matvec<TG, TI>(h, sv, t, st, sc, &ro);
+    } else {
+      ghat_matvec<TG, TI>(h, sv, t, st, sc);
+      seg_reduce_post<TI>(S, 2, red(t, sv, 0, &sc[0].ts), red(t, t, 0, &sc[0].tt), nored(),
+                          h->partial, POST_OMEGA, sc, tol, it, st);
+      h->launches++;
+    }
     update_xr_norm<TI>(S, sc, z, p, sv, r, t, rh, h->partial, tol, it, st);
-    h->launches += 5;  // the two G^ products count their own launches
+    h->launches += 3;  // the two G^ products count their own launches
   };
   if (graphed) {
     // kCheckEvery iterations and the "some system still iterating" flag, one
@@ -1616,6 +1660,15 @@ void build_device(ddps_handle* h, const int32_t* rowptr, const int32_t* colind) 
     h->mv_block = dupload(h, tb);
     h->mv_row = dupload(h, tr);
     h->mv_h = dupload(h, th);
+    // tiles are ordered by block and blocks by system: a system's tiles are
+    // consecutive
+    std::vector<int32_t> stp(A.nsys + 1, 0);
+    for (int32_t b : tb) ++stp[A.block_sys[b] + 1];
+    for (int32_t q = 0; q < A.nsys; ++q) stp[q + 1] += stp[q];
+    h->mv_sys_tptr = dupload(h, stp);
+    h->mv_done = dalloc<int32_t>(h, A.nsys);
+    CK(cudaMemset(h->mv_done, 0, (size_t)std::max<int32_t>(A.nsys, 1) * sizeof(int32_t)));
+    h->mv_partial = dalloc<double>(h, 2 * (int64_t)std::max<int32_t>(h->mv_ntiles, 1));
   }
   h->gcols = dupload(h, A.gcols);
   h->block_ncols = dupload(h, ncols);

@@ -44,54 +44,7 @@ __device__ void seg_finalize(const SegView& S, int sgi, int lane, int nred, cons
     if (lane == 0) spec[q].out[(int64_t)sgi * spec[q].stride] = v;
   }
   if (post == POST_NONE || lane != 0) return;
-  KScal& k = sc[sgi];
-  if (post == POST_CHECK_FULL || post == POST_CHECK_FULL_BETA) k.half_done = 0;
-  if (!k.active) return;
-  const int cap = it < 0 ? -it : 0;
-  if (it < 0) {
-    if (post == POST_BETA) k.it += 1;
-    it = k.it;
-  }
-  switch (post) {
-    case POST_BETA:
-      if (k.rho == 0.0) k.breakdown = 1;
-      k.beta = it == 1 ? 0.0 : (k.rho / k.rho_old) * (k.alpha / k.omega);
-      break;
-    case POST_ALPHA:
-      if (k.sigma == 0.0) {
-        k.breakdown = 1;
-        k.alpha = 0.0;
-      } else {
-        k.alpha = k.rho / k.sigma;
-      }
-      break;
-    case POST_CHECK_HALF:
-      if (k.nrm <= tol * k.ref) {
-        k.half_done = 1;
-        k.active = 0;
-        k.iters = it - 0.5;
-      } else if (k.breakdown) {
-        k.active = 0;
-        k.iters = it;
-      }
-      break;
-    case POST_OMEGA:
-      k.omega = k.tt != 0.0 ? k.ts / k.tt : 0.0;
-      k.rho_old = k.rho;
-      break;
-    case POST_CHECK_FULL:
-    case POST_CHECK_FULL_BETA:
-      k.iters = it;
-      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown || (cap && it >= cap)) {
-        k.active = 0;
-      } else if (post == POST_CHECK_FULL_BETA) {
-        // the next iteration (number it + 1 >= 2) starts here: POST_BETA's step
-        if (cap) k.it += 1;
-        if (k.rho == 0.0) k.breakdown = 1;
-        k.beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
-      }
-      break;
-  }
+  post_step(sc[sgi], post, tol, it);
 }
 
 // The end of a chunk reduction, shared by the reduction kernel and the

@@ -82,6 +82,75 @@ enum Post {
   POST_CHECK_FULL_BETA = 6  // the full-step check, then (still iterating) the next
                             // iteration's beta from the rho reduced with ||r||
 };
+#ifdef __CUDACC__
+// The BiCGStab scalar step `post` of one segment, after its reductions.
+__device__ __forceinline__ void post_step(KScal& k, int post, double tol, int it) {
+  if (post == POST_CHECK_FULL || post == POST_CHECK_FULL_BETA) k.half_done = 0;
+  if (!k.active) return;
+  const int cap = it < 0 ? -it : 0;
+  if (it < 0) {
+    if (post == POST_BETA) k.it += 1;
+    it = k.it;
+  }
+  switch (post) {
+    case POST_BETA:
+      if (k.rho == 0.0) k.breakdown = 1;
+      k.beta = it == 1 ? 0.0 : (k.rho / k.rho_old) * (k.alpha / k.omega);
+      break;
+    case POST_ALPHA:
+      if (k.sigma == 0.0) {
+        k.breakdown = 1;
+        k.alpha = 0.0;
+      } else {
+        k.alpha = k.rho / k.sigma;
+      }
+      break;
+    case POST_CHECK_HALF:
+      if (k.nrm <= tol * k.ref) {
+        k.half_done = 1;
+        k.active = 0;
+        k.iters = it - 0.5;
+      } else if (k.breakdown) {
+        k.active = 0;
+        k.iters = it;
+      }
+      break;
+    case POST_OMEGA:
+      k.omega = k.tt != 0.0 ? k.ts / k.tt : 0.0;
+      k.rho_old = k.rho;
+      break;
+    case POST_CHECK_FULL:
+    case POST_CHECK_FULL_BETA:
+      k.iters = it;
+      if (k.nrm <= tol * k.ref || k.omega == 0.0 || k.breakdown || (cap && it >= cap)) {
+        k.active = 0;
+      } else if (post == POST_CHECK_FULL_BETA) {
+        // the next iteration (number it + 1 >= 2) starts here: POST_BETA's step
+        if (cap) k.it += 1;
+        if (k.rho == 0.0) k.breakdown = 1;
+        k.beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
+      }
+      break;
+  }
+}
+#endif
+
+// Reductions folded into the tiled G^ product (w = G^ v), per system: nred 1,
+// sigma = (x, w); nred 2, ts = (w, v) and tt = (w, w); then the scalar step
+// `post`.  Each tile writes its partial sums, the last tile of a system (in
+// done[]) adds its tiles' partials in a fixed order and takes the step.
+struct MvRed {
+  int nred = 0;
+  const void* x = nullptr;            // nred 1: the first vector (the product's type)
+  double* partial = nullptr;          // 2 x tiles
+  int32_t* done = nullptr;            // per system, zero between products
+  const int32_t* sys_tptr = nullptr;  // tiles of system s: [sys_tptr[s], sys_tptr[s + 1])
+  KScal* sc = nullptr;
+  int post = 0;
+  double tol = 0.0;
+  int it = 0;
+};
+
 template <typename T>
 void seg_reduce_post(const SegView& S, int nred, RedSpec r0, RedSpec r1, RedSpec r2,
                      double* partial, int post, KScal* sc, double tol, int it, cudaStream_t s);

@@ -11,6 +11,7 @@
 namespace ddps {
 
 struct KScal;
+struct MvRed;
 
 // SM count of the current device, cached per device ordinal (a process may
 // switch devices, and devices may differ).
@@ -266,14 +267,16 @@ void launch_ghat_matvec(const TG* ghat, const int32_t* qblock, const int64_t* gq
                         const int32_t* gcols, int64_t m, const TI* v, TI* w, cudaStream_t s);
 // Tiled G^ product: one CTA per (block, 64 reduced rows); needs max_cols
 // entries of shared memory for the block's gathered vector.  With sc
-// non-null, blocks of systems whose inner solve has stopped are skipped.
+// non-null, blocks of systems whose inner solve has stopped are skipped; with
+// red non-null, the product also takes red's reductions and scalar step.
 template <typename TG, typename TI>
 void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const int32_t* tile_row,
                               const int32_t* tile_h, int32_t ntiles, int64_t max_cols,
                               const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
-                              const KScal* sc, const int32_t* block_sys, cudaStream_t s);
+                              const KScal* sc, const int32_t* block_sys, const MvRed* red,
+                              cudaStream_t s);
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s);
 void launch_gather_rt_values(const double* values, const int64_t* rt_src, int64_t nrt,
                              double* rt_val, cudaStream_t s);

@@ -890,7 +890,7 @@ __device__ __forceinline__ void load16<__half>(const __half* p, float* out) {
 }
 
 template <typename TG, typename TI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_ghat_matvec_tiled(const TG* __restrict__ ghat, const int32_t* __restrict__ tile_block,
                         const int32_t* __restrict__ tile_row, const int32_t* __restrict__ tile_h,
                         const int64_t* __restrict__ gq0,
@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(256)
                         const int64_t* __restrict__ ghat_off, const int64_t* __restrict__ gld,
                         const int32_t* __restrict__ gcols,
                         const TI* __restrict__ v, TI* __restrict__ w, const KScal* __restrict__ sc,
-                        const int32_t* __restrict__ block_sys) {
+                        const int32_t* __restrict__ block_sys, MvRed R) {
   using AT = typename Acc<TG>::type;
   constexpr int VN = Vec16<TG>::n;
   extern __shared__ unsigned char smem_raw[];
@@ -960,6 +960,74 @@ __global__ void __launch_bounds__(256)
       for (int o = 16; o > 0; o >>= 1) s4[u] += __shfl_xor_sync(0xffffffffu, s4[u], o);
     if (lane == 0)
       for (int u = 0; u < nv; ++u) w[q0 + ra + u] = (TI)((AT)v[q0 + ra + u] + s4[u]);
+  }
+  if (R.nred) {
+    // after the product: the tile's partial sums (its rows strided over the
+    // threads, warps in order), then the system's, by the last of its tiles
+    // to finish (tiles in order), and its scalar step
+    __shared__ double part[2][8];
+    __shared__ int last;
+    __syncthreads();  // the tile's entries of w are written
+    double red0 = 0.0, red1 = 0.0;
+    const int nrt = (int)min((int64_t)th, nrows - r0);
+    for (int i = threadIdx.x; i < nrt; i += blockDim.x) {
+      const int64_t q = q0 + r0 + i;
+      const double wv = (double)w[q];
+      if (R.nred == 1) {
+        red0 += (double)reinterpret_cast<const TI*>(R.x)[q] * wv;
+      } else {
+        red0 += wv * (double)v[q];
+        red1 += wv * wv;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      red0 += __shfl_xor_sync(0xffffffffu, red0, o);
+      red1 += __shfl_xor_sync(0xffffffffu, red1, o);
+    }
+    if (lane == 0) {
+      part[0][warp] = red0;
+      part[1][warp] = red1;
+    }
+    __syncthreads();
+    const int32_t sys = block_sys[b];
+    const int32_t t0 = R.sys_tptr[sys], t1 = R.sys_tptr[sys + 1];
+    if (threadIdx.x == 0) {
+      double a0 = part[0][0], a1 = part[1][0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+        a0 += part[0][q];
+        a1 += part[1][q];
+      }
+      R.partial[blockIdx.x] = a0;
+      R.partial[gridDim.x + blockIdx.x] = a1;
+      __threadfence();
+      last = atomicAdd(&R.done[sys], 1) == t1 - t0 - 1;
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+      __threadfence();
+      double s0 = 0.0, s1 = 0.0;
+      for (int t = t0 + lane; t < t1; t += 32) {
+        s0 += __ldcg(R.partial + t);
+        s1 += __ldcg(R.partial + gridDim.x + t);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      if (lane == 0) {
+        KScal& k = R.sc[sys];
+        if (R.nred == 1) {
+          k.sigma = s0;
+        } else {
+          k.ts = s0;
+          k.tt = s1;
+        }
+        post_step(k, R.post, R.tol, R.it);
+        R.done[sys] = 0;
+      }
+    }
   }
 }
 
@@ -1180,7 +1248,8 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
                               const int64_t* gq0,
                               const int64_t* gq1, const int64_t* gcol_ptr, const int64_t* ghat_off,
                               const int64_t* gld, const int32_t* gcols, const TI* v, TI* w,
-                              const KScal* sc, const int32_t* block_sys, cudaStream_t s) {
+                              const KScal* sc, const int32_t* block_sys, const MvRed* red,
+                              cudaStream_t s) {
   if (ntiles <= 0) return;
   using AT = typename Acc<TG>::type;
   const size_t sm = (size_t)std::max<int64_t>(max_cols, 1) * sizeof(AT);
@@ -1189,7 +1258,7 @@ void launch_ghat_matvec_tiled(const TG* ghat, const int32_t* tile_block, const i
                          (int)sm));
   k_ghat_matvec_tiled<TG, TI><<<ntiles, 256, sm, s>>>(ghat, tile_block, tile_row, tile_h, gq0, gq1,
                                                        gcol_ptr, ghat_off, gld, gcols, v, w, sc,
-                                                       block_sys);
+                                                       block_sys, red ? *red : MvRed{});
 }
 
 void launch_gather(const double* src, const int64_t* idx, int64_t m, double* dst, cudaStream_t s) {
@@ -1228,7 +1297,7 @@ DDPS_INST_S(float)
                                                  int64_t, const int64_t*, const int64_t*,        \
                                                  const int64_t*, const int64_t*, const int64_t*, \
                                                  const int32_t*, const TI*, TI*, const KScal*,   \
-                                                 const int32_t*, cudaStream_t);
+                                                 const int32_t*, const MvRed*, cudaStream_t);
 DDPS_INST_MV(double, double)
 DDPS_INST_MV(float, double)
 DDPS_INST_MV(float, float)
