@@ -16,15 +16,79 @@
 //    couple to.  Fronts are grouped by tree depth so that the device can
 //    process one depth of all blocks of all systems per launch.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <exception>
+#include <mutex>
 #include <numeric>
 #include <sstream>
+#include <system_error>
+#include <thread>
 
 #include "ddps_internal.h"
 
 namespace ddps {
 namespace {
+
+// An error found inside the analysis (also inside a worker thread); its
+// message is the analysis' result.
+struct AnalyzeError {
+  std::string msg;
+};
+
+// Host threads of the analysis: DDPS_ANALYZE_THREADS if set (>= 1), else the
+// hardware threads, at most 64.
+int analysis_threads() {
+  if (const char* s = std::getenv("DDPS_ANALYZE_THREADS")) {
+    const int v = std::atoi(s);
+    if (v >= 1) return std::min(v, 256);
+  }
+  const unsigned hw = std::thread::hardware_concurrency();
+  return hw == 0 ? 1 : (int)std::min(hw, 64u);
+}
+
+// Runs body(i) for every i in [0, count), items handed out in order from a
+// counter to the calling thread and up to analysis_threads() - 1 others (if
+// a thread cannot be started, the ones running take its share).  Every item
+// writes only its own outputs, so the result does not depend on the number
+// of threads.  The exception of the lowest failing item is rethrown here.
+template <class Body>
+void parallel_items(int64_t count, const Body& body) {
+  if (count <= 0) return;
+  const int nt = (int)std::min<int64_t>(analysis_threads(), count);
+  std::atomic<int64_t> next{0};
+  std::mutex mu;
+  int64_t err_item = -1;
+  std::exception_ptr err;
+  auto work = [&]() {
+    for (;;) {
+      const int64_t i = next.fetch_add(1);
+      if (i >= count) return;
+      try {
+        body(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (err_item < 0 || i < err_item) {
+          err_item = i;
+          err = std::current_exception();
+        }
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (const std::system_error&) {
+      break;
+    }
+  }
+  work();
+  for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
 
 struct Graph {
   int32_t nv = 0;
@@ -230,10 +294,10 @@ class NestedDissection {
 
 }  // namespace
 
-std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
-                    int32_t p, const int64_t* block_ptr, int32_t nsys,
-                    const int32_t* sys_block_ptr, const double* values,
-                    const ddps_options& opt, Analysis& A) {
+static std::string analyze_impl(int64_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colind, int32_t p, const int64_t* block_ptr,
+                                int32_t nsys, const int32_t* sys_block_ptr, const double* values,
+                                const ddps_options& opt, Analysis& A) {
   std::ostringstream err;
   if (n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && !colind) || p <= 0 || !block_ptr)
     return "ddps_analyze: invalid sizes or null pattern pointers";
@@ -283,7 +347,9 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     for (int64_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i) row_block[i] = b;
   std::vector<uint8_t> keep_r(nnz, 0);
   std::vector<uint8_t> is_d(nnz, 0);
-  for (int32_t b = 0; b < p; ++b) {
+  // blocks in parallel: each one sets the flags of its own rows' entries
+  parallel_items(p, [&](int64_t bi) {
+    const int32_t b = (int32_t)bi;
     int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
     int32_t s = A.block_sys[b];
     int64_t s0 = A.sys_row_ptr[s], s1 = A.sys_row_ptr[s + 1];
@@ -296,8 +362,9 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
           continue;
         }
         if (j < s0 || j >= s1) {
-          err << "ddps_analyze: entry (" << i << ", " << j << ") couples two systems";
-          return err.str();
+          std::ostringstream why;
+          why << "ddps_analyze: entry (" << i << ", " << j << ") couples two systems";
+          throw AnalyzeError{why.str()};
         }
         if (opt.drop_mode == DDPS_DROP_ABS)
           keep_r[e] = std::fabs(values[e]) >= opt.drop_tol;
@@ -324,7 +391,7 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
           keep_r[e] = !(it->second <= opt.drop_tol * mx);
         }
     }
-  }
+  });
 
   // ---- Fig. 2 step 5: c ------------------------------------------------------
   std::vector<uint8_t> inc(n, 0);
@@ -345,8 +412,6 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
   const int leaf = opt.leaf_size > 0 ? opt.leaf_size : 64;
   A.perm.assign(n, 0);
   A.iperm.assign(n, 0);
-  std::vector<int32_t> owner(n, -1);  // new index -> front id
-  std::vector<int32_t> pos_scratch(n, -1);
   struct FrontTmp {
     int32_t k;
     int64_t row0;
@@ -362,14 +427,22 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     // ILU(0) keeps every block in its own row order: no dissection, no fronts
     for (int64_t i = 0; i < n; ++i) A.perm[i] = A.iperm[i] = (int32_t)i;
   }
-  for (int32_t b = 0; b < (A.ilu ? 0 : p); ++b) {
-    int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
+  // The blocks are ordered and analysed independently (Sec. 3: each diagonal
+  // block is factored on its own), in parallel: a block writes only its own
+  // rows of perm / iperm and its own list of fronts, numbered from 0 in
+  // postorder; the lists are then appended in block order.
+  const int32_t nblk = A.ilu ? 0 : p;
+  std::vector<std::vector<FrontTmp>> BF(nblk);
+  std::vector<std::vector<int32_t>> BR(nblk);
+  parallel_items(nblk, [&](int64_t bi) {
+    const int32_t b = (int32_t)bi;
+    const int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
+    std::vector<FrontTmp>& Fb = BF[b];
     Graph g = block_graph(rowptr, colind, r0, r1);
     NestedDissection nd(g, leaf);
     nd.run();
     // postorder numbering: children first, then the node's pivots
     int32_t next = 0;
-    const int32_t base = (int32_t)F.size();
     std::vector<int32_t> node2front(nd.nodes.size(), -1);
     std::vector<std::pair<int32_t, int32_t>> stack;
     for (int32_t root : nd.roots) {
@@ -393,42 +466,55 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
         ft.row0 = r0 + nd_.p0;
         ft.block = b;
         for (int32_t c : nd_.children) ft.ch.push_back(node2front[c]);
-        node2front[top.first] = (int32_t)F.size();
-        F.push_back(std::move(ft));
+        node2front[top.first] = (int32_t)Fb.size();
+        Fb.push_back(std::move(ft));
         stack.pop_back();
       }
     }
-    if (next != g.nv) return "ddps_analyze: internal error in the dissection numbering";
-    for (int32_t root : nd.roots) roots.push_back(node2front[root]);
-    // symbolic factorisation, bottom-up (fronts of this block are in postorder)
-    for (int32_t f = base; f < (int32_t)F.size(); ++f) {
-      FrontTmp& ft = F[f];
+    if (next != g.nv) throw AnalyzeError{"ddps_analyze: internal error in the dissection numbering"};
+    for (int32_t root : nd.roots) BR[b].push_back(node2front[root]);
+    // symbolic factorisation, bottom-up (the fronts are in postorder); mark[u
+    // - r0] holds the last front that listed row u
+    std::vector<int32_t> mark(g.nv, -1);
+    for (int32_t f = 0; f < (int32_t)Fb.size(); ++f) {
+      FrontTmp& ft = Fb[f];
       const int64_t end = ft.row0 + ft.k;
-      for (int64_t q = ft.row0; q < end; ++q) owner[q] = f;
       std::vector<int32_t> upd;
       for (int64_t q = ft.row0; q < end; ++q) {
         int64_t vloc = A.perm[q] - r0;
         for (int64_t e = g.xadj[vloc]; e < g.xadj[vloc + 1]; ++e) {
           int32_t u = A.iperm[r0 + g.adj[e]];
-          if (u >= end && pos_scratch[u] != f) {
-            pos_scratch[u] = f;
+          if (u >= end && mark[u - r0] != f) {
+            mark[u - r0] = f;
             upd.push_back(u);
           }
         }
       }
       for (int32_t c : ft.ch) {
-        F[c].parent = f;
-        for (int32_t u : F[c].upd)
-          if (u >= end && pos_scratch[u] != f) {
-            pos_scratch[u] = f;
+        Fb[c].parent = f;
+        for (int32_t u : Fb[c].upd)
+          if (u >= end && mark[u - r0] != f) {
+            mark[u - r0] = f;
             upd.push_back(u);
           }
       }
       std::sort(upd.begin(), upd.end());
       ft.upd = std::move(upd);
     }
+  });
+  for (int32_t b = 0; b < nblk; ++b) {
+    const int32_t base = (int32_t)F.size();
+    for (FrontTmp& ft : BF[b]) {
+      for (int32_t& c : ft.ch) c += base;
+      if (ft.parent >= 0) ft.parent += base;
+      F.push_back(std::move(ft));
+    }
+    for (int32_t r : BR[b]) roots.push_back(r + base);
+    std::vector<FrontTmp>().swap(BF[b]);
   }
-  for (auto& v : pos_scratch) v = -1;
+  std::vector<int32_t> owner(n, -1);  // new index -> front id
+  for (int32_t f = 0; f < (int32_t)F.size(); ++f)
+    for (int64_t q = F[f].row0; q < F[f].row0 + F[f].k; ++q) owner[q] = (int32_t)f;
 
   // depths, levels, storage offsets
   const int32_t nf = (int32_t)F.size();
@@ -486,25 +572,38 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     for (size_t i = 0; i < F[f].upd.size(); ++i) A.idx[o + F[f].k + i] = F[f].upd[i];
   }
   // relative positions of each child's update rows inside its parent's front
+  // (offsets first, then the fronts in parallel chunks)
+  int64_t nrel = 0;
   for (int32_t f = 0; f < nf; ++f) {
     if (F[f].parent < 0) {
       if (!F[f].upd.empty()) return "ddps_analyze: internal error (root front with update rows)";
       continue;
     }
-    const FrontTmp& pf = F[F[f].parent];
-    A.f_rel[f] = (int64_t)A.rel.size();
-    for (int32_t u : F[f].upd) {
-      int64_t pos;
-      if (u >= pf.row0 && u < pf.row0 + pf.k) {
-        pos = u - pf.row0;
-      } else {
-        auto it = std::lower_bound(pf.upd.begin(), pf.upd.end(), u);
-        if (it == pf.upd.end() || *it != u) return "ddps_analyze: internal error (update row not in parent)";
-        pos = pf.k + (it - pf.upd.begin());
-      }
-      A.rel.push_back((int32_t)pos);
-    }
+    A.f_rel[f] = nrel;
+    nrel += (int64_t)F[f].upd.size();
   }
+  A.rel.resize(nrel);
+  constexpr int32_t kFrontChunk = 256;
+  parallel_items((nf + kFrontChunk - 1) / kFrontChunk, [&](int64_t it) {
+    const int32_t f1 = (int32_t)std::min<int64_t>(nf, (it + 1) * kFrontChunk);
+    for (int32_t f = (int32_t)it * kFrontChunk; f < f1; ++f) {
+      if (F[f].parent < 0) continue;
+      const FrontTmp& pf = F[F[f].parent];
+      int32_t* out = A.rel.data() + A.f_rel[f];
+      for (int32_t u : F[f].upd) {
+        int64_t pos;
+        if (u >= pf.row0 && u < pf.row0 + pf.k) {
+          pos = u - pf.row0;
+        } else {
+          auto it2 = std::lower_bound(pf.upd.begin(), pf.upd.end(), u);
+          if (it2 == pf.upd.end() || *it2 != u)
+            throw AnalyzeError{"ddps_analyze: internal error (update row not in parent)"};
+          pos = pf.k + (it2 - pf.upd.begin());
+        }
+        *out++ = (int32_t)pos;
+      }
+    }
+  });
   // level lists and the extend-add schedule
   A.level_ptr.assign(A.nlevels + 1, 0);
   for (int32_t f = 0; f < nf; ++f) A.level_ptr[A.f_depth[f] + 1]++;
@@ -585,21 +684,25 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
       }
     A.factor_lu_entries = (int64_t)A.il_col.size();
   }
-  for (int64_t i = 0; i < (A.ilu ? 0 : n); ++i) {
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      if (!is_d[e]) continue;
-      int32_t a = A.iperm[i], bn = A.iperm[colind[e]];
-      int32_t piv = std::min(a, bn);
-      int32_t f = owner[piv];
-      const FrontTmp& ft = F[f];
-      auto posf = [&](int32_t u) -> int64_t {
-        if (u < ft.row0 + ft.k) return u - ft.row0;
-        auto it = std::lower_bound(ft.upd.begin(), ft.upd.end(), u);
-        return ft.k + (it - ft.upd.begin());
-      };
-      A.amap[e] = A.f_arena[f] + posf(a) + posf(bn) * (int64_t)A.f_m[f];
+  constexpr int64_t kRowChunk = 4096;
+  parallel_items(A.ilu ? 0 : (n + kRowChunk - 1) / kRowChunk, [&](int64_t it) {
+    const int64_t i1 = std::min(n, (it + 1) * kRowChunk);
+    for (int64_t i = it * kRowChunk; i < i1; ++i) {
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        if (!is_d[e]) continue;
+        int32_t a = A.iperm[i], bn = A.iperm[colind[e]];
+        int32_t piv = std::min(a, bn);
+        int32_t f = owner[piv];
+        const FrontTmp& ft = F[f];
+        auto posf = [&](int32_t u) -> int64_t {
+          if (u < ft.row0 + ft.k) return u - ft.row0;
+          auto it2 = std::lower_bound(ft.upd.begin(), ft.upd.end(), u);
+          return ft.k + (it2 - ft.upd.begin());
+        };
+        A.amap[e] = A.f_arena[f] + posf(a) + posf(bn) * (int64_t)A.f_m[f];
+      }
     }
-  }
+  });
 
   // ---- R~ as CSR with reduced column indices; spike right-hand sides --------
   A.rt_rowptr.assign(n + 1, 0);
@@ -609,14 +712,22 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
   A.ghat_off.assign(p + 1, 0);
   A.gld.assign(p, 0);
   std::vector<std::vector<int32_t>> bcols(p);
-  for (int32_t b = 0; b < p; ++b) {
-    int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
+  // stored L and U entries of each block's fronts, summed in front order
+  std::vector<double> blk_lu(p, 0.0);
+  for (int32_t f = 0; f < nf; ++f)
+    blk_lu[A.f_block[f]] += (double)A.f_k[f] * (2.0 * A.f_m[f] - A.f_k[f]);
+  // coupling columns of each block (sorted reduced indices), blocks in parallel
+  parallel_items(p, [&](int64_t b) {
     std::vector<int32_t>& cols = bcols[b];
-    for (int64_t i = r0; i < r1; ++i)
+    for (int64_t i = block_ptr[b]; i < block_ptr[b + 1]; ++i)
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
         if (keep_r[e]) cols.push_back(qpos[colind[e]]);
     std::sort(cols.begin(), cols.end());
     cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+  });
+  for (int32_t b = 0; b < p; ++b) {
+    int64_t r0 = block_ptr[b], r1 = block_ptr[b + 1];
+    const std::vector<int32_t>& cols = bcols[b];
     A.gq0[b] = std::lower_bound(A.c.begin(), A.c.end(), r0) - A.c.begin();
     A.gq1[b] = std::lower_bound(A.c.begin(), A.c.end(), r1) - A.c.begin();
     A.gcol_ptr[b + 1] = A.gcol_ptr[b] + (int64_t)cols.size();
@@ -627,26 +738,36 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
     A.ghat_off[b + 1] = A.ghat_off[b] + (A.gq1[b] - A.gq0[b]) * A.gld[b];
     A.ghat_entries += (A.gq1[b] - A.gq0[b]) * (int64_t)cols.size();
     A.max_rhs = std::max<int64_t>(A.max_rhs, (int64_t)cols.size());
-    double blk_lu = 0;
-    for (int32_t f = 0; f < nf; ++f)
-      if (A.f_block[f] == b) blk_lu += (double)A.f_k[f] * (2.0 * A.f_m[f] - A.f_k[f]);
-    if (A.ilu) blk_lu = (double)(A.il_rp[r1] - A.il_rp[r0]) / 2.0;
-    A.spike_flops += 4.0 * blk_lu * (double)cols.size();
+    const double lu = A.ilu ? (double)(A.il_rp[r1] - A.il_rp[r0]) / 2.0 : blk_lu[b];
+    A.spike_flops += 4.0 * lu * (double)cols.size();
   }
+  // row pointers first, then the rows in parallel chunks
   for (int64_t i = 0; i < n; ++i) {
-    int32_t b = row_block[i];
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      if (!keep_r[e]) continue;
-      int32_t q = qpos[colind[e]];
-      const std::vector<int32_t>& cols = bcols[b];
-      int32_t j = (int32_t)(std::lower_bound(cols.begin(), cols.end(), q) - cols.begin());
-      A.rt_col.push_back(q);
-      A.rt_src.push_back(e);
-      A.rt_rhscol.push_back(j);
-      A.rt_rownew.push_back(A.iperm[i]);
-    }
-    A.rt_rowptr[i + 1] = (int32_t)A.rt_col.size();
+    int32_t kept = 0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) kept += keep_r[e];
+    A.rt_rowptr[i + 1] = A.rt_rowptr[i] + kept;
   }
+  const int64_t nrt = A.rt_rowptr[n];
+  A.rt_col.resize(nrt);
+  A.rt_src.resize(nrt);
+  A.rt_rhscol.resize(nrt);
+  A.rt_rownew.resize(nrt);
+  parallel_items((n + kRowChunk - 1) / kRowChunk, [&](int64_t it) {
+    const int64_t i1 = std::min(n, (it + 1) * kRowChunk);
+    for (int64_t i = it * kRowChunk; i < i1; ++i) {
+      const std::vector<int32_t>& cols = bcols[row_block[i]];
+      int64_t o = A.rt_rowptr[i];
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        if (!keep_r[e]) continue;
+        int32_t q = qpos[colind[e]];
+        A.rt_col[o] = q;
+        A.rt_src[o] = e;
+        A.rt_rhscol[o] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), q) - cols.begin());
+        A.rt_rownew[o] = A.iperm[i];
+        ++o;
+      }
+    }
+  });
   A.c_rownew.resize(m);
   for (int64_t q = 0; q < m; ++q) A.c_rownew[q] = A.iperm[A.c[q]];
 
@@ -660,6 +781,21 @@ std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t
             A.factor_flops, (long long)A.ghat_entries, (long long)A.max_rhs, A.spike_flops);
   }
   return "";
+}
+
+std::string analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                    int32_t p, const int64_t* block_ptr, int32_t nsys,
+                    const int32_t* sys_block_ptr, const double* values,
+                    const ddps_options& opt, Analysis& A) {
+  try {
+    return analyze_impl(n, nnz, rowptr, colind, p, block_ptr, nsys, sys_block_ptr, values, opt, A);
+  } catch (const AnalyzeError& e) {
+    return e.msg;
+  } catch (const std::bad_alloc&) {
+    return "ddps_analyze: host allocation failed";
+  } catch (const std::exception& e) {
+    return std::string("ddps_analyze: ") + e.what();
+  }
 }
 
 }  // namespace ddps

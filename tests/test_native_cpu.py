@@ -112,3 +112,18 @@ def test_symbolic_ilu_keeps_the_block_order(make, drop):
     # a solve streams the stored entries of the diagonal blocks
     nnz_d = sum(Dii.nnz for Dii in orc.D_blocks)
     assert sizes["factor_lu_entries"] == nnz_d
+
+
+@pytest.mark.parametrize("make,drop", [CASES[1], CASES[3]])
+def test_symbolic_does_not_depend_on_the_thread_count(make, drop, monkeypatch):
+    """The blocks are analysed in parallel; every block writes only its own
+    part of the result, so one thread and several give the same analysis."""
+    P = make()
+    out = []
+    for t in ("1", "3", "16"):
+        monkeypatch.setenv("DDPS_ANALYZE_THREADS", t)
+        out.append(N.ddps_symbolic(P.rowptr, P.colind, P.block_ptr, values=P.values,
+                                   options=_opts(drop)))
+    for sizes, perm, c in out[1:]:
+        assert sizes == out[0][0]
+        assert np.array_equal(perm, out[0][1]) and np.array_equal(c, out[0][2])
