@@ -127,3 +127,21 @@ def test_symbolic_does_not_depend_on_the_thread_count(make, drop, monkeypatch):
     for sizes, perm, c in out[1:]:
         assert sizes == out[0][0]
         assert np.array_equal(perm, out[0][1]) and np.array_equal(c, out[0][2])
+
+
+def test_threaded_analysis_reports_the_first_bad_entry(monkeypatch):
+    """With entries coupling two systems in several blocks, the error names
+    the first one in row order, whatever the thread count."""
+    a = W.small_convdiff_2d(8, 4)
+    b = W.small_random_dd(40, 4, seed=5)
+    rp, ci, v, bp, sbp, srp = stack_systems([(a.rowptr, a.colind, a.values, a.block_ptr),
+                                             (b.rowptr, b.colind, b.values, b.block_ptr)])
+    ci2 = ci.copy()
+    for row, col in ((a.n + 35, 3), (20, a.n + 7)):  # a row of b into a, a row of a into b
+        e = rp[row + 1] - 1 if col > ci2[rp[row + 1] - 1] else rp[row]
+        ci2[e] = col
+        ci2[rp[row]:rp[row + 1]] = np.sort(ci2[rp[row]:rp[row + 1]])
+    for t in ("1", "16"):
+        monkeypatch.setenv("DDPS_ANALYZE_THREADS", t)
+        with pytest.raises(N.DDPSError, match=rf"entry \(20, {a.n + 7}\) couples two systems"):
+            N.ddps_symbolic(rp, ci2, bp, sbp)
