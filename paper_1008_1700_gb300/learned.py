@@ -24,6 +24,7 @@ Guess strategies compared by ``run_sequence``:
 
 from __future__ import annotations
 
+import json
 import math
 import time
 
@@ -31,6 +32,11 @@ import numpy as np
 import torch
 
 from . import native as N
+
+# Checkpoint format: one ``.npz`` file holding the flat parameter vector, the
+# two Adam moment vectors and a JSON string ``meta`` (shape, Adam step count,
+# and for ``StepGuess`` its input and output scalings).
+_CKPT_FORMAT = "ddps-guessnet-1"
 
 
 class GuessNet:
@@ -56,6 +62,44 @@ class GuessNet:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.step = 0
         self._ws = {}
+
+    def _meta(self):
+        return {"format": _CKPT_FORMAT, "d_in": self.d_in, "d_out": self.d_out,
+                "hidden": self.hidden, "layers": self.layers, "count": int(self.count),
+                "step": int(self.step)}
+
+    def _arrays(self):
+        return {k: getattr(self, k).detach().to("cpu", torch.float32).numpy()
+                for k in ("params", "m", "v")}
+
+    @classmethod
+    def _from_state(cls, meta, arrays, device):
+        if meta.get("format") != _CKPT_FORMAT:
+            raise ValueError(f"not a GuessNet checkpoint (format {meta.get('format')!r})")
+        net = cls(meta["d_in"], meta["d_out"], meta["hidden"], meta["layers"], device=device)
+        if net.count != meta["count"]:
+            raise ValueError(f"checkpoint holds {meta['count']} parameters, the network "
+                             f"has {net.count}")
+        for k in ("params", "m", "v"):
+            a = np.asarray(arrays[k])
+            if a.dtype != np.float32 or a.shape != (net.count,):
+                raise ValueError(f"checkpoint array {k!r} has dtype {a.dtype} and shape "
+                                 f"{a.shape}, expected float32 ({net.count},)")
+            getattr(net, k).copy_(torch.from_numpy(a))
+        net.step = int(meta["step"])
+        return net
+
+    def save(self, path):
+        """Writes the weights, the Adam moments and step count, and the shape
+        to ``path`` (one ``.npz`` file), so a later run can predict, or go on
+        training, without the training sequence."""
+        _write_ckpt(path, self._meta(), self._arrays())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """The network saved by ``save``, on ``device``."""
+        meta, arrays = _read_ckpt(path)
+        return cls._from_state(meta, arrays, device)
 
     def _workspace(self, B):
         if B not in self._ws:
@@ -95,6 +139,20 @@ class GuessNet:
         return losses
 
 
+def _write_ckpt(path, meta, arrays):
+    with open(path, "wb") as f:
+        np.savez(f, meta=np.array(json.dumps(meta, sort_keys=True)), **arrays)
+
+
+def _read_ckpt(path):
+    with np.load(path, allow_pickle=False) as z:
+        if "meta" not in z.files:
+            raise ValueError(f"{path}: no checkpoint metadata")
+        meta = json.loads(str(z["meta"]))
+        arrays = {k: z[k] for k in z.files if k != "meta"}
+    return meta, arrays
+
+
 def _beta(b, b_mean, b_scale):
     return (b - b_mean) / b_scale
 
@@ -115,6 +173,31 @@ class StepGuess:
                          dtype=torch.float32, device=Z.device)
         self.net = GuessNet(2, Z.shape[1], hidden, layers, seed)
         self.losses = self.net.fit(X, (D / self.scale).to(torch.float32), iters=fit_iters, lr=lr)
+
+    @classmethod
+    def from_parts(cls, net, b_mean, b_scale, scale):
+        """A predictor from a trained network and its scalings (no training)."""
+        g = cls.__new__(cls)
+        g.net, g.b_mean, g.b_scale, g.scale = net, float(b_mean), float(b_scale), float(scale)
+        g.losses = []
+        return g
+
+    def save(self, path):
+        """Writes the network (as ``GuessNet.save``) and the scalings of its
+        input and output to ``path``."""
+        meta = self.net._meta()
+        meta.update(kind="step_guess", b_mean=self.b_mean, b_scale=self.b_scale,
+                    scale=self.scale)
+        _write_ckpt(path, meta, self.net._arrays())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """The predictor saved by ``save``, on ``device``."""
+        meta, arrays = _read_ckpt(path)
+        if meta.get("kind") != "step_guess":
+            raise ValueError(f"{path}: not a StepGuess checkpoint")
+        net = GuessNet._from_state(meta, arrays, device)
+        return cls.from_parts(net, meta["b_mean"], meta["b_scale"], meta["scale"])
 
     def predict(self, z_prev, b_t, b_prev):
         bb = _beta(b_t, self.b_mean, self.b_scale)
