@@ -2,6 +2,7 @@
 // control of the numeric phases.  The arithmetic of every step runs in the
 // kernels of factor.cu, solve.cu and krylov.cu; this file only sequences them.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -277,14 +278,29 @@ cudaEvent_t next_event(ddps_handle* h) {
   return h->ev_pool[h->ev_next++];
 }
 
+// An NVTX range over a scope (API phases, kernel classes): host-side markers
+// that a profiler can show or filter on; without one attached they do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* const kProfName[DDPS_PROF_CLASSES] = {
+    "assemble",     "extend_add",  "front_lu", "spike_fwd",     "spike_bwd",   "ghat_extract",
+    "block_solve",  "ghat_matvec", "spmv",     "direct_factor", "direct_solve"};
+
 // Records a CUDA-event pair around the launches of one kernel class when that
-// class is enabled in the profiling mask.
+// class is enabled in the profiling mask, inside an NVTX range named for the
+// class.
 struct Prof {
   ddps_handle* h;
   int cls;
   cudaStream_t s;
   cudaEvent_t b = nullptr;
   Prof(ddps_handle* hh, int c, cudaStream_t st) : h(hh), cls(c), s(st) {
+    if (cls >= 0) nvtxRangePushA(kProfName[cls]);
     if (cls >= 0 && (h->prof_mask & (1 << cls))) {
       cudaEvent_t a = next_event(h);
       b = next_event(h);
@@ -294,6 +310,7 @@ struct Prof {
   }
   ~Prof() {
     if (b) cudaEventRecord(b, s);
+    if (cls >= 0) nvtxRangePop();
   }
 };
 
@@ -1157,6 +1174,7 @@ double inner_solve(ddps_handle* h, const double* ghat64, double* zhat64, const d
 
 double inner_dispatch(ddps_handle* h, const double* ghat64, double* zhat64, const double* z0,
                       cudaStream_t s) {
+  NvtxRange nv("reduced_solve");
   const int gp = h->opt.ghat_prec, ip = h->opt.inner_prec;
   if (gp == DDPS_FP64) return inner_solve<double, double>(h, ghat64, zhat64, z0, s);
   if (gp == DDPS_FP32)
@@ -2132,6 +2150,7 @@ ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const in
     return DDPS_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  NvtxRange nv("ddps_analyze");
   ddps_handle* h = new (std::nothrow) ddps_handle();
   if (!h) {
     g_last_error = "ddps_analyze: host allocation failed";
@@ -2164,6 +2183,7 @@ ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const in
 
 static ddps_status factor_values(ddps_handle* h, const double* values, bool host, void* stream) {
   if (!h || !values) return DDPS_ERR_INVALID_ARG;
+  NvtxRange nv(host ? "ddps_factor_host" : "ddps_factor");
   cudaStream_t s = as_stream(stream);
   try {
     h->factored = false;
@@ -2230,6 +2250,7 @@ ddps_status ddps_solve(ddps_handle* h, const double* f, double* x, int32_t nrhs,
     h->err = "ddps_solve: call ddps_factor first";
     return DDPS_ERR_STATE;
   }
+  NvtxRange nv("ddps_solve");
   auto t0 = std::chrono::steady_clock::now();
   try {
     const int64_t n = h->A.n;
@@ -2259,6 +2280,7 @@ ddps_status ddps_solve_host(ddps_handle* h, const double* f_host, double* x_host
     h->err = "ddps_solve_host: call ddps_factor first";
     return DDPS_ERR_STATE;
   }
+  NvtxRange nv("ddps_solve_host");
   cudaStream_t s = as_stream(stream);
   auto t0 = std::chrono::steady_clock::now();
   try {
