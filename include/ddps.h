@@ -195,8 +195,8 @@ void ddps_default_options(ddps_options* opt);
  *                     drop rule reads values), else may be NULL
  *   opt               host options (NULL = defaults)
  * The blocks are analysed on host threads (the environment variable
- * DDPS_ANALYZE_THREADS sets their number, default the hardware threads up to
- * 64); the analysis is the same for every thread count.  The call returns
+ * DDPS_ANALYZE_THREADS sets their number, default the CPUs the process may run
+ * on, up to 64); the analysis is the same for every thread count.  The call returns
  * after all of them have finished.
  * On success *out owns the analysis and the device copies of the pattern. */
 ddps_status ddps_analyze(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,

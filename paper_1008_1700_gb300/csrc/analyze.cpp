@@ -27,6 +27,10 @@
 #include <system_error>
 #include <thread>
 
+#ifdef __linux__
+#include <sched.h>
+#endif
+
 #include "ddps_internal.h"
 
 namespace ddps {
@@ -39,14 +43,21 @@ struct AnalyzeError {
 };
 
 // Host threads of the analysis: DDPS_ANALYZE_THREADS if set (>= 1), else the
-// hardware threads, at most 64.
+// CPUs this process may run on (its affinity mask; the hardware threads where
+// that is not available), at most 64.
 int analysis_threads() {
   if (const char* s = std::getenv("DDPS_ANALYZE_THREADS")) {
     const int v = std::atoi(s);
     if (v >= 1) return std::min(v, 256);
   }
-  const unsigned hw = std::thread::hardware_concurrency();
-  return hw == 0 ? 1 : (int)std::min(hw, 64u);
+  int hw = 0;
+#ifdef __linux__
+  cpu_set_t set;
+  CPU_ZERO(&set);
+  if (sched_getaffinity(0, sizeof(set), &set) == 0) hw = CPU_COUNT(&set);
+#endif
+  if (hw <= 0) hw = (int)std::thread::hardware_concurrency();
+  return hw <= 0 ? 1 : std::min(hw, 64);
 }
 
 // Runs body(i) for every i in [0, count), items handed out in order from a
